@@ -1,0 +1,248 @@
+/*
+ * lco.h -- C ABI of the GB300 (sm_103a) library for sparse-tensor
+ * rearrangement and multiplication over the linearised-coordinate (LCO)
+ * format (Harrison & Joseph, "High Performance Rearrangement and
+ * Multiplication Routines for Sparse Tensor Arithmetic").
+ *
+ * Data model (Sec. 3.1, Table 1).  An LCO tensor of order N holds nnz
+ * non-zeros as two parallel arrays: signed 64-bit linearised index values
+ * (LIVs) and IEEE double values.  The LIV of coordinate (c_0 .. c_{N-1})
+ * under lexicographic order `sig` (sig[0] = least significant mode) is
+ *     LIV = c_{sig[0]} + n_{sig[0]} (c_{sig[1]} + n_{sig[1]} (c_{sig[2]} + ...)),
+ * e.g. LIV = i + n_i (j + n_j k) for sig {0,1,2}.  The product of the dims
+ * must not exceed 2^63 - 1 (Sec. 3.1).  A valid tensor has strictly
+ * ascending LIVs (sorted, no duplicates).
+ *
+ * Conventions for every entry point:
+ *   - Array arguments named *_liv, *_val, ws are DEVICE pointers owned by
+ *     the caller; lco_shape / lco_plan_info / lco_rp_info are HOST structs.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All device
+ *     work is enqueued asynchronously on it; nothing synchronises the stream
+ *     unless the entry point says so.
+ *   - The return value is a status (lco_status) of the host-side checks and
+ *     launches.  Errors found on the device (a wait that ran out, a capacity
+ *     that was too small) are written to the workspace header and read with
+ *     lco_workspace_status() once the stream has finished.
+ *   - Workspaces are device buffers of the size the matching *_workspace()
+ *     call reports; they must be 256-byte aligned, zero-filled before their
+ *     first use, and not touched by the caller between calls.  A workspace
+ *     serves one call at a time.
+ *   - Outputs must not alias inputs.
+ *   - No entry point allocates device memory except lco_serve_create.
+ */
+#ifndef LCO_H
+#define LCO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LCO_MAX_ORDER 16
+
+typedef enum {
+    LCO_OK = 0,
+    LCO_ERR_INVALID = 1,    /* malformed arguments (sig, dims, modes, sizes, pointers) */
+    LCO_ERR_OVERFLOW = 2,   /* product of dims (or m*n of a contraction) > 2^63 - 1 */
+    LCO_ERR_UNSORTED = 3,   /* input LIVs not strictly ascending (checking entry points) */
+    LCO_ERR_OOM = 4,        /* workspace smaller than reported, or host allocation failed */
+    LCO_ERR_TIMEOUT = 5,    /* a device-side wait ran out (device status only) */
+    LCO_ERR_CUDA = 6,       /* a CUDA runtime call failed */
+    LCO_ERR_ADMISSION = 7,  /* serve: request does not fit the memory budget */
+    LCO_ERR_CAPACITY = 8    /* output capacity smaller than the product count f */
+} lco_status;
+
+/* Shape of an LCO tensor (host struct).  sig[t] is the mode of significance
+ * rank t, t = 0 least significant; dims[mode] is the range of that mode. */
+typedef struct {
+    int32_t order;
+    int32_t sig[LCO_MAX_ORDER];
+    int64_t dims[LCO_MAX_ORDER];
+    int64_t nnz;
+} lco_shape;
+
+/* Human-readable name of a status code (static string). */
+const char *lco_status_str(int32_t status);
+
+/* Library build identification: returns the CUDA architecture the device
+ * code was compiled for (e.g. 1030 for sm_103a). */
+int32_t lco_build_arch(void);
+
+/* Reads the device status word of a workspace (the first 4 bytes) after
+ * synchronising `stream`.  *status receives LCO_OK or the device error. */
+int32_t lco_workspace_status(const void *ws, int32_t *status, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Kernel timing and launch counting (tracing support; no paper        */
+/* counterpart).  When timing is enabled, every kernel the library     */
+/* launches on a stream that is not being captured into a CUDA graph   */
+/* is bracketed by two CUDA events on that stream.                     */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    char name[40];   /* kernel name */
+    float ms;        /* elapsed time between the bracketing events */
+} lco_timing_record;
+
+/* Enables (1) or disables (0) kernel timing and clears recorded launches. */
+int32_t lco_timing_enable(int32_t enable);
+/* Waits for the recorded launches to finish and copies up to `max` records
+ * (oldest first) to `out`; *count receives the number copied.  The record
+ * buffer (4096 launches) is then cleared. */
+int32_t lco_timing_read(lco_timing_record *out, int32_t max, int32_t *count);
+/* Number of kernels this library has launched from the host since it was
+ * loaded (graph replays are not counted). */
+int64_t lco_launch_count(void);
+
+/* ------------------------------------------------------------------ */
+/* Re-linearisation ("LIV shuffle", Sec. 3.1 and Sec. 4.1 first step)  */
+/* ------------------------------------------------------------------ */
+
+/* Recomputes every LIV of `t` (order t->sig) for the order `new_sig`:
+ * liv_out[e] = LIV of the coordinates of liv_in[e] under new_sig.  The
+ * element order is unchanged.  liv_in / liv_out: device, t->nnz int64 each.
+ * Errors: LCO_ERR_INVALID (sig not a permutation, order outside 1..16,
+ * dims < 1), LCO_ERR_OVERFLOW (product of dims > 2^63 - 1).  LIVs outside
+ * [0, prod dims) give unspecified output values but never out-of-bounds
+ * accesses. */
+int32_t lco_relinearise(const lco_shape *t, const int32_t *new_sig,
+                        const int64_t *liv_in, int64_t *liv_out, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Radix permutation (Sec. 4, "permutation": rearranging sorted data   */
+/* into a new lexicographic order; Sec. 4.1 the RP algorithm)           */
+/* ------------------------------------------------------------------ */
+
+/* Host-side description of how a permutation is carried out (Sec. 4.1):
+ * which modes are rearrangement indices, the region size m_top and the
+ * resting-suffix divisor m_low, the sort key width and the radix passes. */
+typedef struct {
+    int32_t n_rearr;                 /* number of rearrangement indices; 0 = identity */
+    int32_t is_rearr[LCO_MAX_ORDER]; /* per mode: 1 rearrangement, 0 resting */
+    int64_t m_top;                   /* index values per region of constant leading resting indices */
+    int64_t m_low;                   /* product of dims of the resting suffix */
+    int32_t key_bits;                /* bits of the sort key newLIV / m_low */
+    int32_t digit_bits;              /* radix digit width */
+    int32_t passes;                  /* LSD passes (before histogram-based skipping) */
+    int32_t segments;                /* 1 = flat sort */
+} lco_rp_info;
+
+/* Fills *info for permuting a tensor of shape `t` to `new_sig`.  Host only,
+ * no device work.  Errors: LCO_ERR_INVALID, LCO_ERR_OVERFLOW. */
+int32_t lco_radix_permute_info(const lco_shape *t, const int32_t *new_sig, lco_rp_info *info);
+
+/* Workspace bytes for lco_radix_permute on shape `t` (nnz = t->nnz). */
+int32_t lco_radix_permute_workspace(const lco_shape *t, const int32_t *new_sig, size_t *ws_bytes);
+
+/* Rearranges (liv_in, val_in), strictly ascending in order t->sig, into
+ * (liv_out, val_out), strictly ascending in order new_sig, with liv_out
+ * holding the new LIVs.  Values are moved bit-exactly.  Implementation:
+ * a fused re-linearise + one-read digit histogram, then one stable
+ * least-significant-digit scatter pass per radix digit of the key
+ * newLIV div m_low (the resting suffix is supplied by stability); passes
+ * whose digit is constant over the data are skipped on the device.
+ * liv_in/val_in/liv_out/val_out: device, t->nnz elements each, no aliasing.
+ * ws: device workspace of lco_radix_permute_workspace() bytes.
+ * Errors: LCO_ERR_INVALID, LCO_ERR_OVERFLOW, LCO_ERR_OOM (ws too small),
+ * LCO_ERR_CUDA; device status LCO_ERR_TIMEOUT. */
+int32_t lco_radix_permute(const lco_shape *t, const int32_t *new_sig,
+                          const int64_t *liv_in, const double *val_in,
+                          int64_t *liv_out, double *val_out,
+                          void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Contraction C = A x_modes B (Sec. 5: map to matrices, convert to a   */
+/* multiplication datatype and multiply, map back; Table 4 dispatch)    */
+/* ------------------------------------------------------------------ */
+
+typedef enum {
+    LCO_ALG_AUTO = -1,
+    LCO_ALG_CSR = 0,    /* Sec. 5.2.2, row-by-row with an accumulator, B singly compressed */
+    LCO_ALG_CSC = 1,    /* column-by-column counterpart (run as CSR on the transposed product) */
+    LCO_ALG_DCSR = 2,   /* Sec. 5.2.3, B doubly compressed (row-sparse B) */
+    LCO_ALG_DCSC = 3,
+    LCO_ALG_CSRNA = 4,  /* Sec. 5.2.4, no accumulator: expand f(i), sort, sum duplicates */
+    LCO_ALG_CSCNA = 5,
+    LCO_ALG_SOP = 6     /* Sec. 5.2.5, simple outer product: expand all f, sort, sum */
+} lco_alg;
+
+typedef struct lco_plan lco_plan;   /* opaque host object */
+
+typedef struct {
+    int32_t alg;             /* lco_alg chosen (Table 4, or forced) */
+    int32_t transposed;      /* 1: column variant, run on B^T A^T; C is column-major */
+    int32_t class_a;         /* 0 sparse, 1 row-sparse, 2 column-sparse, 3 index-sparse */
+    int32_t class_b;
+    int32_t permute_a;       /* 1 if A must be rearranged into its matrix order */
+    int32_t permute_b;
+    int64_t m, k, n;         /* matrix sizes: A is m x k, B is k x n */
+    lco_shape c_shape;       /* modes, dims and order of C; c_shape.nnz is 0 */
+} lco_plan_info;
+
+/* Plans C = A x B contracting modes_a[i] of A with modes_b[i] of B
+ * (i < ncontract; pairs listed most significant first in the matrix
+ * column/row index).  C's modes are A's free modes in increasing mode
+ * number followed by B's free modes in increasing mode number.  C is
+ * row-major (its last mode least significant) for the row variants and
+ * column-major (B's free modes most significant) for the column variants;
+ * the chosen order is reported in lco_plan_info.c_shape.sig.
+ * force_alg = LCO_ALG_AUTO applies Table 4 with the hyper-sparsity test
+ * dim / nnz > 3; any other lco_alg value forces that algorithm.
+ * Host only.  Errors: LCO_ERR_INVALID (modes, dims mismatch, order),
+ * LCO_ERR_OVERFLOW (m*n > 2^63 - 1). */
+int32_t lco_contract_plan(const lco_shape *a, const lco_shape *b, int32_t ncontract,
+                          const int32_t *modes_a, const int32_t *modes_b,
+                          int32_t force_alg, lco_plan **plan);
+int32_t lco_plan_get_info(const lco_plan *plan, lco_plan_info *info);
+int32_t lco_plan_destroy(lco_plan *plan);
+
+/* Workspace bytes for a contraction whose output capacity is `cap` entries
+ * (cap must be >= f, the number of scalar products). */
+int32_t lco_contract_workspace(const lco_plan *plan, int64_t cap, size_t *ws_bytes);
+
+/* Results of a contraction, written by the device into the workspace
+ * header and read with lco_contract_result(). */
+typedef struct {
+    int32_t status;   /* LCO_OK, LCO_ERR_CAPACITY (f > cap), LCO_ERR_TIMEOUT */
+    int32_t alg;      /* algorithm that ran */
+    int64_t nnz_c;    /* number of entries written to C */
+    int64_t f;        /* number of scalar products (Sec. 5.2 notation f) */
+    int64_t nzr_b;    /* non-empty rows of the (matricised) B */
+} lco_contract_result;
+
+/* Phase 1 ("symbolic"): rearranges A and B into their matrix orders when
+ * needed, builds B's multiplication datatype (CSR row pointers or DCSR
+ * rows with an auxiliary index) and counts the products f.  Leaves its
+ * results in `ws`.  a_liv/a_val/b_liv/b_val: device, nnz of each shape. */
+int32_t lco_contract_symbolic(const lco_plan *plan,
+                              const int64_t *a_liv, const double *a_val,
+                              const int64_t *b_liv, const double *b_val,
+                              void *ws, size_t ws_bytes, void *stream);
+
+/* Phase 2 ("numeric"): multiplies and writes C (c_liv/c_val, device, room
+ * for `cap` entries) sorted in C's order, using the phase-1 results in
+ * `ws`.  If f > cap nothing is written and the device status is
+ * LCO_ERR_CAPACITY.  The number of entries written is in the result. */
+int32_t lco_contract_numeric(const lco_plan *plan,
+                             const int64_t *a_liv, const double *a_val,
+                             const int64_t *b_liv, const double *b_val,
+                             int64_t *c_liv, double *c_val, int64_t cap,
+                             void *ws, size_t ws_bytes, void *stream);
+
+/* Phase 1 followed by phase 2 on the same stream, no host synchronisation. */
+int32_t lco_contract(const lco_plan *plan,
+                     const int64_t *a_liv, const double *a_val,
+                     const int64_t *b_liv, const double *b_val,
+                     int64_t *c_liv, double *c_val, int64_t cap,
+                     void *ws, size_t ws_bytes, void *stream);
+
+/* Synchronises `stream` and copies the result header of `ws` to *out. */
+int32_t lco_contract_result_get(const void *ws, lco_contract_result *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LCO_H */

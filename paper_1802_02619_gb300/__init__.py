@@ -1,0 +1,401 @@
+"""GB300 (sm_103a) sparse-tensor rearrangement and multiplication over the
+linearised-coordinate (LCO) format (Harrison & Joseph, arXiv 1802.02619).
+
+This module is a thin ctypes binding over the C ABI declared in
+``include/lco.h`` (library ``_lib/liblco.so``).  It only marshals arguments:
+every step of the hot path runs in the library's CUDA kernels.  PyTorch is
+used for device memory and streams.  There is no CPU fallback: if the
+library is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import torch
+
+from . import _build
+
+MAX_ORDER = 16
+ALG_NAMES = ("CSR", "CSC", "DCSR", "DCSC", "CSRNA", "CSCNA", "SOP")
+ALG = {name: i for i, name in enumerate(ALG_NAMES)}
+
+STATUS = {
+    0: "ok", 1: "invalid argument", 2: "index space exceeds 2^63-1", 3: "unsorted input",
+    4: "workspace too small", 5: "device wait timed out", 6: "CUDA runtime error",
+    7: "admission refused", 8: "output capacity too small",
+}
+
+
+class LcoError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)} (status {status})")
+
+
+class Shape(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("sig", ctypes.c_int32 * MAX_ORDER),
+                ("dims", ctypes.c_int64 * MAX_ORDER), ("nnz", ctypes.c_int64)]
+
+
+class RpInfo(ctypes.Structure):
+    _fields_ = [("n_rearr", ctypes.c_int32), ("is_rearr", ctypes.c_int32 * MAX_ORDER),
+                ("m_top", ctypes.c_int64), ("m_low", ctypes.c_int64), ("key_bits", ctypes.c_int32),
+                ("digit_bits", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("segments", ctypes.c_int32)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("alg", ctypes.c_int32), ("transposed", ctypes.c_int32),
+                ("class_a", ctypes.c_int32), ("class_b", ctypes.c_int32),
+                ("permute_a", ctypes.c_int32), ("permute_b", ctypes.c_int32),
+                ("m", ctypes.c_int64), ("k", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("c_shape", Shape)]
+
+
+class ContractResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("alg", ctypes.c_int32), ("nnz_c", ctypes.c_int64),
+                ("f", ctypes.c_int64), ("nzr_b", ctypes.c_int64)]
+
+
+class TimingRecord(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("ms", ctypes.c_float)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGNATURES = {
+    "lco_status_str": ([ctypes.c_int32], ctypes.c_char_p),
+    "lco_build_arch": ([], ctypes.c_int32),
+    "lco_workspace_status": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p], ctypes.c_int32),
+    "lco_timing_enable": ([ctypes.c_int32], ctypes.c_int32),
+    "lco_timing_read": ([ctypes.POINTER(TimingRecord), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
+                        ctypes.c_int32),
+    "lco_launch_count": ([], ctypes.c_int64),
+    "lco_relinearise": ([ctypes.POINTER(Shape), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                         ctypes.c_void_p], ctypes.c_int32),
+    "lco_radix_permute_info": ([ctypes.POINTER(Shape), ctypes.c_void_p, ctypes.POINTER(RpInfo)],
+                               ctypes.c_int32),
+    "lco_radix_permute_workspace": ([ctypes.POINTER(Shape), ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int32),
+    "lco_radix_permute": ([ctypes.POINTER(Shape), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                           ctypes.c_void_p], ctypes.c_int32),
+    "lco_contract_plan": ([ctypes.POINTER(Shape), ctypes.POINTER(Shape), ctypes.c_int32, ctypes.c_void_p,
+                           ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int32),
+    "lco_plan_get_info": ([ctypes.c_void_p, ctypes.POINTER(PlanInfo)], ctypes.c_int32),
+    "lco_plan_destroy": ([ctypes.c_void_p], ctypes.c_int32),
+    "lco_contract_workspace": ([ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)],
+                               ctypes.c_int32),
+    "lco_contract_symbolic": ([ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_void_p, ctypes.c_size_t,
+                                                                          ctypes.c_void_p], ctypes.c_int32),
+    "lco_contract_numeric": ([ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.c_int64, ctypes.c_void_p,
+                                                                         ctypes.c_size_t, ctypes.c_void_p],
+                             ctypes.c_int32),
+    "lco_contract": ([ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.c_int64, ctypes.c_void_p,
+                                                                 ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int32),
+    "lco_contract_result_get": ([ctypes.c_void_p, ctypes.POINTER(ContractResult), ctypes.c_void_p],
+                                ctypes.c_int32),
+}
+
+
+def lib_path() -> str:
+    return _build.SO_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Load liblco.so (building it with nvcc if it is missing or stale).
+
+    Raises if the library cannot be built or loaded: there is no fallback."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and _build.is_stale():
+            _build.build()
+        if not os.path.exists(_build.SO_PATH):
+            raise RuntimeError(f"CUDA library not built: {_build.SO_PATH}")
+        lib = ctypes.CDLL(_build.SO_PATH)
+        for name, (args, res) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def exported_symbols():
+    return sorted(_SIGNATURES)
+
+
+def timing_enable(on: bool = True):
+    """Bracket every library kernel launch with CUDA events (outside graph capture)."""
+    _check(load().lco_timing_enable(1 if on else 0), "lco_timing_enable")
+
+
+def timing_read():
+    """[(kernel name, ms)] of the launches recorded since timing was enabled."""
+    lib = load()
+    recs = (TimingRecord * 4096)()
+    n = ctypes.c_int32()
+    _check(lib.lco_timing_read(recs, 4096, ctypes.byref(n)), "lco_timing_read")
+    return [(recs[i].name.decode(), float(recs[i].ms)) for i in range(n.value)]
+
+
+def launch_count() -> int:
+    return int(load().lco_launch_count())
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise LcoError(rc, what)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
+
+
+def _sig_arr(sig):
+    a = (ctypes.c_int32 * MAX_ORDER)()
+    for i, s in enumerate(sig):
+        a[i] = int(s)
+    return a
+
+
+def make_shape(dims: Sequence[int], sig: Sequence[int], nnz: int) -> Shape:
+    if len(dims) != len(sig) or not (1 <= len(dims) <= MAX_ORDER):
+        raise ValueError("dims and sig must have the same length (1..16)")
+    s = Shape()
+    s.order = len(dims)
+    for i, (d, g) in enumerate(zip(dims, sig)):
+        s.dims[i] = int(d)
+        s.sig[i] = int(g)
+    s.nnz = int(nnz)
+    return s
+
+
+def _stream(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and (not t.is_cuda):
+            raise ValueError("LCO arrays must be CUDA tensors")
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    """Zero-filled device workspace of at least nbytes (256-byte aligned)."""
+    n = max(256, (int(nbytes) + 255) // 256 * 256)
+    return torch.zeros(n, dtype=torch.uint8, device=device or "cuda")
+
+
+@dataclass
+class LcoTensor:
+    """An LCO tensor: int64 LIVs (strictly ascending in order `sig`) and
+    float64 values, both on the GPU.  sig[0] is the least significant mode."""
+    dims: list
+    sig: list
+    liv: torch.Tensor
+    val: torch.Tensor
+
+    @property
+    def nnz(self) -> int:
+        return int(self.liv.numel())
+
+    @property
+    def order(self) -> int:
+        return len(self.dims)
+
+    def shape(self) -> Shape:
+        return make_shape(self.dims, self.sig, self.nnz)
+
+    @staticmethod
+    def from_host(T: dict, device="cuda") -> "LcoTensor":
+        liv = torch.as_tensor(T["liv"], dtype=torch.int64).to(device)
+        val = torch.as_tensor(T["val"], dtype=torch.float64).to(device)
+        return LcoTensor(list(T["dims"]), list(T["sig"]), liv, val)
+
+
+# ---------------------------------------------------------------------------
+# Re-linearisation and permutation
+# ---------------------------------------------------------------------------
+
+def relinearise(t: LcoTensor, new_sig, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """LIV shuffle (Sec. 3.1): the LIVs of t in order new_sig (element order kept)."""
+    lib = load()
+    _require_cuda(t.liv)
+    if out is None:
+        out = torch.empty_like(t.liv)
+    sh = t.shape()
+    _check(lib.lco_relinearise(ctypes.byref(sh), _sig_arr(new_sig), _ptr(t.liv), _ptr(out), _stream(stream)),
+           "lco_relinearise")
+    return out
+
+
+def radix_permute_info(dims, sig, new_sig, nnz: int = 0) -> dict:
+    lib = load()
+    sh = make_shape(dims, sig, nnz)
+    info = RpInfo()
+    _check(lib.lco_radix_permute_info(ctypes.byref(sh), _sig_arr(new_sig), ctypes.byref(info)),
+           "lco_radix_permute_info")
+    return {"n_rearr": info.n_rearr, "is_rearr": [info.is_rearr[i] for i in range(len(dims))],
+            "m_top": info.m_top, "m_low": info.m_low, "key_bits": info.key_bits,
+            "digit_bits": info.digit_bits, "passes": info.passes, "segments": info.segments}
+
+
+class Permuter:
+    """Reusable permutation of tensors of one shape to one new order (holds
+    the workspace so repeated calls allocate nothing)."""
+
+    def __init__(self, dims, sig, new_sig, nnz: int, device="cuda"):
+        self.lib = load()
+        self.dims, self.sig, self.new_sig = list(dims), list(sig), list(new_sig)
+        self.nnz = int(nnz)
+        self.sh = make_shape(self.dims, self.sig, self.nnz)
+        self._new = _sig_arr(self.new_sig)
+        nb = ctypes.c_size_t()
+        _check(self.lib.lco_radix_permute_workspace(ctypes.byref(self.sh), self._new, ctypes.byref(nb)),
+               "lco_radix_permute_workspace")
+        self.ws = workspace(nb.value, device)
+
+    def __call__(self, liv, val, liv_out=None, val_out=None, stream=None):
+        _require_cuda(liv, val)
+        if liv.numel() != self.nnz:
+            raise ValueError("nnz differs from the planned size")
+        liv_out = torch.empty_like(liv) if liv_out is None else liv_out
+        val_out = torch.empty_like(val) if val_out is None else val_out
+        _check(self.lib.lco_radix_permute(ctypes.byref(self.sh), self._new, _ptr(liv), _ptr(val), _ptr(liv_out),
+                                          _ptr(val_out), _ptr(self.ws), ctypes.c_size_t(self.ws.numel()),
+                                          _stream(stream)), "lco_radix_permute")
+        return liv_out, val_out
+
+    def device_status(self, stream=None) -> int:
+        st = ctypes.c_int32()
+        _check(self.lib.lco_workspace_status(_ptr(self.ws), ctypes.byref(st), _stream(stream)),
+               "lco_workspace_status")
+        return st.value
+
+
+def radix_permute(t: LcoTensor, new_sig, stream=None) -> LcoTensor:
+    """Rearrange t into lexicographic order new_sig (Sec. 4.1, RP)."""
+    p = Permuter(t.dims, t.sig, new_sig, t.nnz, device=t.liv.device)
+    liv, val = p(t.liv, t.val, stream=stream)
+    st = p.device_status(stream)
+    if st != 0:
+        raise LcoError(st, "lco_radix_permute (device)")
+    return LcoTensor(list(t.dims), list(new_sig), liv, val)
+
+
+# ---------------------------------------------------------------------------
+# Contraction
+# ---------------------------------------------------------------------------
+
+class ContractPlan:
+    """Plan for C = A x_modes B (Sec. 5.2 poly-algorithm, Table 4 dispatch)."""
+
+    def __init__(self, a_dims, a_sig, a_nnz, b_dims, b_sig, b_nnz, modes_a, modes_b, alg=None):
+        self.lib = load()
+        self.sa = make_shape(a_dims, a_sig, a_nnz)
+        self.sb = make_shape(b_dims, b_sig, b_nnz)
+        if len(modes_a) != len(modes_b):
+            raise ValueError("modes_a and modes_b must pair up")
+        nc = len(modes_a)
+        self._ma = (ctypes.c_int32 * max(1, nc))(*[int(x) for x in modes_a])
+        self._mb = (ctypes.c_int32 * max(1, nc))(*[int(x) for x in modes_b])
+        force = -1 if alg is None else (ALG[alg] if isinstance(alg, str) else int(alg))
+        h = ctypes.c_void_p()
+        _check(self.lib.lco_contract_plan(ctypes.byref(self.sa), ctypes.byref(self.sb), nc, self._ma, self._mb,
+                                          force, ctypes.byref(h)), "lco_contract_plan")
+        self.handle = h
+        info = PlanInfo()
+        _check(self.lib.lco_plan_get_info(h, ctypes.byref(info)), "lco_plan_get_info")
+        cs = info.c_shape
+        self.info = {"alg": ALG_NAMES[info.alg], "transposed": info.transposed, "class_a": info.class_a,
+                     "class_b": info.class_b, "permute_a": info.permute_a, "permute_b": info.permute_b,
+                     "m": info.m, "k": info.k, "n": info.n}
+        self.c_dims = [cs.dims[i] for i in range(cs.order)]
+        self.c_sig = [cs.sig[i] for i in range(cs.order)]
+        self.ws = None
+        self.cap = -1
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None) is not None and self.handle.value:
+                self.lib.lco_plan_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+    def workspace_bytes(self, cap: int) -> int:
+        nb = ctypes.c_size_t()
+        _check(self.lib.lco_contract_workspace(self.handle, ctypes.c_int64(int(cap)), ctypes.byref(nb)),
+               "lco_contract_workspace")
+        return nb.value
+
+    def ensure_workspace(self, cap: int, device="cuda"):
+        if self.ws is None or cap > self.cap:
+            old = self.ws
+            self.ws = workspace(self.workspace_bytes(cap), device)
+            if old is not None:
+                # keep the header and phase-1 region (layout is independent of cap)
+                n = min(old.numel(), self.workspace_bytes(0))
+                self.ws[:n].copy_(old[:n])
+            self.cap = cap
+        return self.ws
+
+    def result(self, stream=None) -> dict:
+        r = ContractResult()
+        _check(self.lib.lco_contract_result_get(_ptr(self.ws), ctypes.byref(r), _stream(stream)),
+               "lco_contract_result_get")
+        return {"status": r.status, "alg": ALG_NAMES[r.alg] if 0 <= r.alg < len(ALG_NAMES) else r.alg,
+                "nnz_c": r.nnz_c, "f": r.f, "nzr_b": r.nzr_b}
+
+    def symbolic(self, A: LcoTensor, B: LcoTensor, stream=None):
+        _require_cuda(A.liv, A.val, B.liv, B.val)
+        _check(self.lib.lco_contract_symbolic(self.handle, _ptr(A.liv), _ptr(A.val), _ptr(B.liv), _ptr(B.val),
+                                              _ptr(self.ws), ctypes.c_size_t(self.ws.numel()), _stream(stream)),
+               "lco_contract_symbolic")
+
+    def numeric(self, A: LcoTensor, B: LcoTensor, c_liv, c_val, stream=None):
+        _check(self.lib.lco_contract_numeric(self.handle, _ptr(A.liv), _ptr(A.val), _ptr(B.liv), _ptr(B.val),
+                                             _ptr(c_liv), _ptr(c_val), ctypes.c_int64(c_liv.numel()),
+                                             _ptr(self.ws), ctypes.c_size_t(self.ws.numel()), _stream(stream)),
+               "lco_contract_numeric")
+
+    def run(self, A: LcoTensor, B: LcoTensor, c_liv, c_val, stream=None):
+        """Both phases, no host synchronisation (c_liv/c_val must hold >= f entries)."""
+        _check(self.lib.lco_contract(self.handle, _ptr(A.liv), _ptr(A.val), _ptr(B.liv), _ptr(B.val),
+                                     _ptr(c_liv), _ptr(c_val), ctypes.c_int64(c_liv.numel()),
+                                     _ptr(self.ws), ctypes.c_size_t(self.ws.numel()), _stream(stream)),
+               "lco_contract")
+
+
+def contract(A: LcoTensor, B: LcoTensor, modes_a, modes_b, alg=None, stream=None, return_info=False):
+    """C = A x_modes B as an LCO tensor (Sec. 5.2).  Synchronises twice:
+    after phase 1 to size C by the product count f, and at the end to read nnz_C."""
+    plan = ContractPlan(A.dims, A.sig, A.nnz, B.dims, B.sig, B.nnz, modes_a, modes_b, alg)
+    dev = A.liv.device
+    plan.ensure_workspace(0, dev)
+    plan.symbolic(A, B, stream)
+    r = plan.result(stream)
+    if r["status"] != 0:
+        raise LcoError(r["status"], "lco_contract_symbolic (device)")
+    f = r["f"]
+    plan.ensure_workspace(f, dev)
+    c_liv = torch.empty(max(f, 1), dtype=torch.int64, device=dev)
+    c_val = torch.empty(max(f, 1), dtype=torch.float64, device=dev)
+    plan.numeric(A, B, c_liv[:f] if f else c_liv[:0], c_val[:f] if f else c_val[:0], stream)
+    r = plan.result(stream)
+    if r["status"] != 0:
+        raise LcoError(r["status"], "lco_contract_numeric (device)")
+    n = r["nnz_c"]
+    C = LcoTensor(plan.c_dims, plan.c_sig, c_liv[:n], c_val[:n])
+    if return_info:
+        return C, dict(plan.info, **r)
+    return C

@@ -1,0 +1,120 @@
+// lco_api.cu -- status strings, workspace helpers and kernel timing of the C ABI.
+#include <atomic>
+#include <cstring>
+#include <mutex>
+
+#include "lco_internal.cuh"
+
+namespace lco {
+namespace {
+
+constexpr int kTimingSlots = 4096;
+
+struct TimingSlot {
+    char name[40];
+    cudaEvent_t ev0, ev1;
+    bool used;
+};
+
+std::mutex g_mu;
+bool g_timing = false;
+TimingSlot g_slots[kTimingSlots];
+int g_nslots = 0;
+int g_open = -1;
+std::atomic<long long> g_launches{0};
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+    return st != cudaStreamCaptureStatusNone;
+}
+
+}  // namespace
+
+void timing_begin(const char *name, cudaStream_t s) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_open = -1;
+    if (!g_timing || g_nslots >= kTimingSlots || capturing(s)) return;
+    TimingSlot &t = g_slots[g_nslots];
+    if (!t.used) {
+        if (cudaEventCreate(&t.ev0) != cudaSuccess || cudaEventCreate(&t.ev1) != cudaSuccess) return;
+        t.used = true;
+    }
+    std::strncpy(t.name, name, sizeof(t.name) - 1);
+    t.name[sizeof(t.name) - 1] = 0;
+    if (cudaEventRecord(t.ev0, s) != cudaSuccess) return;
+    g_open = g_nslots;
+}
+
+void timing_end(cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_open < 0) return;
+    if (cudaEventRecord(g_slots[g_open].ev1, s) == cudaSuccess) ++g_nslots;
+    g_open = -1;
+}
+
+}  // namespace lco
+
+extern "C" {
+
+const char *lco_status_str(int32_t status) {
+    switch (status) {
+    case LCO_OK: return "ok";
+    case LCO_ERR_INVALID: return "invalid argument";
+    case LCO_ERR_OVERFLOW: return "index space exceeds 2^63-1";
+    case LCO_ERR_UNSORTED: return "input LIVs not strictly ascending";
+    case LCO_ERR_OOM: return "workspace too small or allocation failed";
+    case LCO_ERR_TIMEOUT: return "device wait timed out";
+    case LCO_ERR_CUDA: return "CUDA runtime error";
+    case LCO_ERR_ADMISSION: return "request exceeds the memory budget";
+    case LCO_ERR_CAPACITY: return "output capacity smaller than the product count";
+    default: return "unknown status";
+    }
+}
+
+int32_t lco_build_arch(void) {
+#ifdef LCO_BUILD_ARCH
+    return LCO_BUILD_ARCH;
+#else
+    return 0;
+#endif
+}
+
+int32_t lco_workspace_status(const void *ws, int32_t *status, void *stream) {
+    if (!ws || !status) return LCO_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LCO_ERR_CUDA;
+    if (cudaMemcpy(status, ws, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) return LCO_ERR_CUDA;
+    return LCO_OK;
+}
+
+int32_t lco_timing_enable(int32_t enable) {
+    std::lock_guard<std::mutex> lk(lco::g_mu);
+    lco::g_timing = enable != 0;
+    lco::g_nslots = 0;
+    lco::g_open = -1;
+    return LCO_OK;
+}
+
+int32_t lco_timing_read(lco_timing_record *out, int32_t max, int32_t *count) {
+    if (!count || (max > 0 && !out)) return LCO_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(lco::g_mu);
+    int32_t n = 0;
+    for (int i = 0; i < lco::g_nslots && n < max; ++i) {
+        lco::TimingSlot &t = lco::g_slots[i];
+        if (cudaEventSynchronize(t.ev1) != cudaSuccess) return LCO_ERR_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.ev0, t.ev1) != cudaSuccess) return LCO_ERR_CUDA;
+        std::memcpy(out[n].name, t.name, sizeof(out[n].name));
+        out[n].ms = ms;
+        ++n;
+    }
+    *count = n;
+    lco::g_nslots = 0;
+    return LCO_OK;
+}
+
+int64_t lco_launch_count(void) { return lco::g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,1466 @@
+// lco_contract.cu -- sparse tensor contraction over LCO (Sec. 5 of the paper).
+//
+// The product is computed on the matricised operands (Sec. 5.2, "map to a
+// matrix, convert to a multiplication datatype and multiply, map back"):
+//   L : mL x k, LIV = row * k + c        (the left operand, sorted row-major)
+//   R : k x nR, LIV = c * nR + col       (the right operand, sorted row-major)
+//   C : mL x nR, LIV = row * nR + col    (sorted, row-major)
+// Row variants (CSR, DCSR, CSRNA, SOP) take L = A, R = B.  Column variants
+// (CSC, DCSC, CSCNA) run the same row kernels on the transposed product
+// C^T = B^T A^T, i.e. L = B, R = A, which yields C in column-major order.
+//
+// Phase 1 (symbolic): rearrange operands into their matrix orders (radix
+// permutation), build R's multiplication datatype -- CSR row pointers
+// (Sec. 5.2.2) or DCSR rows with an auxiliary coarse index (Sec. 5.2.3) --
+// and scan the work 1 + |R row| of every L entry, which gives f.
+// Phase 2 (numeric): the rows of L are cut into chunks of kChunkWork work
+// units; a persistent CTA multiplies a chunk in shared memory, either with a
+// hash accumulator and a sort of the nnz_C(i) distinct outputs (the
+// accumulator branches, Table 6 rows CSC/DCSC) or by sorting all f(i)
+// products and summing duplicates (no-accumulator branch, Sec. 5.2.4), and
+// places its output with decoupled look-back.  SOP (Sec. 5.2.5) expands all f
+// products, sorts them by output LIV with the radix engine and sums runs.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "lco_host.h"
+
+namespace lco {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kCT = 256;                    // threads of the chunk / scan kernels
+constexpr int kCW = kCT / 32;
+constexpr int kChunkWork = 1024;            // work units (entries + products) per chunk
+constexpr int kEntCap = 2048;               // fast path: L entries per chunk
+constexpr int kProdCap = 2048;              // fast path: products per chunk
+constexpr int kHashSlots = 2 * kProdCap;
+constexpr int kSortItems = 8;               // CTA sort: items per thread
+constexpr int kSortTile = kCT * kSortItems; // == kProdCap
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kCT * kScanItems;
+constexpr uint64_t kEmpty = ~0ull;
+
+// header counter slots
+constexpr int kCtrDcsr = 10;
+constexpr int kCtrScan = 11;
+constexpr int kCtrChunk = 12;
+constexpr int kCtrReduce = 13;
+
+enum Lookup { kLookupCsr = 0, kLookupDcsr = 1 };
+
+struct Mdt {                 // multiplication datatype of R
+    int32_t kind;            // Lookup
+    int64_t k;
+    int64_t nnz;
+    const int64_t *row_ptr;  // CSR: [k+1]; DCSR: [nzr+1]
+    const int64_t *row_id;   // DCSR: [nzr]
+    const int64_t *aux;      // DCSR: [naux+1]
+    int32_t aux_shift;
+    int64_t naux;
+};
+
+// (start, length) of R's row c, length 0 when the row is empty.
+__device__ __forceinline__ void mdt_lookup(const Mdt &m, int64_t c, int64_t &b0, int64_t &len) {
+    if (m.kind == kLookupCsr) {
+        b0 = m.row_ptr[c];
+        len = m.row_ptr[c + 1] - b0;
+        return;
+    }
+    const int64_t bkt = c >> m.aux_shift;
+    int64_t lo = m.aux[bkt], hi = m.aux[bkt + 1];
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (m.row_id[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    if (lo < m.aux[bkt + 1] && m.row_id[lo] == c) {
+        b0 = m.row_ptr[lo];
+        len = m.row_ptr[lo + 1] - b0;
+    } else {
+        b0 = 0;
+        len = 0;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Block-wide scans (kCT threads)
+// ------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T u = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Exclusive scan of one value per thread; returns the exclusive prefix and
+// the block total in *total.  Uses `s_tmp` (kCW entries).
+template <typename T>
+__device__ __forceinline__ T block_excl(T v, T *s_tmp, T *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T incl = warp_incl_scan(v);
+    __syncthreads();
+    if (lane == 31) s_tmp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < kCW ? s_tmp[lane] : T(0);
+        T wi = warp_incl_scan(w);
+        if (lane < kCW) s_tmp[lane] = wi - w;
+        if (lane == kCW - 1) s_tmp[kCW] = wi;
+    }
+    __syncthreads();
+    T r = s_tmp[warp] + incl - v;
+    *total = s_tmp[kCW];
+    __syncthreads();
+    return r;
+}
+
+// ------------------------------------------------------------------------
+// CTA-level stable LSD radix sort of (uint64 key, double value) pairs held
+// in shared or global memory (generic pointers), 8-bit digits over the low
+// `kbits` bits.  Ping-pongs between (k0,v0) and (k1,v1); returns 0 if the
+// result ends in (k0,v0), 1 otherwise.  s_whist: kCW*256 u32, s_run: 256 i64.
+// ------------------------------------------------------------------------
+__device__ int cta_sort(uint64_t *k0, double *v0, uint64_t *k1, double *v1, int64_t n, int kbits,
+                        uint32_t *s_whist, int64_t *s_run, int64_t *s_tmp64) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = lanemask_lt();
+    int cur = 0;
+    for (int shift = 0; shift < kbits; shift += 8) {
+        uint64_t *sk = cur ? k1 : k0;
+        double *sv = cur ? v1 : v0;
+        uint64_t *dk = cur ? k0 : k1;
+        double *dv = cur ? v0 : v1;
+        // digit histogram over the whole range -> running digit offsets
+        for (int d = tid; d < kCW * 256; d += kCT) s_whist[d] = 0;
+        __syncthreads();
+        for (int64_t i = tid; i < n; i += kCT) atomicAdd(&s_whist[(uint32_t)(sk[i] >> shift) & 255u], 1u);
+        __syncthreads();
+        {
+            int64_t c = s_whist[tid], tot;
+            int64_t ex = block_excl<int64_t>(c, s_tmp64, &tot);
+            s_run[tid] = ex;
+        }
+        __syncthreads();
+        for (int64_t base = 0; base < n; base += kSortTile) {
+            for (int d = tid; d < kCW * 256; d += kCT) s_whist[d] = 0;
+            __syncthreads();
+            uint32_t pk[kSortItems];
+            uint64_t key[kSortItems];
+            double val[kSortItems];
+            uint32_t *wh = s_whist + warp * 256;
+#pragma unroll
+            for (int i = 0; i < kSortItems; ++i) {
+                const int64_t e = base + warp * (32 * kSortItems) + i * 32 + lane;
+                const bool valid = e < n;
+                key[i] = valid ? sk[e] : 0;
+                val[i] = valid ? sv[e] : 0.0;
+                const uint32_t d = (uint32_t)(key[i] >> shift) & 255u;
+                unsigned peers = __ballot_sync(kFull, valid);
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const unsigned bit = (d >> b) & 1u;
+                    const unsigned bal = __ballot_sync(kFull, bit);
+                    peers &= bit ? bal : ~bal;
+                }
+                const int leader = valid ? __ffs(peers) - 1 : lane;
+                uint32_t bv = 0;
+                if (valid && lane == leader) {
+                    bv = wh[d];
+                    wh[d] = bv + (uint32_t)__popc(peers);
+                }
+                bv = __shfl_sync(kFull, bv, leader);
+                pk[i] = d | ((bv + (uint32_t)__popc(peers & lt)) << 8);
+                __syncwarp();
+            }
+            __syncthreads();
+            // per digit: offsets of each warp, tile total
+            {
+                const int d = tid;   // kCT == 256 digits
+                uint32_t run = 0;
+                for (int w = 0; w < kCW; ++w) {
+                    uint32_t c = s_whist[w * 256 + d];
+                    s_whist[w * 256 + d] = run;
+                    run += c;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < kSortItems; ++i) {
+                    const int64_t e = base + warp * (32 * kSortItems) + i * 32 + lane;
+                    if (e < n) {
+                        const uint32_t dd = pk[i] & 255u;
+                        const int64_t pos = s_run[dd] + wh[dd] + (pk[i] >> 8);
+                        dk[pos] = key[i];
+                        dv[pos] = val[i];
+                    }
+                }
+                __syncthreads();
+                s_run[d] += run;
+            }
+            __syncthreads();
+        }
+        cur ^= 1;
+    }
+    return cur;
+}
+
+__device__ __forceinline__ int bits_for(uint64_t range) {   // ceil(log2(range)), range >= 1
+    return range <= 1 ? 0 : 64 - __clzll((long long)(range - 1));
+}
+
+// ------------------------------------------------------------------------
+// MDT kernels (Sec. 5.2.2 CSR, Sec. 5.2.3 DCSR)
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_csr_rowptr(const int64_t *liv, int64_t nnz, DivU64 div_n, int64_t k,
+                                                    int64_t *row_ptr) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // rows are clamped to [0, k - 1] so that LIVs outside the index space
+    // can never address past row_ptr
+    for (int64_t e = gt; e < nnz; e += gsz) {
+        const uint64_t r0 = divu(div_n, (uint64_t)liv[e]);
+        const int64_t row = r0 < (uint64_t)k ? (int64_t)r0 : k - 1;
+        int64_t prev = -1;
+        if (e > 0) {
+            const uint64_t p0 = divu(div_n, (uint64_t)liv[e - 1]);
+            prev = p0 < (uint64_t)k ? (int64_t)p0 : k - 1;
+        }
+        for (int64_t r = prev + 1; r <= row; ++r) row_ptr[r] = e;
+    }
+    int64_t last = -1;
+    if (nnz > 0) {
+        const uint64_t l0 = divu(div_n, (uint64_t)liv[nnz - 1]);
+        last = l0 < (uint64_t)k ? (int64_t)l0 : k - 1;
+    }
+    for (int64_t r = last + 1 + gt; r <= k; r += gsz) row_ptr[r] = nnz;
+}
+
+struct DcsrArgs {
+    const int64_t *liv;
+    int64_t nnz;
+    DivU64 div_n;
+    int64_t *row_id;
+    int64_t *row_ptr;
+    uint64_t *state;
+    WsHeader *hdr;
+};
+
+// Head flags -> single-pass scan -> compacted (row_id, row_ptr).
+__global__ void __launch_bounds__(kCT) k_dcsr_build(const __grid_constant__ DcsrArgs a) {
+    __shared__ int64_t s_tmp[kCW + 1];
+    __shared__ int64_t s_tile, s_excl;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&a.hdr->counters[kCtrDcsr], 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t rows[kScanItems];
+    int heads = 0;
+    int64_t prev = base > 0 && base - 1 < a.nnz ? (int64_t)divu(a.div_n, (uint64_t)a.liv[base - 1]) : -1;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t e = base + i;
+        if (e < a.nnz) {
+            rows[i] = (int64_t)divu(a.div_n, (uint64_t)a.liv[e]);
+            heads += rows[i] != prev;
+            prev = rows[i];
+        } else {
+            rows[i] = -2;
+        }
+    }
+    int64_t tot;
+    int64_t ex = block_excl<int64_t>((int64_t)heads, s_tmp, &tot);
+    if (threadIdx.x == 0) {
+        lb_store(a.state + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
+        int64_t e = 0;
+        if (tile > 0) {
+            e = (int64_t)lookback(a.state, tile, 1, &a.hdr->status);
+            lb_store(a.state + tile, kFlagIncl | (uint64_t)(e + tot));
+        }
+        s_excl = e;
+        const int64_t ntiles = (a.nnz + kScanTile - 1) / kScanTile;
+        if (tile == ntiles - 1) {
+            a.row_ptr[e + tot] = a.nnz;
+            a.hdr->nzr_b = e + tot;
+        }
+    }
+    __syncthreads();
+    int64_t pos = s_excl + ex;
+    prev = base > 0 && base - 1 < a.nnz ? (int64_t)divu(a.div_n, (uint64_t)a.liv[base - 1]) : -1;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t e = base + i;
+        if (e < a.nnz && rows[i] != prev) {
+            a.row_id[pos] = rows[i];
+            a.row_ptr[pos] = e;
+            ++pos;
+        }
+        if (e < a.nnz) prev = rows[i];
+    }
+}
+
+// Auxiliary coarse index over the sorted row ids: aux[b] = first i with
+// (row_id[i] >> shift) >= b (Buluc & Gilbert's AUX array idea).
+__global__ void __launch_bounds__(256) k_dcsr_aux(const int64_t *row_id, const WsHeader *hdr, int32_t shift,
+                                                  int64_t naux, int64_t *aux, int64_t cap) {
+    const int64_t nzr = hdr->nzr_b;
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= nzr && i <= cap; i += gsz) {
+        int64_t bi = i < nzr ? (int64_t)((uint64_t)row_id[i] >> shift) : naux;
+        int64_t bp = i > 0 ? (int64_t)((uint64_t)row_id[i - 1] >> shift) : -1;
+        if (bi > naux) bi = naux;      // row ids outside [0, k) cannot address past aux
+        if (bp > naux) bp = naux;
+        for (int64_t b = bp + 1; b <= bi; ++b) aux[b] = i;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Work scan over L entries: P[e] = sum_{e' < e} (1 + |R row of e'|).
+// ------------------------------------------------------------------------
+struct ScanArgs {
+    int32_t alg;
+    const int64_t *l_liv;
+    int64_t nnz_l;
+    DivU64 div_k;
+    int64_t k;
+    Mdt mdt;
+    int64_t *P;            // [nnz_l + 1]
+    uint64_t *state;
+    WsHeader *hdr;
+};
+
+__global__ void __launch_bounds__(kCT) k_work_scan(const __grid_constant__ ScanArgs a) {
+    __shared__ int64_t s_tmp[kCW + 1];
+    __shared__ int64_t s_tile, s_excl;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&a.hdr->counters[kCtrScan], 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t w[kScanItems];
+    int64_t local = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t e = base + i;
+        w[i] = 0;
+        if (e < a.nnz_l) {
+            const uint64_t liv = (uint64_t)a.l_liv[e];
+            const uint64_t row = divu(a.div_k, liv);
+            const int64_t c = (int64_t)(liv - row * (uint64_t)a.k);
+            int64_t b0, len;
+            mdt_lookup(a.mdt, c, b0, len);
+            w[i] = 1 + len;
+        }
+        local += w[i];
+    }
+    int64_t tot;
+    int64_t ex = block_excl<int64_t>(local, s_tmp, &tot);
+    if (threadIdx.x == 0) {
+        lb_store(a.state + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
+        int64_t e = 0;
+        if (tile > 0) {
+            e = (int64_t)lookback(a.state, tile, 1, &a.hdr->status);
+            lb_store(a.state + tile, kFlagIncl | (uint64_t)(e + tot));
+        }
+        s_excl = e;
+        const int64_t ntiles = (a.nnz_l + kScanTile - 1) / kScanTile;
+        if (tile == ntiles - 1) {
+            const int64_t W = e + tot;
+            a.P[a.nnz_l] = W;
+            a.hdr->work_total = W;
+            a.hdr->f = W - a.nnz_l;
+            a.hdr->nchunks = (W + kChunkWork - 1) / kChunkWork;
+            a.hdr->alg = a.alg;
+        }
+    }
+    __syncthreads();
+    int64_t run = s_excl + ex;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t e = base + i;
+        if (e < a.nnz_l) a.P[e] = run;
+        run += w[i];
+    }
+}
+
+// ------------------------------------------------------------------------
+// Chunk kernel (phase 2)
+// ------------------------------------------------------------------------
+struct ChunkArgs {
+    const int64_t *l_liv;
+    const double *l_val;
+    const int64_t *r_liv;
+    const double *r_val;
+    int64_t nnz_l;
+    DivU64 div_k;
+    int64_t k;
+    DivU64 div_n;          // nR
+    int64_t nR;
+    int32_t colbits;
+    int32_t acc;           // 1: hash accumulator, 0: sort all products
+    Mdt mdt;
+    const int64_t *P;
+    int64_t *c_liv;
+    double *c_val;
+    int64_t cap;
+    uint64_t *chunk_state;
+    uint32_t *chunk_ctr;
+    // spill scratch (cap-sized, indexed by product offset)
+    uint64_t *sk0;
+    double *sv0;
+    uint64_t *sk1;
+    double *sv1;
+    WsHeader *hdr;
+};
+
+__device__ __forceinline__ int64_t row_of(const ChunkArgs &a, int64_t e) {
+    return (int64_t)divu(a.div_k, (uint64_t)a.l_liv[e]);
+}
+
+// first entry index >= e that starts a row of L (or nnz_l)
+__device__ int64_t first_head_from(const ChunkArgs &a, int64_t e) {
+    if (e >= a.nnz_l) return a.nnz_l;
+    if (e == 0) return 0;
+    const int64_t r = row_of(a, e);
+    if (r != row_of(a, e - 1)) return e;
+    // first entry with LIV >= (r + 1) * k
+    const int64_t bound = (r + 1) * a.k;
+    int64_t lo = e, hi = a.nnz_l;
+    while (lo < hi) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        if (a.l_liv[mid] < bound) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ int64_t lower_bound_P(const int64_t *P, int64_t n, int64_t x) {   // first e in [0,n] with P[e] >= x
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        if (P[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+struct ChunkSmem {
+    int32_t poff[kEntCap + 1];
+    int64_t b0[kEntCap];      // ACC: reused as compacted keys
+    double aval[kEntCap];     // ACC: reused as compacted values
+    uint16_t lrow[kEntCap];
+    int64_t gid[kEntCap];
+    uint64_t pk0[kProdCap];   // products (ping-pong); ACC: 4096-slot hash keys over pk0..pk1
+    uint64_t pk1[kProdCap];
+    double pv0[kProdCap];     // ACC: hash values over pv0..pv1
+    double pv1[kProdCap];
+    uint32_t whist[kCW * 256];
+    int64_t run[256];
+    int64_t tmp64[kCW + 2];
+    int32_t tmp32[kCW + 2];
+};
+
+__global__ void __launch_bounds__(kCT, 1) k_chunk(const __grid_constant__ ChunkArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ChunkSmem &S = *reinterpret_cast<ChunkSmem *>(smem_raw);
+    __shared__ int64_t s_g, s_h0, s_eend, s_e1, s_nprod, s_pbase, s_off;
+    __shared__ int s_fast;
+    const int tid = threadIdx.x;
+    const int64_t f = a.hdr->f;
+    if (f > a.cap) {
+        if (blockIdx.x == 0 && tid == 0) {
+            set_error(&a.hdr->status, LCO_ERR_CAPACITY);
+            a.hdr->nnz_c = 0;
+        }
+        return;
+    }
+    const int64_t W = a.hdr->work_total;
+    const int64_t nchunks = a.hdr->nchunks;
+    const uint64_t colmask = a.colbits >= 64 ? ~0ull : ((1ull << a.colbits) - 1);
+
+    for (;;) {
+        if (tid == 0) {
+            const int64_t g = atomicAdd(a.chunk_ctr, 1u);
+            s_g = g;
+            if (g < nchunks) {
+                const int64_t lo = g * kChunkWork;
+                const int64_t hi = lo + kChunkWork < W ? lo + kChunkWork : W;
+                const int64_t e0 = lower_bound_P(a.P, a.nnz_l, lo);
+                const int64_t e1 = hi >= W ? a.nnz_l : lower_bound_P(a.P, a.nnz_l, hi);
+                const int64_t h0 = first_head_from(a, e0);
+                const int64_t eend = h0 < e1 ? first_head_from(a, e1) : h0;
+                s_h0 = h0;
+                s_e1 = e1;
+                s_eend = eend;
+                s_pbase = a.P[h0] - h0;
+                s_nprod = (a.P[eend] - eend) - (a.P[h0] - h0);
+                s_fast = (eend - h0) <= kEntCap && s_nprod <= kProdCap;
+            }
+        }
+        __syncthreads();
+        const int64_t g = s_g;
+        if (g >= nchunks) break;
+        const int64_t h0 = s_h0, eend = s_eend;
+        const int nent_fast = (int)(eend - h0);
+        const int64_t nprod = s_nprod;
+        int64_t nout = 0;
+
+        if (s_fast) {
+            // ---- stage entries: lookup, local rows, product offsets ----
+            int32_t len_i[kEntCap / kCT];
+            int32_t head_i[kEntCap / kCT];
+            int64_t row_i[kEntCap / kCT];
+            int32_t lsum = 0, hsum = 0;
+#pragma unroll
+            for (int q = 0; q < kEntCap / kCT; ++q) {
+                const int j = tid * (kEntCap / kCT) + q;
+                len_i[q] = 0;
+                head_i[q] = 0;
+                row_i[q] = 0;
+                if (j < nent_fast) {
+                    const int64_t e = h0 + j;
+                    const uint64_t liv = (uint64_t)a.l_liv[e];
+                    const uint64_t row = divu(a.div_k, liv);
+                    const int64_t c = (int64_t)(liv - row * (uint64_t)a.k);
+                    int64_t b0, len;
+                    mdt_lookup(a.mdt, c, b0, len);
+                    S.b0[j] = b0;
+                    S.aval[j] = a.l_val[e];
+                    len_i[q] = (int32_t)len;
+                    row_i[q] = (int64_t)row;
+                    head_i[q] = (j == 0) || ((int64_t)row != row_of(a, e - 1));
+                }
+                lsum += len_i[q];
+                hsum += head_i[q];
+            }
+            int32_t ltot, htot;
+            int32_t lex = block_excl<int32_t>(lsum, S.tmp32, &ltot);
+            int32_t hex = block_excl<int32_t>(hsum, S.tmp32, &htot);
+#pragma unroll
+            for (int q = 0; q < kEntCap / kCT; ++q) {
+                const int j = tid * (kEntCap / kCT) + q;
+                if (j < nent_fast) {
+                    S.poff[j] = lex;
+                    hex += head_i[q];
+                    S.lrow[j] = (uint16_t)(hex - 1);
+                    if (head_i[q]) S.gid[hex - 1] = row_i[q];
+                }
+                lex += len_i[q];
+            }
+            if (tid == 0) S.poff[nent_fast] = ltot;
+            const int nrows = htot;
+            const int np = ltot;
+            if (a.acc) {
+                uint64_t *hk = S.pk0;   // pk0|pk1 contiguous: kHashSlots keys
+                double *hv = S.pv0;     // pv0|pv1 contiguous: kHashSlots values
+                for (int i = tid; i < kHashSlots; i += kCT) {
+                    hk[i] = kEmpty;
+                    hv[i] = 0.0;
+                }
+            }
+            __syncthreads();
+            // ---- expand products ----
+            for (int p = tid; p < np; p += kCT) {
+                int lo = 0, hi = nent_fast;   // owner: last j with poff[j] <= p
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (S.poff[mid] <= p) lo = mid; else hi = mid;
+                }
+                const int own = lo;
+                const int64_t b = S.b0[own] + (p - S.poff[own]);
+                const uint64_t rl = (uint64_t)a.r_liv[b];
+                const uint64_t col = rl - divu(a.div_n, rl) * (uint64_t)a.nR;
+                const uint64_t key = ((uint64_t)S.lrow[own] << a.colbits) | col;
+                const double v = S.aval[own] * a.r_val[b];
+                if (!a.acc) {
+                    S.pk0[p] = key;
+                    S.pv0[p] = v;
+                } else {
+                    uint64_t *hk = S.pk0;
+                    double *hv = S.pv0;
+                    uint32_t slot = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 52) & (kHashSlots - 1);
+                    for (;;) {
+                        const unsigned long long old =
+                            atomicCAS(reinterpret_cast<unsigned long long *>(&hk[slot]), kEmpty, key);
+                        if (old == kEmpty || old == key) {
+                            atomicAdd(&hv[slot], v);
+                            break;
+                        }
+                        slot = (slot + 1) & (kHashSlots - 1);
+                    }
+                }
+            }
+            __syncthreads();
+            const int kbits = a.colbits + bits_for((uint64_t)(nrows > 0 ? nrows : 1));
+            if (!a.acc) {
+                const int res = cta_sort(S.pk0, S.pv0, S.pk1, S.pv1, np, kbits, S.whist, S.run, S.tmp64);
+                uint64_t *k = res ? S.pk1 : S.pk0;
+                double *v = res ? S.pv1 : S.pv0;
+                uint64_t *ok = reinterpret_cast<uint64_t *>(S.b0);
+                double *ov = S.aval;
+                // segmented sum of equal keys, in sorted (generation) order
+                int32_t hcount = 0;
+                for (int q = 0; q < kProdCap / kCT; ++q) {
+                    const int i = tid * (kProdCap / kCT) + q;
+                    if (i < np && (i == 0 || k[i] != k[i - 1])) ++hcount;
+                }
+                int32_t htot2;
+                int32_t o = block_excl<int32_t>(hcount, S.tmp32, &htot2);
+                for (int q = 0; q < kProdCap / kCT; ++q) {
+                    const int i = tid * (kProdCap / kCT) + q;
+                    if (i < np && (i == 0 || k[i] != k[i - 1])) {
+                        double s = v[i];
+                        for (int t = i + 1; t < np && k[t] == k[i]; ++t) s += v[t];
+                        ok[o] = k[i];
+                        ov[o] = s;
+                        ++o;
+                    }
+                }
+                nout = htot2;
+            } else {
+                uint64_t *hk = S.pk0;
+                double *hv = S.pv0;
+                uint64_t *ok = reinterpret_cast<uint64_t *>(S.b0);
+                double *ov = S.aval;
+                int32_t cnt = 0;
+                for (int q = 0; q < kHashSlots / kCT; ++q) cnt += hk[tid * (kHashSlots / kCT) + q] != kEmpty;
+                int32_t tot;
+                int32_t o = block_excl<int32_t>(cnt, S.tmp32, &tot);
+                for (int q = 0; q < kHashSlots / kCT; ++q) {
+                    const int i = tid * (kHashSlots / kCT) + q;
+                    if (hk[i] != kEmpty) {
+                        ok[o] = hk[i];
+                        ov[o] = hv[i];
+                        ++o;
+                    }
+                }
+                __syncthreads();
+                nout = tot;
+                // sort the distinct entries (b0/aval -> pk1/pv1 ping-pong)
+                int r = cta_sort(ok, ov, S.pk1, S.pv1, nout, kbits, S.whist, S.run, S.tmp64);
+                if (r) {
+                    for (int i = tid; i < nout; i += kCT) {
+                        ok[i] = S.pk1[i];
+                        ov[i] = S.pv1[i];
+                    }
+                }
+            }
+            __syncthreads();
+        } else {
+            // ---- spill path: products sorted and reduced in global scratch ----
+            const int64_t pbase = s_pbase;
+            uint64_t *gk0 = a.sk0 + pbase;
+            double *gv0 = a.sv0 + pbase;
+            uint64_t *gk1 = a.sk1 + pbase;
+            double *gv1 = a.sv1 + pbase;
+            int64_t rows_before = 0;
+            int64_t prod_before = 0;
+            for (int64_t t0 = h0; t0 < eend; t0 += kEntCap) {
+                const int ne = (int)((eend - t0) < kEntCap ? (eend - t0) : kEntCap);
+                int32_t len_i[kEntCap / kCT];
+                int32_t head_i[kEntCap / kCT];
+                int64_t row_i[kEntCap / kCT];
+                int64_t lsum = 0;
+                int32_t hsum = 0;
+#pragma unroll
+                for (int q = 0; q < kEntCap / kCT; ++q) {
+                    const int j = tid * (kEntCap / kCT) + q;
+                    len_i[q] = 0;
+                    head_i[q] = 0;
+                    row_i[q] = 0;
+                    if (j < ne) {
+                        const int64_t e = t0 + j;
+                        const uint64_t liv = (uint64_t)a.l_liv[e];
+                        const uint64_t row = divu(a.div_k, liv);
+                        const int64_t c = (int64_t)(liv - row * (uint64_t)a.k);
+                        int64_t b0, len;
+                        mdt_lookup(a.mdt, c, b0, len);
+                        S.b0[j] = b0;
+                        S.aval[j] = a.l_val[e];
+                        len_i[q] = (int32_t)len;
+                        row_i[q] = (int64_t)row;
+                        head_i[q] = (e == h0) || ((int64_t)row != row_of(a, e - 1));
+                    }
+                    lsum += len_i[q];
+                    hsum += head_i[q];
+                }
+                int64_t ltot;
+                int32_t htot;
+                int64_t lex = block_excl<int64_t>(lsum, S.tmp64, &ltot);
+                int32_t hex = block_excl<int32_t>(hsum, S.tmp32, &htot);
+#pragma unroll
+                for (int q = 0; q < kEntCap / kCT; ++q) {
+                    const int j = tid * (kEntCap / kCT) + q;
+                    if (j < ne) {
+                        hex += head_i[q];
+                        const int64_t lr = rows_before + hex - 1;
+                        S.lrow[j] = (uint16_t)lr;   // rows per chunk < kChunkWork
+                        if (head_i[q]) S.gid[lr] = row_i[q];
+                        // expand this entry's products directly (contiguous R row)
+                        const int64_t po = prod_before + lex;
+                        for (int32_t t = 0; t < len_i[q]; ++t) {
+                            const int64_t b = S.b0[j] + t;
+                            const uint64_t rl = (uint64_t)a.r_liv[b];
+                            const uint64_t col = rl - divu(a.div_n, rl) * (uint64_t)a.nR;
+                            gk0[po + t] = ((uint64_t)lr << a.colbits) | col;
+                            gv0[po + t] = S.aval[j] * a.r_val[b];
+                        }
+                    }
+                    lex += len_i[q];
+                }
+                rows_before += htot;
+                prod_before += ltot;
+                __syncthreads();
+            }
+            const int kbits = a.colbits + bits_for((uint64_t)(rows_before > 0 ? rows_before : 1));
+            const int r = cta_sort(gk0, gv0, gk1, gv1, nprod, kbits, S.whist, S.run, S.tmp64);
+            uint64_t *k = r ? gk1 : gk0;
+            double *v = r ? gv1 : gv0;
+            uint64_t *ok = r ? gk0 : gk1;
+            double *ov = r ? gv0 : gv1;
+            // reduce runs of equal keys into the other buffer, in tiles
+            int64_t outc = 0;
+            for (int64_t t0 = 0; t0 < nprod; t0 += kCT) {
+                const int64_t i = t0 + tid;
+                const int hd = (i < nprod) && (i == 0 || k[i] != k[i - 1]);
+                int32_t tot;
+                int32_t o = block_excl<int32_t>(hd, S.tmp32, &tot);
+                if (hd) {
+                    double s = v[i];
+                    for (int64_t t = i + 1; t < nprod && k[t] == k[i]; ++t) s += v[t];
+                    ok[outc + o] = k[i];
+                    ov[outc + o] = s;
+                }
+                outc += tot;
+            }
+            __syncthreads();
+            nout = outc;
+            // remember which global buffer holds the reduced output
+            if (tid == 0) S.tmp64[kCW + 1] = r;
+            __syncthreads();
+        }
+
+        // ---- place the chunk's output: decoupled look-back over chunks ----
+        if (tid == 0) {
+            lb_store(a.chunk_state + g, (g == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)nout);
+            int64_t ex = 0;
+            if (g > 0) {
+                ex = (int64_t)lookback(a.chunk_state, g, 1, &a.hdr->status);
+                lb_store(a.chunk_state + g, kFlagIncl | (uint64_t)(ex + nout));
+            }
+            s_off = ex;
+            if (g == nchunks - 1) a.hdr->nnz_c = ex + nout;
+        }
+        __syncthreads();
+        const int64_t off = s_off;
+        if (s_fast) {
+            const uint64_t *ok = reinterpret_cast<const uint64_t *>(S.b0);
+            const double *ov = S.aval;
+            for (int64_t i = tid; i < nout; i += kCT) {
+                const uint64_t key = ok[i];
+                const int64_t lr = (int64_t)(key >> a.colbits);
+                a.c_liv[off + i] = S.gid[lr] * a.nR + (int64_t)(key & colmask);
+                a.c_val[off + i] = ov[i];
+            }
+        } else {
+            const int r = (int)S.tmp64[kCW + 1];
+            const int64_t pbase = s_pbase;
+            const uint64_t *ok = (r ? a.sk0 : a.sk1) + pbase;
+            const double *ov = (r ? a.sv0 : a.sv1) + pbase;
+            for (int64_t i = tid; i < nout; i += kCT) {
+                const uint64_t key = ok[i];
+                const int64_t lr = (int64_t)(key >> a.colbits);
+                a.c_liv[off + i] = S.gid[lr] * a.nR + (int64_t)(key & colmask);
+                a.c_val[off + i] = ov[i];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------
+// SOP (Sec. 5.2.5): expand every product with its output LIV, sort, sum runs
+// ------------------------------------------------------------------------
+struct SopArgs {
+    const int64_t *l_liv;
+    const double *l_val;
+    const int64_t *r_liv;
+    const double *r_val;
+    int64_t nnz_l;
+    DivU64 div_k;
+    int64_t k;
+    int64_t nR;
+    Mdt mdt;
+    const int64_t *P;
+    int64_t cap;
+    int64_t *out_liv;
+    double *out_val;
+    WsHeader *hdr;
+};
+
+__global__ void __launch_bounds__(256) k_sop_expand(const __grid_constant__ SopArgs a) {
+    if (a.hdr->f > a.cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_error(&a.hdr->status, LCO_ERR_CAPACITY);
+        return;
+    }
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.nnz_l; e += gsz) {
+        const uint64_t liv = (uint64_t)a.l_liv[e];
+        const uint64_t row = divu(a.div_k, liv);
+        const int64_t c = (int64_t)(liv - row * (uint64_t)a.k);
+        int64_t b0, len;
+        mdt_lookup(a.mdt, c, b0, len);
+        const int64_t po = a.P[e] - e;
+        const double av = a.l_val[e];
+        const int64_t rowbase = (int64_t)row * a.nR;
+        for (int64_t t = 0; t < len; ++t) {
+            const int64_t rl = a.r_liv[b0 + t];
+            a.out_liv[po + t] = rowbase + (rl - c * a.nR);
+            a.out_val[po + t] = av * a.r_val[b0 + t];
+        }
+    }
+}
+
+struct ReduceArgs {
+    const int64_t *key;
+    const double *val;
+    int64_t cap;
+    int64_t *c_liv;
+    double *c_val;
+    uint64_t *state;
+    uint32_t *ctr;
+    WsHeader *hdr;
+};
+
+__global__ void __launch_bounds__(kCT) k_reduce_by_key(const __grid_constant__ ReduceArgs a) {
+    __shared__ int64_t s_tmp[kCW + 1];
+    __shared__ int64_t s_tile, s_excl;
+    const int64_t n = a.hdr->f;
+    if (n > a.cap) return;
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    if (tile >= ntiles) {
+        if (n == 0 && tile == 0 && threadIdx.x == 0) a.hdr->nnz_c = 0;
+        return;
+    }
+    const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int heads = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t e = base + i;
+        if (e < n && (e == 0 || a.key[e] != a.key[e - 1])) ++heads;
+    }
+    int64_t tot;
+    int64_t ex = block_excl<int64_t>((int64_t)heads, s_tmp, &tot);
+    if (threadIdx.x == 0) {
+        lb_store(a.state + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
+        int64_t e = 0;
+        if (tile > 0) {
+            e = (int64_t)lookback(a.state, tile, 1, &a.hdr->status);
+            lb_store(a.state + tile, kFlagIncl | (uint64_t)(e + tot));
+        }
+        s_excl = e;
+        if (tile == ntiles - 1) a.hdr->nnz_c = e + tot;
+    }
+    __syncthreads();
+    int64_t o = s_excl + ex;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t e = base + i;
+        if (e < n && (e == 0 || a.key[e] != a.key[e - 1])) {
+            double s = a.val[e];
+            for (int64_t t = e + 1; t < n && a.key[t] == a.key[e]; ++t) s += a.val[t];
+            a.c_liv[o] = a.key[e];
+            a.c_val[o] = s;
+            ++o;
+        }
+    }
+}
+
+__global__ void k_set_empty(WsHeader *hdr, int32_t alg) {
+    hdr->alg = alg;
+    hdr->f = 0;
+    hdr->work_total = 0;
+    hdr->nchunks = 0;
+    hdr->nnz_c = 0;
+    hdr->nzr_b = 0;
+}
+
+int sm_count() { return radix_sm_count(); }
+
+int bits_host(uint64_t range) {
+    int b = 0;
+    while (b < 63 && (1ull << b) < range) ++b;
+    return b;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Plan
+// ---------------------------------------------------------------------------
+}  // namespace lco
+
+struct lco_plan {
+    lco::RpPlan rp_l, rp_r;      // L and R rearrangements (source shapes -> matrix orders)
+    lco_shape src_l, src_r;      // shapes of the operands feeding L and R
+    int32_t l_is_a;              // 1: L = A (row variants), 0: L = B (column variants)
+    int32_t need_l, need_r;
+    int32_t lookup;              // lco::Lookup
+    int32_t acc;                 // 1 accumulator, 0 no accumulator, 2 SOP
+    int64_t mL, k, nR;
+    int64_t nnz_l, nnz_r;
+    int32_t colbits;
+    int32_t aux_shift;
+    int64_t naux;
+    int32_t sop_bits;
+    lco_plan_info info;
+    // workspace layout (offsets from ws)
+    size_t off_l_liv, off_l_val, off_r_liv, off_r_val, off_rp;
+    size_t off_p1state, p1state_bytes;
+    size_t off_mdt_rowptr, off_mdt_rowid, off_mdt_aux;
+    size_t off_P;
+    size_t phase1_end;
+};
+
+namespace lco {
+namespace {
+
+int sparsity_class(int64_t rows, int64_t cols, int64_t nnz) {
+    if (nnz <= 0) return 3;
+    const bool rs = (double)rows / (double)nnz > 3.0;
+    const bool cs = (double)cols / (double)nnz > 3.0;
+    return rs && cs ? 3 : (rs ? 1 : (cs ? 2 : 0));
+}
+
+// Table 4 (rows: A class, columns: B class; order sparse, row-, column-, index-sparse).
+// Values >= 10 mark cells naming a column/row pair.
+const int kTable4[4][4] = {
+    {10, LCO_ALG_CSC, LCO_ALG_CSC, LCO_ALG_CSC},
+    {LCO_ALG_CSR, LCO_ALG_DCSR, 12, LCO_ALG_CSCNA},
+    {LCO_ALG_CSR, 11, LCO_ALG_DCSC, LCO_ALG_DCSC},
+    {LCO_ALG_CSR, LCO_ALG_DCSR, LCO_ALG_CSRNA, LCO_ALG_SOP},
+};
+
+bool same_sig(int order, const int32_t *a, const int32_t *b) {
+    for (int i = 0; i < order; ++i)
+        if (a[i] != b[i]) return false;
+    return true;
+}
+
+// Phase-2 workspace layout (offsets from the end of the phase-1 region).
+struct P2Layout {
+    int64_t capc, nchunks_max;
+    size_t chunk_state, chunk_ctr, reduce_state, zero_bytes;
+    size_t arr[6];          // cap-sized scratch arrays (8 bytes per entry)
+    size_t sop_radix;
+    int sop_D, sop_P;
+    size_t total;
+};
+
+P2Layout p2_layout(const lco_plan *p, int64_t cap);
+
+size_t contract_phase2_bytes(const lco_plan *p, int64_t cap) { return p2_layout(p, cap).total; }
+
+}  // namespace
+}  // namespace lco
+
+using namespace lco;
+
+extern "C" {
+
+int32_t lco_contract_plan(const lco_shape *a, const lco_shape *b, int32_t ncontract, const int32_t *modes_a,
+                          const int32_t *modes_b, int32_t force_alg, lco_plan **plan_out) {
+    if (!plan_out) return LCO_ERR_INVALID;
+    *plan_out = nullptr;
+    int64_t ta, tb;
+    int32_t rc;
+    if ((rc = check_shape(a, &ta)) != LCO_OK) return rc;
+    if ((rc = check_shape(b, &tb)) != LCO_OK) return rc;
+    if (ncontract < 0 || ncontract > a->order || ncontract > b->order) return LCO_ERR_INVALID;
+    if (ncontract > 0 && (!modes_a || !modes_b)) return LCO_ERR_INVALID;
+    if (force_alg < -1 || force_alg > LCO_ALG_SOP) return LCO_ERR_INVALID;
+    int con_a[kMaxOrder] = {0}, con_b[kMaxOrder] = {0};
+    for (int i = 0; i < ncontract; ++i) {
+        const int ma = modes_a[i], mb = modes_b[i];
+        if (ma < 0 || ma >= a->order || mb < 0 || mb >= b->order) return LCO_ERR_INVALID;
+        if (con_a[ma] || con_b[mb]) return LCO_ERR_INVALID;
+        if (a->dims[ma] != b->dims[mb]) return LCO_ERR_INVALID;
+        con_a[ma] = con_b[mb] = 1;
+    }
+    int free_a[kMaxOrder], free_b[kMaxOrder], nfa = 0, nfb = 0;
+    for (int t = 0; t < a->order; ++t) if (!con_a[t]) free_a[nfa++] = t;
+    for (int t = 0; t < b->order; ++t) if (!con_b[t]) free_b[nfb++] = t;
+    if (nfa + nfb > kMaxOrder) return LCO_ERR_INVALID;
+    int64_t m = 1, k = 1, n = 1;
+    for (int i = 0; i < nfa; ++i) m *= a->dims[free_a[i]];
+    for (int i = 0; i < ncontract; ++i) k *= a->dims[modes_a[i]];
+    for (int i = 0; i < nfb; ++i) n *= b->dims[free_b[i]];
+    if (m > INT64_MAX / n) return LCO_ERR_OVERFLOW;
+
+    // matrix orders (most significant first), converted to sig (least significant first)
+    int32_t a_row[kMaxOrder], a_col[kMaxOrder], b_row[kMaxOrder], b_col[kMaxOrder];
+    {
+        int32_t msf[kMaxOrder];
+        int q = 0;
+        for (int i = 0; i < nfa; ++i) msf[q++] = free_a[i];
+        for (int i = 0; i < ncontract; ++i) msf[q++] = modes_a[i];
+        for (int i = 0; i < q; ++i) a_row[i] = msf[q - 1 - i];
+        q = 0;
+        for (int i = 0; i < ncontract; ++i) msf[q++] = modes_a[i];
+        for (int i = 0; i < nfa; ++i) msf[q++] = free_a[i];
+        for (int i = 0; i < q; ++i) a_col[i] = msf[q - 1 - i];
+        q = 0;
+        for (int i = 0; i < ncontract; ++i) msf[q++] = modes_b[i];
+        for (int i = 0; i < nfb; ++i) msf[q++] = free_b[i];
+        for (int i = 0; i < q; ++i) b_row[i] = msf[q - 1 - i];
+        q = 0;
+        for (int i = 0; i < nfb; ++i) msf[q++] = free_b[i];
+        for (int i = 0; i < ncontract; ++i) msf[q++] = modes_b[i];
+        for (int i = 0; i < q; ++i) b_col[i] = msf[q - 1 - i];
+    }
+    const int perm_row = !same_sig(a->order, a->sig, a_row) + !same_sig(b->order, b->sig, b_row);
+    const int perm_col = !same_sig(a->order, a->sig, a_col) + !same_sig(b->order, b->sig, b_col);
+    const int ca = sparsity_class(m, k, a->nnz), cb = sparsity_class(k, n, b->nnz);
+    int alg = force_alg;
+    if (alg < 0) {
+        const int cell = kTable4[ca][cb];
+        if (cell < 10) {
+            alg = cell;
+        } else {
+            const bool colv = perm_col < perm_row ? true : (perm_row < perm_col ? false : n > m);
+            alg = cell == 10 ? (colv ? LCO_ALG_CSC : LCO_ALG_CSR)
+                : cell == 11 ? (colv ? LCO_ALG_DCSC : LCO_ALG_DCSR)
+                             : (colv ? LCO_ALG_CSCNA : LCO_ALG_CSRNA);
+        }
+    }
+    const bool transposed = alg == LCO_ALG_CSC || alg == LCO_ALG_DCSC || alg == LCO_ALG_CSCNA;
+
+    lco_plan *p = new (std::nothrow) lco_plan();
+    if (!p) return LCO_ERR_OOM;
+    std::memset(p, 0, sizeof(*p));
+    p->l_is_a = !transposed;
+    p->src_l = transposed ? *b : *a;
+    p->src_r = transposed ? *a : *b;
+    const int32_t *l_target = transposed ? b_col : a_row;
+    const int32_t *r_target = transposed ? a_col : b_row;
+    if ((rc = rp_plan(&p->src_l, l_target, &p->rp_l)) != LCO_OK) { delete p; return rc; }
+    if ((rc = rp_plan(&p->src_r, r_target, &p->rp_r)) != LCO_OK) { delete p; return rc; }
+    p->need_l = !same_sig(p->src_l.order, p->src_l.sig, l_target);
+    p->need_r = !same_sig(p->src_r.order, p->src_r.sig, r_target);
+    p->mL = transposed ? n : m;
+    p->nR = transposed ? m : n;
+    p->k = k;
+    p->nnz_l = p->src_l.nnz;
+    p->nnz_r = p->src_r.nnz;
+    p->colbits = bits_host((uint64_t)p->nR);
+    p->acc = (alg == LCO_ALG_SOP) ? 2 : ((alg == LCO_ALG_CSRNA || alg == LCO_ALG_CSCNA) ? 0 : 1);
+    p->lookup = (alg == LCO_ALG_DCSR || alg == LCO_ALG_DCSC || alg == LCO_ALG_SOP) ? kLookupDcsr : kLookupCsr;
+    // keys of the chunk kernel pack (local row < 2^11, column): wide columns go to SOP
+    if (p->acc != 2 && p->colbits > 52) {
+        p->acc = 2;
+        p->lookup = kLookupDcsr;
+    }
+    p->sop_bits = bits_host((uint64_t)p->mL * (uint64_t)p->nR);
+    {
+        uint64_t na = 1;
+        while (na < (uint64_t)(p->nnz_r > 0 ? p->nnz_r : 1)) na <<= 1;
+        const int kb = bits_host((uint64_t)k);
+        const int nb = bits_host(na);
+        p->aux_shift = kb > nb ? kb - nb : 0;
+        p->naux = (int64_t)(((uint64_t)(k - 1) >> p->aux_shift) + 1);
+    }
+    // info
+    p->info.alg = alg;
+    p->info.transposed = transposed;
+    p->info.class_a = ca;
+    p->info.class_b = cb;
+    p->info.permute_a = transposed ? p->need_r : p->need_l;
+    p->info.permute_b = transposed ? p->need_l : p->need_r;
+    p->info.m = m;
+    p->info.k = k;
+    p->info.n = n;
+    {
+        lco_shape &cs = p->info.c_shape;
+        cs.order = nfa + nfb;
+        int q = 0;
+        for (int i = 0; i < nfa; ++i) cs.dims[q++] = a->dims[free_a[i]];
+        for (int i = 0; i < nfb; ++i) cs.dims[q++] = b->dims[free_b[i]];
+        if (cs.order == 0) {
+            cs.order = 1;
+            cs.dims[0] = 1;
+            cs.sig[0] = 0;
+        } else if (!transposed) {
+            for (int i = 0; i < cs.order; ++i) cs.sig[i] = cs.order - 1 - i;
+        } else {
+            // most significant first: B's free modes (nfa..), then A's free modes (0..nfa-1)
+            int32_t msf[kMaxOrder];
+            int t = 0;
+            for (int i = 0; i < nfb; ++i) msf[t++] = nfa + i;
+            for (int i = 0; i < nfa; ++i) msf[t++] = i;
+            for (int i = 0; i < cs.order; ++i) cs.sig[i] = msf[cs.order - 1 - i];
+        }
+        cs.nnz = 0;
+    }
+    // workspace layout, phase 1
+    size_t off = kWsHeaderBytes;
+    auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes ? bytes : 1); return o; };
+    const int64_t nl = p->nnz_l > 0 ? p->nnz_l : 1, nr = p->nnz_r > 0 ? p->nnz_r : 1;
+    p->off_l_liv = p->need_l ? take((size_t)nl * 8) : 0;
+    p->off_l_val = p->need_l ? take((size_t)nl * 8) : 0;
+    p->off_r_liv = p->need_r ? take((size_t)nr * 8) : 0;
+    p->off_r_val = p->need_r ? take((size_t)nr * 8) : 0;
+    {
+        size_t rb = 0;
+        if (p->need_l) rb = rp_region_bytes(p->rp_l, p->nnz_l);
+        if (p->need_r) { size_t x = rp_region_bytes(p->rp_r, p->nnz_r); if (x > rb) rb = x; }
+        p->off_rp = take(rb);
+    }
+    const size_t scan_tiles = (size_t)((nl + kScanTile - 1) / kScanTile) + 1;
+    const size_t dcsr_tiles = (size_t)((nr + kScanTile - 1) / kScanTile) + 1;
+    p->off_p1state = take((scan_tiles + dcsr_tiles) * 8);
+    p->p1state_bytes = align_up((scan_tiles + dcsr_tiles) * 8);
+    if (p->lookup == kLookupCsr) {
+        p->off_mdt_rowptr = take((size_t)(k + 1) * 8);
+    } else {
+        p->off_mdt_rowptr = take((size_t)(nr + 1) * 8);
+        p->off_mdt_rowid = take((size_t)nr * 8);
+        p->off_mdt_aux = take((size_t)(p->naux + 1) * 8);
+    }
+    p->off_P = take((size_t)(nl + 1) * 8);
+    p->phase1_end = off;
+    *plan_out = p;
+    return LCO_OK;
+}
+
+int32_t lco_plan_get_info(const lco_plan *plan, lco_plan_info *info) {
+    if (!plan || !info) return LCO_ERR_INVALID;
+    *info = plan->info;
+    return LCO_OK;
+}
+
+int32_t lco_plan_destroy(lco_plan *plan) {
+    delete plan;
+    return LCO_OK;
+}
+
+int32_t lco_contract_workspace(const lco_plan *plan, int64_t cap, size_t *ws_bytes) {
+    if (!plan || !ws_bytes || cap < 0) return LCO_ERR_INVALID;
+    *ws_bytes = plan->phase1_end + contract_phase2_bytes(plan, cap);
+    return LCO_OK;
+}
+
+}  // extern "C"
+
+namespace lco {
+namespace {
+
+struct Operands {
+    const int64_t *l_liv;
+    const double *l_val;
+    const int64_t *r_liv;
+    const double *r_val;
+};
+
+Operands operands(const lco_plan *p, const int64_t *a_liv, const double *a_val, const int64_t *b_liv,
+                  const double *b_val, char *ws) {
+    Operands o;
+    const int64_t *src_l_liv = p->l_is_a ? a_liv : b_liv;
+    const double *src_l_val = p->l_is_a ? a_val : b_val;
+    const int64_t *src_r_liv = p->l_is_a ? b_liv : a_liv;
+    const double *src_r_val = p->l_is_a ? b_val : a_val;
+    o.l_liv = p->need_l ? reinterpret_cast<int64_t *>(ws + p->off_l_liv) : src_l_liv;
+    o.l_val = p->need_l ? reinterpret_cast<double *>(ws + p->off_l_val) : src_l_val;
+    o.r_liv = p->need_r ? reinterpret_cast<int64_t *>(ws + p->off_r_liv) : src_r_liv;
+    o.r_val = p->need_r ? reinterpret_cast<double *>(ws + p->off_r_val) : src_r_val;
+    return o;
+}
+
+Mdt make_mdt(const lco_plan *p, char *ws) {
+    Mdt m{};
+    m.kind = p->lookup;
+    m.k = p->k;
+    m.nnz = p->nnz_r;
+    m.row_ptr = reinterpret_cast<int64_t *>(ws + p->off_mdt_rowptr);
+    if (p->lookup == kLookupDcsr) {
+        m.row_id = reinterpret_cast<int64_t *>(ws + p->off_mdt_rowid);
+        m.aux = reinterpret_cast<int64_t *>(ws + p->off_mdt_aux);
+        m.aux_shift = p->aux_shift;
+        m.naux = p->naux;
+    }
+    return m;
+}
+
+bool check_ptrs(const lco_plan *p, const int64_t *a_liv, const double *a_val, const int64_t *b_liv,
+                const double *b_val) {
+    const int64_t na = p->l_is_a ? p->nnz_l : p->nnz_r;
+    const int64_t nb = p->l_is_a ? p->nnz_r : p->nnz_l;
+    if (na > 0 && (!a_liv || !a_val)) return false;
+    if (nb > 0 && (!b_liv || !b_val)) return false;
+    return true;
+}
+
+int32_t symbolic_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a_val, const int64_t *b_liv,
+                         const double *b_val, char *ws, cudaStream_t s) {
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
+    // reset header (status, results, counters) and the phase-1 look-back state
+    if (cudaMemsetAsync(ws, 0, kWsHeaderBytes, s) != cudaSuccess) return LCO_ERR_CUDA;
+    if (cudaMemsetAsync(ws + p->off_p1state, 0, p->p1state_bytes, s) != cudaSuccess) return LCO_ERR_CUDA;
+    if (p->nnz_l == 0 || p->nnz_r == 0) {
+        LCO_LAUNCH("k_set_empty", s, k_set_empty<<<1, 1, 0, s>>>(hdr, p->info.alg));
+        return cudaGetLastError() == cudaSuccess ? LCO_OK : LCO_ERR_CUDA;
+    }
+    const int64_t *src_l_liv = p->l_is_a ? a_liv : b_liv;
+    const double *src_l_val = p->l_is_a ? a_val : b_val;
+    const int64_t *src_r_liv = p->l_is_a ? b_liv : a_liv;
+    const double *src_r_val = p->l_is_a ? b_val : a_val;
+    Operands o = operands(p, a_liv, a_val, b_liv, b_val, ws);
+    char *rp_region = ws + p->off_rp;
+    if (p->need_l) {
+        if (rp_enqueue(p->rp_l, p->nnz_l, src_l_liv, src_l_val, const_cast<int64_t *>(o.l_liv),
+                       const_cast<double *>(o.l_val), rp_region, hdr, s) != cudaSuccess)
+            return LCO_ERR_CUDA;
+    }
+    if (p->need_r) {
+        if (rp_enqueue(p->rp_r, p->nnz_r, src_r_liv, src_r_val, const_cast<int64_t *>(o.r_liv),
+                       const_cast<double *>(o.r_val), rp_region, hdr, s) != cudaSuccess)
+            return LCO_ERR_CUDA;
+    }
+    const int sms = sm_count();
+    Mdt mdt = make_mdt(p, ws);
+    const DivU64 div_n = make_div((uint64_t)p->nR);
+    uint64_t *scan_state = reinterpret_cast<uint64_t *>(ws + p->off_p1state);
+    uint64_t *dcsr_state = scan_state + ((p->nnz_l + kScanTile - 1) / kScanTile) + 1;
+    if (p->lookup == kLookupCsr) {
+        int64_t grid = (std::max<int64_t>(p->nnz_r, p->k + 1) + 255) / 256;
+        if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
+        LCO_LAUNCH("k_csr_rowptr", s, k_csr_rowptr<<<(unsigned)grid, 256, 0, s>>>(o.r_liv, p->nnz_r, div_n, p->k,
+                                                    const_cast<int64_t *>(mdt.row_ptr)));
+    } else {
+        DcsrArgs d{};
+        d.liv = o.r_liv;
+        d.nnz = p->nnz_r;
+        d.div_n = div_n;
+        d.row_id = const_cast<int64_t *>(mdt.row_id);
+        d.row_ptr = const_cast<int64_t *>(mdt.row_ptr);
+        d.state = dcsr_state;
+        d.hdr = hdr;
+        const int64_t tiles = (p->nnz_r + kScanTile - 1) / kScanTile;
+        LCO_LAUNCH("k_dcsr_build", s, k_dcsr_build<<<(unsigned)tiles, kCT, 0, s>>>(d));
+        int64_t grid = (p->nnz_r + 1 + 255) / 256;
+        if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
+        LCO_LAUNCH("k_dcsr_aux", s, k_dcsr_aux<<<(unsigned)grid, 256, 0, s>>>(mdt.row_id, hdr, p->aux_shift, p->naux,
+                                                  const_cast<int64_t *>(mdt.aux), p->nnz_r));
+    }
+    ScanArgs sa{};
+    sa.alg = p->info.alg;
+    sa.l_liv = o.l_liv;
+    sa.nnz_l = p->nnz_l;
+    sa.div_k = make_div((uint64_t)p->k);
+    sa.k = p->k;
+    sa.mdt = mdt;
+    sa.P = reinterpret_cast<int64_t *>(ws + p->off_P);
+    sa.state = scan_state;
+    sa.hdr = hdr;
+    const int64_t tiles = (p->nnz_l + kScanTile - 1) / kScanTile;
+    LCO_LAUNCH("k_work_scan", s, k_work_scan<<<(unsigned)tiles, kCT, 0, s>>>(sa));
+    return cudaGetLastError() == cudaSuccess ? LCO_OK : LCO_ERR_CUDA;
+}
+
+int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a_val, const int64_t *b_liv,
+                        const double *b_val, int64_t *c_liv, double *c_val, int64_t cap, char *ws,
+                        cudaStream_t s) {
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
+    if (p->nnz_l == 0 || p->nnz_r == 0) {
+        LCO_LAUNCH("k_set_empty", s, k_set_empty<<<1, 1, 0, s>>>(hdr, p->info.alg));
+        return cudaGetLastError() == cudaSuccess ? LCO_OK : LCO_ERR_CUDA;
+    }
+    Operands o = operands(p, a_liv, a_val, b_liv, b_val, ws);
+    const P2Layout L = p2_layout(p, cap);
+    const int64_t capc = L.capc;
+    const int64_t nchunks_max = L.nchunks_max;
+    char *p2 = ws + p->phase1_end;
+    uint64_t *chunk_state = reinterpret_cast<uint64_t *>(p2 + L.chunk_state);
+    uint32_t *chunk_ctr = reinterpret_cast<uint32_t *>(p2 + L.chunk_ctr);
+    uint64_t *reduce_state = reinterpret_cast<uint64_t *>(p2 + L.reduce_state);
+    uint64_t *sk0 = reinterpret_cast<uint64_t *>(p2 + L.arr[0]);
+    double *sv0 = reinterpret_cast<double *>(p2 + L.arr[1]);
+    uint64_t *sk1 = reinterpret_cast<uint64_t *>(p2 + L.arr[2]);
+    double *sv1 = reinterpret_cast<double *>(p2 + L.arr[3]);
+    uint64_t *sk2 = reinterpret_cast<uint64_t *>(p2 + L.arr[4]);
+    double *sv2 = reinterpret_cast<double *>(p2 + L.arr[5]);
+    char *sop_region = p2 + L.sop_radix;
+    if (cudaMemsetAsync(p2, 0, L.zero_bytes, s) != cudaSuccess) return LCO_ERR_CUDA;
+    Mdt mdt = make_mdt(p, ws);
+    const int sms = sm_count();
+    const int64_t *P = reinterpret_cast<const int64_t *>(ws + p->off_P);
+    if (p->acc != 2) {
+        ChunkArgs ca{};
+        ca.l_liv = o.l_liv;
+        ca.l_val = o.l_val;
+        ca.r_liv = o.r_liv;
+        ca.r_val = o.r_val;
+        ca.nnz_l = p->nnz_l;
+        ca.div_k = make_div((uint64_t)p->k);
+        ca.k = p->k;
+        ca.div_n = make_div((uint64_t)p->nR);
+        ca.nR = p->nR;
+        ca.colbits = p->colbits;
+        ca.acc = p->acc;
+        ca.mdt = mdt;
+        ca.P = P;
+        ca.c_liv = c_liv;
+        ca.c_val = c_val;
+        ca.cap = cap;
+        ca.chunk_state = chunk_state;
+        ca.chunk_ctr = chunk_ctr;
+        ca.sk0 = sk0;
+        ca.sv0 = sv0;
+        ca.sk1 = sk1;
+        ca.sv1 = sv1;
+        ca.hdr = hdr;
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_chunk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ChunkSmem));
+            attr = true;
+        }
+        int64_t grid = nchunks_max < (int64_t)sms ? nchunks_max : (int64_t)sms;
+        LCO_LAUNCH("k_chunk", s, k_chunk<<<(unsigned)grid, kCT, sizeof(ChunkSmem), s>>>(ca));
+    } else {
+        SopArgs sa{};
+        sa.l_liv = o.l_liv;
+        sa.l_val = o.l_val;
+        sa.r_liv = o.r_liv;
+        sa.r_val = o.r_val;
+        sa.nnz_l = p->nnz_l;
+        sa.div_k = make_div((uint64_t)p->k);
+        sa.k = p->k;
+        sa.nR = p->nR;
+        sa.mdt = mdt;
+        sa.P = P;
+        sa.cap = cap;
+        sa.out_liv = reinterpret_cast<int64_t *>(sk0);
+        sa.out_val = sv0;
+        sa.hdr = hdr;
+        int64_t grid = (p->nnz_l + 255) / 256;
+        if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
+        LCO_LAUNCH("k_sop_expand", s, k_sop_expand<<<(unsigned)grid, 256, 0, s>>>(sa));
+        // sort products by output LIV with the radix engine (device-side count f)
+        RadixJob j{};
+        j.relin.nseg = 1;
+        j.relin.identity = 1;
+        j.key_div = make_div(1);
+        j.D = L.sop_D;
+        j.P = L.sop_P;
+        j.n_host = 0;
+        j.n_dev = &hdr->f;
+        j.n_cap = capc;
+        j.src_liv = reinterpret_cast<int64_t *>(sk0);
+        j.src_val = sv0;
+        j.dst_liv = reinterpret_cast<int64_t *>(sk1);
+        j.dst_val = sv1;
+        j.tmp_liv = reinterpret_cast<int64_t *>(sk2);
+        j.tmp_val = sv2;
+        radix_carve(j, sop_region);
+        j.counters = hdr->counters;
+        j.status = &hdr->status;
+        if (radix_enqueue(j, s) != cudaSuccess) return LCO_ERR_CUDA;
+        ReduceArgs ra{};
+        ra.key = reinterpret_cast<int64_t *>(sk1);
+        ra.val = sv1;
+        ra.cap = cap;
+        ra.c_liv = c_liv;
+        ra.c_val = c_val;
+        ra.state = reduce_state;
+        ra.ctr = chunk_ctr + 1;
+        ra.hdr = hdr;
+        const int64_t tiles = (capc + kScanTile - 1) / kScanTile;
+        LCO_LAUNCH("k_reduce_by_key", s, k_reduce_by_key<<<(unsigned)(tiles > 0 ? tiles : 1), kCT, 0, s>>>(ra));
+    }
+    return cudaGetLastError() == cudaSuccess ? LCO_OK : LCO_ERR_CUDA;
+}
+
+P2Layout p2_layout(const lco_plan *p, int64_t cap) {
+    P2Layout L{};
+    L.capc = cap > 0 ? cap : 1;
+    L.nchunks_max = (p->nnz_l + L.capc + kChunkWork - 1) / kChunkWork + 2;
+    size_t off = 0;
+    L.chunk_state = off;
+    L.chunk_ctr = (size_t)L.nchunks_max * 8;
+    off += align_up((size_t)L.nchunks_max * 8 + 64);
+    L.reduce_state = off;
+    off += align_up((size_t)((L.capc + kScanTile - 1) / kScanTile + 2) * 8);
+    L.zero_bytes = off;
+    for (int i = 0; i < 6; ++i) {
+        L.arr[i] = off;
+        off += align_up((size_t)L.capc * 8);
+    }
+    L.sop_radix = off;
+    radix_digits(p->sop_bits, &L.sop_D, &L.sop_P);
+    if (p->acc == 2) off += radix_state_bytes(L.capc, L.sop_D, L.sop_P);
+    L.total = off;
+    return L;
+}
+
+int32_t check_ws(const lco_plan *p, void *ws, size_t ws_bytes, int64_t cap) {
+    if (!ws) return LCO_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return LCO_ERR_INVALID;
+    size_t need = p->phase1_end + (cap >= 0 ? contract_phase2_bytes(p, cap) : 0);
+    if (ws_bytes < need) return LCO_ERR_OOM;
+    return LCO_OK;
+}
+
+}  // namespace
+}  // namespace lco
+
+extern "C" {
+
+int32_t lco_contract_symbolic(const lco_plan *plan, const int64_t *a_liv, const double *a_val,
+                              const int64_t *b_liv, const double *b_val, void *ws, size_t ws_bytes,
+                              void *stream) {
+    if (!plan) return LCO_ERR_INVALID;
+    int32_t rc = check_ws(plan, ws, ws_bytes, -1);
+    if (rc != LCO_OK) return rc;
+    if (!check_ptrs(plan, a_liv, a_val, b_liv, b_val)) return LCO_ERR_INVALID;
+    return symbolic_enqueue(plan, a_liv, a_val, b_liv, b_val, reinterpret_cast<char *>(ws),
+                            (cudaStream_t)stream);
+}
+
+int32_t lco_contract_numeric(const lco_plan *plan, const int64_t *a_liv, const double *a_val,
+                             const int64_t *b_liv, const double *b_val, int64_t *c_liv, double *c_val,
+                             int64_t cap, void *ws, size_t ws_bytes, void *stream) {
+    if (!plan || cap < 0) return LCO_ERR_INVALID;
+    int32_t rc = check_ws(plan, ws, ws_bytes, cap);
+    if (rc != LCO_OK) return rc;
+    if (!check_ptrs(plan, a_liv, a_val, b_liv, b_val)) return LCO_ERR_INVALID;
+    if (cap > 0 && (!c_liv || !c_val)) return LCO_ERR_INVALID;
+    return numeric_enqueue(plan, a_liv, a_val, b_liv, b_val, c_liv, c_val, cap, reinterpret_cast<char *>(ws),
+                           (cudaStream_t)stream);
+}
+
+int32_t lco_contract(const lco_plan *plan, const int64_t *a_liv, const double *a_val, const int64_t *b_liv,
+                     const double *b_val, int64_t *c_liv, double *c_val, int64_t cap, void *ws, size_t ws_bytes,
+                     void *stream) {
+    int32_t rc = lco_contract_symbolic(plan, a_liv, a_val, b_liv, b_val, ws, ws_bytes, stream);
+    if (rc != LCO_OK) return rc;
+    return lco_contract_numeric(plan, a_liv, a_val, b_liv, b_val, c_liv, c_val, cap, ws, ws_bytes, stream);
+}
+
+int32_t lco_contract_result_get(const void *ws, lco_contract_result *out, void *stream) {
+    if (!ws || !out) return LCO_ERR_INVALID;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return LCO_ERR_CUDA;
+    WsHeader h;
+    if (cudaMemcpy(&h, ws, sizeof(WsHeader), cudaMemcpyDeviceToHost) != cudaSuccess) return LCO_ERR_CUDA;
+    out->status = h.status;
+    out->alg = h.alg;
+    out->nnz_c = h.nnz_c;
+    out->f = h.f;
+    out->nzr_b = h.nzr_b;
+    return LCO_OK;
+}
+
+}  // extern "C"

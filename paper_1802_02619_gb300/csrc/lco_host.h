@@ -1,0 +1,42 @@
+// lco_host.h -- host-side planning shared by the permutation and contraction entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lco_internal.cuh"
+#include "lco_radix.cuh"
+
+namespace lco {
+
+int32_t check_sig(int32_t order, const int32_t *sig);
+// Validates order, sig and dims; *total receives the product of the dims.
+int32_t check_shape(const lco_shape *t, int64_t *total);
+
+// How a permutation of one tensor is carried out (Sec. 4.1).
+struct RpPlan {
+    lco_rp_info info;
+    RelinParams relin;   // old LIV -> new LIV
+    DivU64 key_div;      // key = newLIV div m_low
+    int64_t total;       // product of dims
+    int32_t identity;    // new order equals old order
+};
+
+int32_t rp_plan(const lco_shape *t, const int32_t *new_sig, RpPlan *out);
+// Bytes the radix engine needs for this plan on nnz elements (state + tmp buffers),
+// excluding the workspace header.
+size_t rp_region_bytes(const RpPlan &plan, int64_t nnz);
+// Enqueues the permutation.  `region` holds rp_region_bytes bytes; `hdr` is
+// the workspace header whose counters and status word the kernels use.
+cudaError_t rp_enqueue(const RpPlan &plan, int64_t nnz, const int64_t *in_liv, const double *in_val,
+                       int64_t *out_liv, double *out_val, char *region, WsHeader *hdr,
+                       cudaStream_t stream);
+
+// Re-linearisation parameters from old to new order (modes merged into
+// segments when they stay adjacent and in the same relative order).
+RelinParams make_relin(int32_t order, const int64_t *dims, const int32_t *sig_old,
+                       const int32_t *sig_new);
+
+cudaError_t relin_enqueue(const RelinParams &p, int64_t n, const int64_t *in, int64_t *out,
+                          cudaStream_t stream);
+
+}  // namespace lco

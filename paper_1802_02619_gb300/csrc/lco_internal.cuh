@@ -1,0 +1,177 @@
+// lco_internal.cuh -- device helpers shared by the LCO kernels (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lco.h"
+
+namespace lco {
+
+constexpr int kMaxOrder = LCO_MAX_ORDER;
+constexpr int kWsHeaderBytes = 256;
+// Bounded device waits: a look-back spin gives up after this many SM clock
+// cycles (about one second at 2 GHz), records LCO_ERR_TIMEOUT and continues
+// with a zero contribution so that the kernel always terminates.
+constexpr long long kSpinBudgetCycles = 2000000000LL;
+
+// ---------------------------------------------------------------------------
+// Unsigned 64-bit division by an invariant divisor.
+//
+// Granlund & Montgomery, "Division by invariant integers using
+// multiplication" (PLDI 1994), Fig. 4.1: for a divisor d >= 1 let
+// l = ceil(log2 d) and m' = floor(2^64 (2^l - d) / d) + 1; then for every
+// 64-bit n, q = (t1 + ((n - t1) >> 1)) >> (l - 1) with t1 = mulhi(m', n).
+// Powers of two use a plain shift.
+// ---------------------------------------------------------------------------
+struct DivU64 {
+    uint64_t d;
+    uint64_t m;
+    uint32_t shift;
+    uint32_t pow2;
+};
+
+inline DivU64 make_div(uint64_t d) {
+    DivU64 v{};
+    v.d = d;
+    if ((d & (d - 1)) == 0) {
+        v.pow2 = 1;
+        v.shift = (uint32_t)__builtin_ctzll(d);
+        v.m = 0;
+        return v;
+    }
+    uint32_t l = 64u - (uint32_t)__builtin_clzll(d - 1);   // ceil(log2 d), 2 <= l <= 63
+    unsigned __int128 num = ((unsigned __int128)((1ull << l) - d)) << 64;
+    v.m = (uint64_t)(num / d) + 1u;
+    v.shift = l - 1;
+    v.pow2 = 0;
+    return v;
+}
+
+__host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+__host__ __device__ __forceinline__ uint64_t divu(const DivU64 &v, uint64_t n) {
+    if (v.pow2) return n >> v.shift;
+    uint64_t t1 = mulhi64(v.m, n);
+    return (t1 + ((n - t1) >> 1)) >> v.shift;
+}
+
+// ---------------------------------------------------------------------------
+// Re-linearisation (Sec. 3.1 "LIV shuffle").  Modes that are adjacent and in
+// the same relative order in both the old and the new order are merged into
+// one "segment" on the host, so an order-N shuffle costs (segments - 1)
+// divisions.  Segments are listed in old significance order (least
+// significant first); seg_div[t] is the range of segment t and seg_stride[t]
+// its stride in the new LIV.
+// ---------------------------------------------------------------------------
+struct RelinParams {
+    int32_t nseg;
+    int32_t identity;
+    DivU64 seg_div[kMaxOrder];
+    int64_t seg_stride[kMaxOrder];
+};
+
+__host__ __device__ __forceinline__ int64_t relin(const RelinParams &p, int64_t liv) {
+    if (p.identity) return liv;
+    uint64_t r = (uint64_t)liv;
+    int64_t out = 0;
+#pragma unroll 1
+    for (int t = 0; t < p.nseg - 1; ++t) {
+        uint64_t q = divu(p.seg_div[t], r);
+        uint64_t c = r - q * p.seg_div[t].d;
+        out += (int64_t)c * p.seg_stride[t];
+        r = q;
+    }
+    out += (int64_t)r * p.seg_stride[p.nseg - 1];
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace header (first 256 bytes of every workspace).
+// ---------------------------------------------------------------------------
+struct WsHeader {
+    int32_t status;      // first device error (0 = none)
+    int32_t alg;
+    int64_t nnz_c;
+    int64_t f;
+    int64_t nzr_b;
+    int64_t nchunks;
+    int64_t work_total;
+    uint32_t counters[32];   // tile/chunk counters and "last block" counters
+};
+static_assert(sizeof(WsHeader) <= kWsHeaderBytes, "header too large");
+
+__device__ __forceinline__ void set_error(int32_t *status, int32_t err) {
+    atomicCAS(status, 0, err);
+}
+
+// ---------------------------------------------------------------------------
+// Decoupled look-back state words: [flag:2 | value:62].
+// flag 0 = not yet published, 1 = aggregate of the tile only, 2 = inclusive
+// prefix through the tile.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagIncl = 2ull << 62;
+constexpr uint64_t kValueMask = (1ull << 62) - 1;
+
+__device__ __forceinline__ void lb_store(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t lb_load(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Exclusive prefix of the tiles before `tile` for one counter column; `state`
+// is laid out [tile][stride].  Waits (bounded) for predecessors to publish.
+__device__ __forceinline__ uint64_t lookback(const uint64_t *state, int64_t tile, int64_t stride,
+                                             int32_t *status) {
+    uint64_t excl = 0;
+    long long t0 = clock64();
+    for (int64_t t = tile - 1; t >= 0; --t) {
+        uint64_t s = lb_load(state + t * stride);
+        while ((s >> 62) == 0) {
+            if (clock64() - t0 > kSpinBudgetCycles) {
+                set_error(status, LCO_ERR_TIMEOUT);
+                return excl;
+            }
+            s = lb_load(state + t * stride);
+        }
+        excl += s & kValueMask;
+        if ((s >> 62) == 2) break;
+    }
+    return excl;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// Kernel timing / launch counting (implemented in lco_api.cu).
+void timing_begin(const char *name, cudaStream_t s);
+void timing_end(cudaStream_t s);
+
+}  // namespace lco
+
+// Launch a kernel through the timing hooks: LCO_LAUNCH("name", stream, kernel<<<g, b, sm, stream>>>(args));
+#define LCO_LAUNCH(name, stream, ...)        \
+    do {                                     \
+        ::lco::timing_begin((name), (stream)); \
+        __VA_ARGS__;                         \
+        ::lco::timing_end((stream));         \
+    } while (0)
+
+namespace lco {
+
+}  // namespace lco

@@ -1,0 +1,67 @@
+// lco_radix.cuh -- stable LSD radix engine over (int64 LIV, double value) pairs.
+//
+// Used for the permutation of Sec. 4 (keys are re-linearised LIVs shaved by
+// the resting suffix, Sec. 4.1) and for sorting product lists by output LIV
+// (SOP, Sec. 5.2.5).  One launch computes every digit histogram in a single
+// read; each following launch is one stable scatter pass.  Tiles are ranked
+// with warp ballots (a multi-split) and placed with decoupled look-back
+// (Merrill & Garland 2016; the single-pass "Onesweep" arrangement of Adinets
+// & Merrill 2022).  Passes whose digit is the same for every element are
+// detected on the device and skipped.
+#pragma once
+
+#include "lco_internal.cuh"
+
+namespace lco {
+
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 16;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;
+constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr int kMaxDigitBits = 11;
+constexpr int kMaxPasses = 6;
+constexpr int kUpsweepCtasPerSm = 4;
+
+struct RadixJob {
+    RelinParams relin;     // applied to source keys on first read (identity allowed)
+    DivU64 key_div;        // key = relin(liv) div key_div
+    int32_t D;             // digit bits
+    int32_t P;             // passes
+    int64_t n_host;        // element count, or
+    const int64_t *n_dev;  // device element count (overrides n_host when set)
+    int64_t n_cap;         // upper bound on the element count (sizes grids and state)
+    const int64_t *src_liv;
+    const double *src_val;
+    int64_t *dst_liv;
+    double *dst_val;
+    int64_t *tmp_liv;
+    double *tmp_val;
+    // workspace pieces
+    uint64_t *ghist;       // [P][NB]
+    uint64_t *offs;        // [P][NB]
+    int32_t *active;       // [kMaxPasses] + count at [16]
+    uint64_t *state;       // [P][tiles][NB]
+    uint32_t *counters;    // [kMaxPasses] tile counters + [8] done counter
+    int32_t *status;
+};
+
+// Digit plan for a key range of `key_bits` bits.
+inline void radix_digits(int key_bits, int *D, int *P) {
+    if (key_bits <= 0) { *D = 1; *P = 1; return; }
+    int p = (key_bits + kMaxDigitBits - 1) / kMaxDigitBits;
+    int d = (key_bits + p - 1) / p;
+    *D = d;
+    *P = p;
+}
+
+// Bytes of workspace the engine needs for up to n_cap elements (excluding the
+// header and excluding the tmp buffers when those are supplied elsewhere).
+size_t radix_state_bytes(int64_t n_cap, int D, int P);
+// Lays the engine's pieces out in `region` (which must hold
+// radix_state_bytes bytes); counters/status live in the caller's header.
+void radix_carve(RadixJob &job, char *region);
+// Enqueues the histogram launch and P scatter launches.
+cudaError_t radix_enqueue(const RadixJob &job, cudaStream_t stream);
+int radix_sm_count();
+
+}  // namespace lco

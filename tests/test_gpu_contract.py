@@ -1,0 +1,176 @@
+"""GPU parity of the contraction (every poly-algorithm branch) against the
+oracle: index patterns bit-exact, FP64 values within 1e-13 * sum |a||b|."""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1802_02619_gb300 as lco
+import synth
+from gpu_util import assert_contract_matches, dev, host
+
+pytestmark = pytest.mark.gpu
+
+ALL_ALGS = list(lco.ALG_NAMES)
+
+
+def _rand(dims, density, seed, sig=None, nnz=None):
+    rng = np.random.default_rng(seed)
+    total = int(np.prod(dims))
+    nnz = nnz if nnz is not None else max(1, int(total * density))
+    if total <= 4 * nnz:
+        liv = np.sort(rng.choice(total, size=min(nnz, total), replace=False))
+    else:
+        liv = np.unique(rng.integers(0, total, size=int(nnz * 1.3) + 8))[:nnz]
+    liv = np.sort(liv).astype(np.int64)
+    T = {"dims": list(dims), "sig": list(range(len(dims) - 1, -1, -1)), "liv": liv,
+         "val": rng.uniform(-1, 1, liv.shape[0])}
+    if sig is not None:
+        lo, vo = oracle.permute(T["dims"], T["sig"], sig, T["liv"], T["val"])
+        T = {"dims": list(dims), "sig": list(sig), "liv": lo, "val": vo}
+    return T
+
+
+def _run(A, B, ma, mb, alg=None):
+    C, info = lco.contract(dev(A), dev(B), ma, mb, alg=alg, return_info=True)
+    assert info["status"] == 0
+    if alg is not None:
+        assert info["alg"] == alg
+    return C, info
+
+
+def test_fd2d_laplacian_squared_closed_form_bit_exact():
+    """16x16 5-point Laplacian composed with itself: 3012 entries of the
+    13-point biharmonic stencil; small integers, so bit-exact."""
+    cfg = synth.config_fd2d(16)
+    C, info = _run(cfg["A"], cfg["B"], cfg["modes_a"], cfg["modes_b"])
+    assert info["alg"] == "CSR" and info["f"] == 5832 and info["nnz_c"] == 3012
+    liv, val = host(C)
+    rl, rv, _ = oracle.contract(cfg["A"], cfg["B"], cfg["modes_a"], cfg["modes_b"])
+    assert np.array_equal(liv, rl) and np.array_equal(val, rv)
+
+
+@pytest.mark.parametrize("alg", ALL_ALGS)
+def test_every_branch_fd2d(alg):
+    cfg = synth.config_fd2d(16)
+    C, _ = _run(cfg["A"], cfg["B"], cfg["modes_a"], cfg["modes_b"], alg)
+    assert_contract_matches(C, cfg["A"], cfg["B"], cfg["modes_a"], cfg["modes_b"], tol=0.0)
+
+
+@pytest.mark.parametrize("alg", ALL_ALGS)
+def test_every_branch_random_mixed_orders(alg):
+    A = _rand([6, 7, 8, 5], 0.15, 11, sig=[2, 0, 3, 1])
+    B = _rand([8, 9, 6], 0.2, 12)
+    for ma, mb in [([2], [0]), ([2, 0], [0, 2]), ([0, 2], [2, 0]), ([], [])]:
+        C, _ = _run(A, B, ma, mb, alg)
+        assert_contract_matches(C, A, B, ma, mb)
+
+
+def test_all_34_matchings_order3():
+    """Every partial permutation of modes between two 5x5x5 tensors (Sec. 3.1: 34 matchings)."""
+    A = _rand([5, 5, 5], 0.3, 13)
+    B = _rand([5, 5, 5], 0.3, 14, sig=[1, 2, 0])
+    count = 0
+    for i in range(4):
+        for sa in itertools.combinations(range(3), i):
+            for sb in itertools.permutations(range(3), i):
+                C, _ = _run(A, B, list(sa), list(sb))
+                assert_contract_matches(C, A, B, list(sa), list(sb))
+                count += 1
+    assert count == 34
+
+
+@pytest.mark.parametrize("alg", ALL_ALGS)
+def test_every_branch_hypersparse_rmat(alg):
+    """Small R-MAT pair in the a_ijk b_ljk form (column-sparse x row-sparse)."""
+    A = synth.rmat3((9, 9, 6), 20_000, 21)
+    B = synth.rmat3((9, 9, 6), 20_000, 22)
+    C, _ = _run(A, B, [1, 2], [1, 2], alg)
+    assert_contract_matches(C, A, B, [1, 2], [1, 2])
+
+
+@pytest.mark.parametrize("alg", ["CSRNA", "CSR", "SOP"])
+def test_rmat_mode2_x_mode0_small(alg):
+    cfg = synth.config_rmat_na(bits=(10, 10, 8), nnz=1 << 14, seeds=(5, 6))
+    C, _ = _run(cfg["A"], cfg["B"], cfg["modes_a"], cfg["modes_b"], alg)
+    assert_contract_matches(C, cfg["A"], cfg["B"], cfg["modes_a"], cfg["modes_b"])
+
+
+def test_heavy_rows_take_the_spill_path():
+    """Rows with thousands of products exceed the shared-memory chunk and are
+    sorted and reduced in global scratch."""
+    rng = np.random.default_rng(30)
+    # A: 3 rows, each hitting 40 dense R rows of 300 entries -> 12000 products per row
+    a_co = np.array([(r, c) for r in range(3) for c in range(0, 80, 2)])
+    A = {"dims": [3, 80], "sig": [1, 0],
+         "liv": np.ravel_multi_index(tuple(a_co.T), (3, 80)).astype(np.int64), "val": rng.uniform(-1, 1, len(a_co))}
+    b_co = np.array([(c, j) for c in range(80) for j in rng.choice(1000, 300, replace=False)])
+    b_liv = np.sort(np.ravel_multi_index(tuple(b_co.T), (80, 1000))).astype(np.int64)
+    B = {"dims": [80, 1000], "sig": [1, 0], "liv": b_liv, "val": rng.uniform(-1, 1, len(b_liv))}
+    for alg in ("CSR", "CSRNA", "DCSR"):
+        C, info = _run(A, B, [1], [0], alg)
+        assert info["f"] == 3 * 40 * 300
+        assert_contract_matches(C, A, B, [1], [0])
+
+
+def test_empty_and_disjoint():
+    A = _rand([10, 10], 0.2, 40)
+    E = {"dims": [10, 10], "sig": [1, 0], "liv": np.empty(0, np.int64), "val": np.empty(0)}
+    C, info = _run(A, E, [1], [0])
+    assert C.nnz == 0 and info["f"] == 0
+    C, info = _run(E, A, [1], [0])
+    assert C.nnz == 0
+    # no matching contracted index at all
+    A1 = {"dims": [4, 4], "sig": [1, 0], "liv": np.array([0, 4], np.int64), "val": np.array([1.0, 2.0])}
+    B1 = {"dims": [4, 4], "sig": [1, 0], "liv": np.array([5, 6], np.int64), "val": np.array([1.0, 2.0])}
+    C, info = _run(A1, B1, [1], [0])
+    assert C.nnz == 0 and info["f"] == 0
+
+
+def test_outer_and_full_contraction():
+    A = _rand([6, 5], 0.4, 41)
+    B = _rand([6, 5], 0.4, 42)
+    C, _ = _run(A, B, [], [])                 # outer product, order 4
+    assert_contract_matches(C, A, B, [], [])
+    C, _ = _run(A, B, [0, 1], [0, 1])         # scalar
+    assert_contract_matches(C, A, B, [0, 1], [0, 1])
+
+
+def test_capacity_error_reported():
+    cfg = synth.config_fd2d(8)
+    A, B = dev(cfg["A"]), dev(cfg["B"])
+    plan = lco.ContractPlan(A.dims, A.sig, A.nnz, B.dims, B.sig, B.nnz, cfg["modes_a"], cfg["modes_b"])
+    plan.ensure_workspace(10)
+    c_liv = torch.empty(10, dtype=torch.int64, device="cuda")
+    c_val = torch.empty(10, dtype=torch.float64, device="cuda")
+    plan.run(A, B, c_liv, c_val)
+    r = plan.result()
+    assert r["status"] == 8 and r["f"] > 10
+
+
+def test_fd3d_full_size_against_oracle():
+    """The 64^3 7-point Laplacian x seeded U(-1,1) x-derivative at full size,
+    in the launch configuration the benchmark times, element by element."""
+    cfg = synth.config_fd3d()
+    C, info = _run(cfg["A"], cfg["B"], cfg["modes_a"], cfg["modes_b"])
+    assert info["alg"] == "CSR" and info["f"] == 3_669_504 and info["nnz_c"] == 3_382_784
+    assert_contract_matches(C, cfg["A"], cfg["B"], cfg["modes_a"], cfg["modes_b"])
+
+
+def test_rmat_na_full_size_against_oracle():
+    """2^14 x 2^14 x 2^12 R-MAT pair, mode 2 x mode 0 (CSRNA) at 2^18 nnz each."""
+    cfg = synth.config_rmat_na()
+    C, info = _run(cfg["A"], cfg["B"], cfg["modes_a"], cfg["modes_b"])
+    assert info["alg"] == "CSRNA"
+    assert_contract_matches(C, cfg["A"], cfg["B"], cfg["modes_a"], cfg["modes_b"])
+
+
+def test_rmat_dcsr_reduced_size_against_oracle():
+    """a_ijk b_ljk on 2^16 x 2^16 x 2^10 R-MAT tensors (1M nnz each): DCSR with
+    B permuted (i,j,k) -> (j,k,i)."""
+    cfg = synth.config_rmat_dcsr(bits=(16, 16, 10), nnz=1_000_000, seeds=(3, 4))
+    C, info = _run(cfg["A"], cfg["B"], cfg["modes_a"], cfg["modes_b"])
+    assert info["alg"] == "DCSR" and info["permute_b"] == 1
+    assert_contract_matches(C, cfg["A"], cfg["B"], cfg["modes_a"], cfg["modes_b"])
