@@ -51,7 +51,8 @@ typedef enum {
     LCO_ERR_TIMEOUT = 5,    /* a device-side wait ran out (device status only) */
     LCO_ERR_CUDA = 6,       /* a CUDA runtime call failed */
     LCO_ERR_ADMISSION = 7,  /* serve: request does not fit the memory budget */
-    LCO_ERR_CAPACITY = 8    /* output capacity smaller than the product count f */
+    LCO_ERR_CAPACITY = 8,   /* output capacity smaller than the product count f */
+    LCO_ERR_TOO_LARGE = 9   /* input larger than lco_radix_permute_static's fixed scratch */
 } lco_status;
 
 /* Shape of an LCO tensor (host struct).  sig[t] is the mode of significance
@@ -151,6 +152,31 @@ int32_t lco_radix_permute(const lco_shape *t, const int32_t *new_sig,
                           const int64_t *liv_in, const double *val_in,
                           int64_t *liv_out, double *val_out,
                           void *ws, size_t ws_bytes, void *stream);
+
+/* Same permutation as lco_radix_permute, for callers that cannot
+ * allocate device memory: a plug-in inside a host application that owns
+ * every device allocation (its own caching allocator, or all memory
+ * reserved at start-up with no allocation allowed afterwards) can neither
+ * call cudaMalloc nor obtain a workspace of a size it does not know in
+ * advance.  This entry point takes no workspace and allocates nothing:
+ * its scratch is one fixed 3 MiB array in device memory, defined by this
+ * library and held by every GPU that loads it until the process exits.
+ * The paper has no counterpart; it is a deployment convenience.
+ *   - t->nnz must not exceed 65536; larger inputs return
+ *     LCO_ERR_TOO_LARGE without doing any device work.
+ *   - The first call on each device looks up the device address of the
+ *     array (with that device current); make that first call before any
+ *     stream capture on the device.
+ *   - Every call on a device shares the one array: calls whose device
+ *     work overlaps (different streams, or different host threads) race
+ *     and corrupt each other's results.  Serialise them.
+ *   - Inputs and outputs are device arrays as for lco_radix_permute.
+ *     Device-side wait timeouts are not reported by this entry point.
+ * Errors: LCO_ERR_INVALID, LCO_ERR_OVERFLOW, LCO_ERR_TOO_LARGE,
+ * LCO_ERR_CUDA. */
+int32_t lco_radix_permute_static(const lco_shape *t, const int32_t *new_sig,
+                                 const int64_t *liv_in, const double *val_in,
+                                 int64_t *liv_out, double *val_out, void *stream);
 
 /* ------------------------------------------------------------------ */
 /* Contraction C = A x_modes B (Sec. 5: map to matrices, convert to a   */

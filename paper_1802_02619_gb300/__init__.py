@@ -26,7 +26,7 @@ ALG = {name: i for i, name in enumerate(ALG_NAMES)}
 STATUS = {
     0: "ok", 1: "invalid argument", 2: "index space exceeds 2^63-1", 3: "unsorted input",
     4: "workspace too small", 5: "device wait timed out", 6: "CUDA runtime error",
-    7: "admission refused", 8: "output capacity too small",
+    7: "admission refused", 8: "output capacity too small", 9: "input exceeds the fixed scratch",
 }
 
 
@@ -85,6 +85,8 @@ _SIGNATURES = {
     "lco_radix_permute": ([ctypes.POINTER(Shape), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                            ctypes.c_void_p], ctypes.c_int32),
+    "lco_radix_permute_static": ([ctypes.POINTER(Shape), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
     "lco_contract_plan": ([ctypes.POINTER(Shape), ctypes.POINTER(Shape), ctypes.c_int32, ctypes.c_void_p,
                            ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int32),
     "lco_plan_get_info": ([ctypes.c_void_p, ctypes.POINTER(PlanInfo)], ctypes.c_int32),

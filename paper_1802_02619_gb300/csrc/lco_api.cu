@@ -69,6 +69,7 @@ const char *lco_status_str(int32_t status) {
     case LCO_ERR_CUDA: return "CUDA runtime error";
     case LCO_ERR_ADMISSION: return "request exceeds the memory budget";
     case LCO_ERR_CAPACITY: return "output capacity smaller than the product count";
+    case LCO_ERR_TOO_LARGE: return "input larger than the fixed scratch of the no-allocation entry point";
     default: return "unknown status";
     }
 }

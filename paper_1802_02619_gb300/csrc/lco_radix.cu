@@ -351,6 +351,8 @@ size_t radix_state_bytes(int64_t n_cap, int D, int P) {
     return b;
 }
 
+size_t radix_hist_table_bytes() { return align_up(kHistTableBytes); }
+
 void radix_carve(RadixJob &job, char *region) {
     char *p = region;
     job.ghist = reinterpret_cast<uint64_t *>(p); p += align_up(kHistTableBytes);

@@ -62,6 +62,8 @@ size_t radix_state_bytes(int64_t n_cap, int D, int P);
 void radix_carve(RadixJob &job, char *region);
 // Enqueues the histogram launch and P scatter launches.
 cudaError_t radix_enqueue(const RadixJob &job, cudaStream_t stream);
+// Bytes of the digit-histogram table at the start of a carved region.
+size_t radix_hist_table_bytes();
 int radix_sm_count();
 
 }  // namespace lco
