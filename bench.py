@@ -58,6 +58,10 @@ def parse_args():
     ap.add_argument("--impl", choices=["lco", "reference"], default="lco")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=["step", "permute"], default="step",
+                    help="step: the benchmark workload; permute: a stand-alone radix permutation "
+                         "of a random 6th-order 64^6 tensor (profiling aid)")
+    ap.add_argument("--nnz", type=int, default=16 << 20, help="non-zeros for --case permute")
     return ap.parse_args()
 
 
@@ -478,8 +482,45 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_permute_case(args):
+    """Stand-alone permutation (k,l,m,i,j,n) of a random 64^6 tensor with
+    --nnz non-zeros; prints per-kernel times.  Not the benchmark line."""
+    import torch
+    import paper_1802_02619_gb300 as lco
+    rng = np.random.default_rng(7)
+    liv = np.unique(rng.integers(0, 1 << 36, size=int(args.nnz * 1.02) + 16))[:args.nnz].astype(np.int64)
+    val = rng.standard_normal(liv.shape[0])
+    t = lco.LcoTensor([64] * 6, [5, 4, 3, 2, 1, 0], torch.tensor(liv, device="cuda"),
+                      torch.tensor(val, device="cuda"))
+    new_sig = [5, 1, 0, 4, 3, 2]
+    perm = lco.Permuter(t.dims, t.sig, new_sig, t.nnz)
+    out_l, out_v = torch.empty_like(t.liv), torch.empty_like(t.val)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        perm(t.liv, t.val, out_l, out_v)
+    torch.cuda.synchronize()
+    lco.timing_enable(True)
+    for _ in range(args.steps):
+        flush.zero_()
+        perm(t.liv, t.val, out_l, out_v)
+    recs = lco.timing_read()
+    lco.timing_enable(False)
+    per = {}
+    for nm, ms in recs:
+        per.setdefault(nm, []).append(ms)
+    n = t.nnz
+    out = {"case": "permute", "nnz": n, "kernels": {k: round(sum(v) / len(v), 5) for k, v in per.items()}}
+    if "k_radix_scatter" in per:
+        ms = sum(per["k_radix_scatter"]) / len(per["k_radix_scatter"])
+        out["scatter_gbs"] = round(32 * n / (ms * 1e-3) / 1e9, 1)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.case == "permute":
+        run_permute_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
