@@ -42,7 +42,9 @@ WORKLOAD = "fd3d_laplacian7_64^3_x_dx_uniform + permute_to_klmijn"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "roofline_traffic.md")
 KERNEL_SOURCES = {
-    "k_chunk": "paper_1802_02619_gb300/csrc/lco_contract.cu",
+    "k_wchunk": "paper_1802_02619_gb300/csrc/lco_contract.cu",
+    "k_heavy": "paper_1802_02619_gb300/csrc/lco_contract.cu",
+    "k_row_table": "paper_1802_02619_gb300/csrc/lco_contract.cu",
     "k_work_scan": "paper_1802_02619_gb300/csrc/lco_contract.cu",
     "k_csr_rowptr": "paper_1802_02619_gb300/csrc/lco_contract.cu",
     "k_radix_scatter": "paper_1802_02619_gb300/csrc/lco_radix.cu",
@@ -365,8 +367,10 @@ def run_lco(args):
 def algorithmic_bytes(kernel, step):
     """Bytes the method must move per launch of `kernel` (lower bound)."""
     nA, nB, nC = step.A.nnz, step.B.nnz, step.nnz_c
-    if kernel == "k_chunk":
+    if kernel == "k_wchunk":
         return 16 * (nA + nB + nC)            # read L and R once, write C
+    if kernel == "k_row_table":
+        return 8 * nA                         # row work offsets (upper bound: one row per entry)
     if kernel == "k_radix_scatter":
         return 32 * nC                        # read key+value, write key+value
     if kernel == "k_radix_upsweep":

@@ -12,14 +12,18 @@
 // Phase 1 (symbolic): rearrange operands into their matrix orders (radix
 // permutation), build R's multiplication datatype -- CSR row pointers
 // (Sec. 5.2.2) or DCSR rows with an auxiliary coarse index (Sec. 5.2.3) --
-// and scan the work 1 + |R row| of every L entry, which gives f.
-// Phase 2 (numeric): the rows of L are cut into chunks of kChunkWork work
-// units; a persistent CTA multiplies a chunk in shared memory, either with a
-// hash accumulator and a sort of the nnz_C(i) distinct outputs (the
-// accumulator branches, Table 6 rows CSC/DCSC) or by sorting all f(i)
-// products and summing duplicates (no-accumulator branch, Sec. 5.2.4), and
-// places its output with decoupled look-back.  SOP (Sec. 5.2.5) expands all f
-// products, sorts them by output LIV with the radix engine and sums runs.
+// and scan the work 1 + |R row| of every L entry, which gives f and L's row
+// table.
+// Phase 2 (numeric): rows whose work exceeds kHeavyWork are multiplied first,
+// one CTA per row, either with a shared-memory hash accumulator and a sort of
+// the nnz_C(i) distinct outputs (the accumulator branches, Table 6 rows
+// CSC/DCSC) or by sorting all f(i) products and summing duplicates (the
+// no-accumulator branch, Sec. 5.2.4).  The remaining (light) rows are cut
+// into chunks of kWarpWork work units, one warp per chunk: a lane merges a
+// row's sorted B rows, which accumulates and sorts in one go.  Every chunk
+// places its output with decoupled look-back, so C is written once, in
+// order.  SOP (Sec. 5.2.5) expands all f products, sorts them by output LIV
+// with the radix engine and sums runs.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -34,15 +38,24 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kCT = 256;                    // threads of the chunk / scan kernels
 constexpr int kCW = kCT / 32;
-constexpr int kChunkWork = 1024;            // work units (entries + products) per chunk
-constexpr int kEntCap = 2048;               // fast path: L entries per chunk
-constexpr int kProdCap = 2048;              // fast path: products per chunk
+constexpr int kEntCap = 2048;               // heavy rows, shared-memory path: L entries
+constexpr int kProdCap = 2048;              // heavy rows, shared-memory path: products
 constexpr int kHashSlots = 2 * kProdCap;
 constexpr int kSortItems = 8;               // CTA sort: items per thread
 constexpr int kSortTile = kCT * kSortItems; // == kProdCap
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kCT * kScanItems;
 constexpr uint64_t kEmpty = ~0ull;
+
+// warp-chunk kernel (light rows)
+constexpr int kWarpWork = 256;              // work units per warp chunk
+constexpr int kHeavyWork = 256;             // rows above this work go to the heavy-row kernel
+constexpr int kWarpProd = kWarpWork + kHeavyWork;   // products of a chunk's light rows
+constexpr int kWarpEnt = kWarpWork + kHeavyWork;    // L entries of a chunk's light rows
+constexpr int kWarpRows = kWarpWork;        // rows starting in a chunk
+constexpr int kMergeRuns = 8;               // runs a lane merges at once
+constexpr int kLaneCopy = 8;                // B rows longer than this are copied by the whole warp
+constexpr int kWarpThreads = 128;           // 4 warps per CTA
 
 // header counter slots
 constexpr int kCtrDcsr = 10;
@@ -320,7 +333,10 @@ __global__ void __launch_bounds__(256) k_dcsr_aux(const int64_t *row_id, const W
 }
 
 // ------------------------------------------------------------------------
-// Work scan over L entries: P[e] = sum_{e' < e} (1 + |R row of e'|).
+// Phase 1: work scan over L entries.  An entry costs 1 + |R row of its
+// column| work units.  The scan produces the row table of L (first entry,
+// row id, work offset of every non-empty row) and, for SOP, the per-entry
+// work prefix P.
 // ------------------------------------------------------------------------
 struct ScanArgs {
     int32_t alg;
@@ -329,24 +345,32 @@ struct ScanArgs {
     DivU64 div_k;
     int64_t k;
     Mdt mdt;
-    int64_t *P;            // [nnz_l + 1]
-    uint64_t *state;
+    int64_t *P;            // [nnz_l + 1] or null
+    int64_t *row_start;    // [nrows + 1]
+    int64_t *row_id;       // [nrows]
+    int64_t *row_work;     // [nrows + 1]
+    uint64_t *state_w;     // look-back words (work)
+    uint64_t *state_h;     // look-back words (row heads)
     WsHeader *hdr;
 };
 
 __global__ void __launch_bounds__(kCT) k_work_scan(const __grid_constant__ ScanArgs a) {
     __shared__ int64_t s_tmp[kCW + 1];
-    __shared__ int64_t s_tile, s_excl;
+    __shared__ int64_t s_tile, s_ew, s_eh;
     if (threadIdx.x == 0) s_tile = atomicAdd(&a.hdr->counters[kCtrScan], 1u);
     __syncthreads();
     const int64_t tile = s_tile;
     const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    int64_t w[kScanItems];
-    int64_t local = 0;
+    int64_t w[kScanItems], rows[kScanItems];
+    int64_t wsum = 0, hsum = 0;
+    uint32_t heads = 0;
+    int64_t prev = -1;
+    if (base > 0 && base - 1 < a.nnz_l) prev = (int64_t)divu(a.div_k, (uint64_t)a.l_liv[base - 1]);
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         const int64_t e = base + i;
         w[i] = 0;
+        rows[i] = -1;
         if (e < a.nnz_l) {
             const uint64_t liv = (uint64_t)a.l_liv[e];
             const uint64_t row = divu(a.div_k, liv);
@@ -354,172 +378,168 @@ __global__ void __launch_bounds__(kCT) k_work_scan(const __grid_constant__ ScanA
             int64_t b0, len;
             mdt_lookup(a.mdt, c, b0, len);
             w[i] = 1 + len;
+            rows[i] = (int64_t)row;
+            if ((int64_t)row != prev) heads |= 1u << i;
+            prev = (int64_t)row;
         }
-        local += w[i];
+        wsum += w[i];
     }
-    int64_t tot;
-    int64_t ex = block_excl<int64_t>(local, s_tmp, &tot);
+    hsum = __popc(heads);
+    int64_t wtot, htot;
+    const int64_t wex = block_excl<int64_t>(wsum, s_tmp, &wtot);
+    const int64_t hex = block_excl<int64_t>(hsum, s_tmp, &htot);
     if (threadIdx.x == 0) {
-        lb_store(a.state + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
-        int64_t e = 0;
+        lb_store(a.state_w + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)wtot);
+        lb_store(a.state_h + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)htot);
+        int64_t ew = 0, eh = 0;
         if (tile > 0) {
-            e = (int64_t)lookback(a.state, tile, 1, &a.hdr->status);
-            lb_store(a.state + tile, kFlagIncl | (uint64_t)(e + tot));
+            ew = (int64_t)lookback(a.state_w, tile, 1, &a.hdr->status);
+            lb_store(a.state_w + tile, kFlagIncl | (uint64_t)(ew + wtot));
+            eh = (int64_t)lookback(a.state_h, tile, 1, &a.hdr->status);
+            lb_store(a.state_h + tile, kFlagIncl | (uint64_t)(eh + htot));
         }
-        s_excl = e;
+        s_ew = ew;
+        s_eh = eh;
         const int64_t ntiles = (a.nnz_l + kScanTile - 1) / kScanTile;
         if (tile == ntiles - 1) {
-            const int64_t W = e + tot;
-            a.P[a.nnz_l] = W;
+            const int64_t W = ew + wtot, R = eh + htot;
+            if (a.P) a.P[a.nnz_l] = W;
+            a.row_start[R] = a.nnz_l;
+            a.row_work[R] = W;
             a.hdr->work_total = W;
             a.hdr->f = W - a.nnz_l;
-            a.hdr->nchunks = (W + kChunkWork - 1) / kChunkWork;
+            a.hdr->nrows_l = R;
+            a.hdr->nchunks = (W + kWarpWork - 1) / kWarpWork;
             a.hdr->alg = a.alg;
         }
     }
     __syncthreads();
-    int64_t run = s_excl + ex;
+    int64_t run = s_ew + wex;
+    int64_t h = s_eh + hex;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         const int64_t e = base + i;
-        if (e < a.nnz_l) a.P[e] = run;
+        if (e < a.nnz_l) {
+            if (a.P) a.P[e] = run;
+            if (heads & (1u << i)) {
+                a.row_start[h] = e;
+                a.row_id[h] = rows[i];
+                a.row_work[h] = run;
+                ++h;
+            }
+        }
         run += w[i];
     }
 }
 
+// Chunk table and heavy rows.  Chunk g of the warp kernel holds the rows
+// whose work offset lies in [g * kWarpWork, (g + 1) * kWarpWork):
+// chunk_row[g] = first row r with row_work[r] >= g * kWarpWork.  Rows whose
+// work exceeds kHeavyWork are listed for the CTA-level heavy-row kernel.
+struct TableArgs {
+    const int64_t *row_work;
+    int64_t *chunk_row;    // [nchunks + 1]
+    int64_t *heavy_list;   // [nrows]
+    unsigned long long *nheavy;
+    int64_t cap_rows;      // upper bound on nrows (array sizes)
+    int64_t cap;           // output capacity (f must not exceed it)
+    WsHeader *hdr;
+};
+
+__global__ void __launch_bounds__(256) k_row_table(const __grid_constant__ TableArgs a) {
+    if (a.hdr->f > a.cap) return;
+    const int64_t nrows = a.hdr->nrows_l;
+    const int64_t nchunks = a.hdr->nchunks;
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= nrows && r <= a.cap_rows; r += gsz) {
+        const int64_t wr = a.row_work[r];
+        const int64_t g_lo = r == 0 ? 0 : a.row_work[r - 1] / kWarpWork + 1;
+        const int64_t g_hi = r == nrows ? nchunks : wr / kWarpWork;
+        for (int64_t g = g_lo; g <= g_hi && g <= nchunks; ++g) a.chunk_row[g] = r;
+        if (r < nrows && a.row_work[r + 1] - wr > kHeavyWork) {
+            const unsigned long long h = atomicAdd(a.nheavy, 1ull);
+            a.heavy_list[h] = r;
+        }
+    }
+}
+
 // ------------------------------------------------------------------------
-// Chunk kernel (phase 2)
+// Heavy rows (work > kHeavyWork): one CTA per row.  Products are
+// accumulated in a shared-memory hash and the distinct entries sorted (the
+// accumulator branches), or sorted and summed (no-accumulator branch); rows
+// whose products exceed shared memory are sorted and reduced in global
+// scratch.  The reduced row is left at the row's product offset in scratch
+// and its length in row_hout[r] (bit 62 set when it lies in the second
+// scratch buffer).
 // ------------------------------------------------------------------------
-struct ChunkArgs {
+struct HeavyArgs {
     const int64_t *l_liv;
     const double *l_val;
     const int64_t *r_liv;
     const double *r_val;
-    int64_t nnz_l;
     DivU64 div_k;
     int64_t k;
-    DivU64 div_n;          // nR
+    DivU64 div_n;
     int64_t nR;
     int32_t colbits;
-    int32_t acc;           // 1: hash accumulator, 0: sort all products
+    int32_t acc;
     Mdt mdt;
-    const int64_t *P;
-    int64_t *c_liv;
-    double *c_val;
+    const int64_t *row_start;
+    const int64_t *row_work;
+    const int64_t *heavy_list;
+    const unsigned long long *nheavy;
+    int64_t *row_hout;
     int64_t cap;
-    uint64_t *chunk_state;
-    uint32_t *chunk_ctr;
-    // spill scratch (cap-sized, indexed by product offset)
     uint64_t *sk0;
     double *sv0;
     uint64_t *sk1;
     double *sv1;
+    uint32_t *ctr;
     WsHeader *hdr;
 };
 
-__device__ __forceinline__ int64_t row_of(const ChunkArgs &a, int64_t e) {
-    return (int64_t)divu(a.div_k, (uint64_t)a.l_liv[e]);
-}
-
-// first entry index >= e that starts a row of L (or nnz_l)
-__device__ int64_t first_head_from(const ChunkArgs &a, int64_t e) {
-    if (e >= a.nnz_l) return a.nnz_l;
-    if (e == 0) return 0;
-    const int64_t r = row_of(a, e);
-    if (r != row_of(a, e - 1)) return e;
-    // first entry with LIV >= (r + 1) * k
-    const int64_t bound = (r + 1) * a.k;
-    int64_t lo = e, hi = a.nnz_l;
-    while (lo < hi) {
-        int64_t mid = lo + ((hi - lo) >> 1);
-        if (a.l_liv[mid] < bound) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-__device__ int64_t lower_bound_P(const int64_t *P, int64_t n, int64_t x) {   // first e in [0,n] with P[e] >= x
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        int64_t mid = lo + ((hi - lo) >> 1);
-        if (P[mid] < x) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-struct ChunkSmem {
+struct HeavySmem {
     int32_t poff[kEntCap + 1];
-    int64_t b0[kEntCap];      // ACC: reused as compacted keys
-    double aval[kEntCap];     // ACC: reused as compacted values
-    uint16_t lrow[kEntCap];
-    int64_t gid[kEntCap];
-    uint64_t pk0[kProdCap];   // products (ping-pong); ACC: 4096-slot hash keys over pk0..pk1
+    int64_t b0[kEntCap];
+    double aval[kEntCap];
+    uint64_t pk0[kProdCap];   // ACC: kHashSlots hash keys over pk0..pk1
     uint64_t pk1[kProdCap];
     double pv0[kProdCap];     // ACC: hash values over pv0..pv1
     double pv1[kProdCap];
+    uint64_t ok[kProdCap];
+    double ov[kProdCap];
     uint32_t whist[kCW * 256];
     int64_t run[256];
     int64_t tmp64[kCW + 2];
     int32_t tmp32[kCW + 2];
 };
 
-__global__ void __launch_bounds__(kCT, 1) k_chunk(const __grid_constant__ ChunkArgs a) {
+__global__ void __launch_bounds__(kCT, 1) k_heavy(const __grid_constant__ HeavyArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ChunkSmem &S = *reinterpret_cast<ChunkSmem *>(smem_raw);
-    __shared__ int64_t s_g, s_h0, s_eend, s_e1, s_nprod, s_pbase, s_off;
-    __shared__ int s_fast;
+    HeavySmem &S = *reinterpret_cast<HeavySmem *>(smem_raw);
+    __shared__ int64_t s_h;
     const int tid = threadIdx.x;
-    const int64_t f = a.hdr->f;
-    if (f > a.cap) {
-        if (blockIdx.x == 0 && tid == 0) {
-            set_error(&a.hdr->status, LCO_ERR_CAPACITY);
-            a.hdr->nnz_c = 0;
-        }
-        return;
-    }
-    const int64_t W = a.hdr->work_total;
-    const int64_t nchunks = a.hdr->nchunks;
-    const uint64_t colmask = a.colbits >= 64 ? ~0ull : ((1ull << a.colbits) - 1);
-
+    if (a.hdr->f > a.cap) return;
+    const int64_t nheavy = (int64_t)*a.nheavy;
     for (;;) {
-        if (tid == 0) {
-            const int64_t g = atomicAdd(a.chunk_ctr, 1u);
-            s_g = g;
-            if (g < nchunks) {
-                const int64_t lo = g * kChunkWork;
-                const int64_t hi = lo + kChunkWork < W ? lo + kChunkWork : W;
-                const int64_t e0 = lower_bound_P(a.P, a.nnz_l, lo);
-                const int64_t e1 = hi >= W ? a.nnz_l : lower_bound_P(a.P, a.nnz_l, hi);
-                const int64_t h0 = first_head_from(a, e0);
-                const int64_t eend = h0 < e1 ? first_head_from(a, e1) : h0;
-                s_h0 = h0;
-                s_e1 = e1;
-                s_eend = eend;
-                s_pbase = a.P[h0] - h0;
-                s_nprod = (a.P[eend] - eend) - (a.P[h0] - h0);
-                s_fast = (eend - h0) <= kEntCap && s_nprod <= kProdCap;
-            }
-        }
+        if (tid == 0) s_h = atomicAdd(a.ctr, 1u);
         __syncthreads();
-        const int64_t g = s_g;
-        if (g >= nchunks) break;
-        const int64_t h0 = s_h0, eend = s_eend;
-        const int nent_fast = (int)(eend - h0);
-        const int64_t nprod = s_nprod;
-        int64_t nout = 0;
-
-        if (s_fast) {
-            // ---- stage entries: lookup, local rows, product offsets ----
-            int32_t len_i[kEntCap / kCT];
-            int32_t head_i[kEntCap / kCT];
-            int64_t row_i[kEntCap / kCT];
-            int32_t lsum = 0, hsum = 0;
+        const int64_t h = s_h;
+        if (h >= nheavy) break;
+        const int64_t r = a.heavy_list[h];
+        const int64_t h0 = a.row_start[r], eend = a.row_start[r + 1];
+        const int64_t pbase = a.row_work[r] - h0;
+        const int64_t nprod = (a.row_work[r + 1] - eend) - pbase;
+        const int64_t nent = eend - h0;
+        if (nent <= kEntCap && nprod <= kProdCap) {
+            // ---- shared-memory path ----
+            int64_t len_i[kEntCap / kCT];
+            int64_t lsum = 0;
 #pragma unroll
             for (int q = 0; q < kEntCap / kCT; ++q) {
                 const int j = tid * (kEntCap / kCT) + q;
                 len_i[q] = 0;
-                head_i[q] = 0;
-                row_i[q] = 0;
-                if (j < nent_fast) {
+                if (j < nent) {
                     const int64_t e = h0 + j;
                     const uint64_t liv = (uint64_t)a.l_liv[e];
                     const uint64_t row = divu(a.div_k, liv);
@@ -528,64 +548,47 @@ __global__ void __launch_bounds__(kCT, 1) k_chunk(const __grid_constant__ ChunkA
                     mdt_lookup(a.mdt, c, b0, len);
                     S.b0[j] = b0;
                     S.aval[j] = a.l_val[e];
-                    len_i[q] = (int32_t)len;
-                    row_i[q] = (int64_t)row;
-                    head_i[q] = (j == 0) || ((int64_t)row != row_of(a, e - 1));
+                    len_i[q] = len;
                 }
                 lsum += len_i[q];
-                hsum += head_i[q];
             }
-            int32_t ltot, htot;
-            int32_t lex = block_excl<int32_t>(lsum, S.tmp32, &ltot);
-            int32_t hex = block_excl<int32_t>(hsum, S.tmp32, &htot);
+            int32_t ltot;
+            int32_t lex = block_excl<int32_t>((int32_t)lsum, S.tmp32, &ltot);
 #pragma unroll
             for (int q = 0; q < kEntCap / kCT; ++q) {
                 const int j = tid * (kEntCap / kCT) + q;
-                if (j < nent_fast) {
-                    S.poff[j] = lex;
-                    hex += head_i[q];
-                    S.lrow[j] = (uint16_t)(hex - 1);
-                    if (head_i[q]) S.gid[hex - 1] = row_i[q];
-                }
-                lex += len_i[q];
+                if (j < nent) S.poff[j] = lex;
+                lex += (int32_t)len_i[q];
             }
-            if (tid == 0) S.poff[nent_fast] = ltot;
-            const int nrows = htot;
-            const int np = ltot;
+            if (tid == 0) S.poff[nent] = ltot;
             if (a.acc) {
-                uint64_t *hk = S.pk0;   // pk0|pk1 contiguous: kHashSlots keys
-                double *hv = S.pv0;     // pv0|pv1 contiguous: kHashSlots values
                 for (int i = tid; i < kHashSlots; i += kCT) {
-                    hk[i] = kEmpty;
-                    hv[i] = 0.0;
+                    S.pk0[i] = kEmpty;   // pk0|pk1 contiguous
+                    S.pv0[i] = 0.0;      // pv0|pv1 contiguous
                 }
             }
             __syncthreads();
-            // ---- expand products ----
+            const int np = ltot;
             for (int p = tid; p < np; p += kCT) {
-                int lo = 0, hi = nent_fast;   // owner: last j with poff[j] <= p
+                int lo = 0, hi = (int)nent;
                 while (hi - lo > 1) {
                     const int mid = (lo + hi) >> 1;
                     if (S.poff[mid] <= p) lo = mid; else hi = mid;
                 }
-                const int own = lo;
-                const int64_t b = S.b0[own] + (p - S.poff[own]);
+                const int64_t b = S.b0[lo] + (p - S.poff[lo]);
                 const uint64_t rl = (uint64_t)a.r_liv[b];
                 const uint64_t col = rl - divu(a.div_n, rl) * (uint64_t)a.nR;
-                const uint64_t key = ((uint64_t)S.lrow[own] << a.colbits) | col;
-                const double v = S.aval[own] * a.r_val[b];
+                const double v = S.aval[lo] * a.r_val[b];
                 if (!a.acc) {
-                    S.pk0[p] = key;
+                    S.pk0[p] = col;
                     S.pv0[p] = v;
                 } else {
-                    uint64_t *hk = S.pk0;
-                    double *hv = S.pv0;
-                    uint32_t slot = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 52) & (kHashSlots - 1);
+                    uint32_t slot = (uint32_t)((col * 0x9E3779B97F4A7C15ull) >> 52) & (kHashSlots - 1);
                     for (;;) {
                         const unsigned long long old =
-                            atomicCAS(reinterpret_cast<unsigned long long *>(&hk[slot]), kEmpty, key);
-                        if (old == kEmpty || old == key) {
-                            atomicAdd(&hv[slot], v);
+                            atomicCAS(reinterpret_cast<unsigned long long *>(&S.pk0[slot]), kEmpty, col);
+                        if (old == kEmpty || old == col) {
+                            atomicAdd(&S.pv0[slot], v);
                             break;
                         }
                         slot = (slot + 1) & (kHashSlots - 1);
@@ -593,140 +596,99 @@ __global__ void __launch_bounds__(kCT, 1) k_chunk(const __grid_constant__ ChunkA
                 }
             }
             __syncthreads();
-            const int kbits = a.colbits + bits_for((uint64_t)(nrows > 0 ? nrows : 1));
+            int64_t nout = 0;
             if (!a.acc) {
-                const int res = cta_sort(S.pk0, S.pv0, S.pk1, S.pv1, np, kbits, S.whist, S.run, S.tmp64);
-                uint64_t *k = res ? S.pk1 : S.pk0;
-                double *v = res ? S.pv1 : S.pv0;
-                uint64_t *ok = reinterpret_cast<uint64_t *>(S.b0);
-                double *ov = S.aval;
-                // segmented sum of equal keys, in sorted (generation) order
-                int32_t hcount = 0;
+                const int rs = cta_sort(S.pk0, S.pv0, S.pk1, S.pv1, np, a.colbits, S.whist, S.run, S.tmp64);
+                const uint64_t *k = rs ? S.pk1 : S.pk0;
+                const double *v = rs ? S.pv1 : S.pv0;
+                int32_t hc = 0;
                 for (int q = 0; q < kProdCap / kCT; ++q) {
                     const int i = tid * (kProdCap / kCT) + q;
-                    if (i < np && (i == 0 || k[i] != k[i - 1])) ++hcount;
+                    if (i < np && (i == 0 || k[i] != k[i - 1])) ++hc;
                 }
-                int32_t htot2;
-                int32_t o = block_excl<int32_t>(hcount, S.tmp32, &htot2);
+                int32_t htot;
+                int32_t o = block_excl<int32_t>(hc, S.tmp32, &htot);
                 for (int q = 0; q < kProdCap / kCT; ++q) {
                     const int i = tid * (kProdCap / kCT) + q;
                     if (i < np && (i == 0 || k[i] != k[i - 1])) {
                         double s = v[i];
                         for (int t = i + 1; t < np && k[t] == k[i]; ++t) s += v[t];
-                        ok[o] = k[i];
-                        ov[o] = s;
+                        S.ok[o] = k[i];
+                        S.ov[o] = s;
                         ++o;
                     }
                 }
-                nout = htot2;
+                nout = htot;
             } else {
-                uint64_t *hk = S.pk0;
-                double *hv = S.pv0;
-                uint64_t *ok = reinterpret_cast<uint64_t *>(S.b0);
-                double *ov = S.aval;
                 int32_t cnt = 0;
-                for (int q = 0; q < kHashSlots / kCT; ++q) cnt += hk[tid * (kHashSlots / kCT) + q] != kEmpty;
+                for (int q = 0; q < kHashSlots / kCT; ++q) cnt += S.pk0[tid * (kHashSlots / kCT) + q] != kEmpty;
                 int32_t tot;
                 int32_t o = block_excl<int32_t>(cnt, S.tmp32, &tot);
                 for (int q = 0; q < kHashSlots / kCT; ++q) {
                     const int i = tid * (kHashSlots / kCT) + q;
-                    if (hk[i] != kEmpty) {
-                        ok[o] = hk[i];
-                        ov[o] = hv[i];
+                    if (S.pk0[i] != kEmpty) {
+                        S.ok[o] = S.pk0[i];
+                        S.ov[o] = S.pv0[i];
                         ++o;
                     }
                 }
                 __syncthreads();
                 nout = tot;
-                // sort the distinct entries (b0/aval -> pk1/pv1 ping-pong)
-                int r = cta_sort(ok, ov, S.pk1, S.pv1, nout, kbits, S.whist, S.run, S.tmp64);
-                if (r) {
+                const int rs = cta_sort(S.ok, S.ov, S.pk1, S.pv1, nout, a.colbits, S.whist, S.run, S.tmp64);
+                if (rs) {
                     for (int i = tid; i < nout; i += kCT) {
-                        ok[i] = S.pk1[i];
-                        ov[i] = S.pv1[i];
+                        S.ok[i] = S.pk1[i];
+                        S.ov[i] = S.pv1[i];
                     }
                 }
             }
             __syncthreads();
+            for (int64_t i = tid; i < nout; i += kCT) {
+                a.sk0[pbase + i] = S.ok[i];
+                a.sv0[pbase + i] = S.ov[i];
+            }
+            if (tid == 0) a.row_hout[r] = nout;
+            __syncthreads();
         } else {
-            // ---- spill path: products sorted and reduced in global scratch ----
-            const int64_t pbase = s_pbase;
+            // ---- global path: expand, sort and reduce in scratch ----
             uint64_t *gk0 = a.sk0 + pbase;
             double *gv0 = a.sv0 + pbase;
             uint64_t *gk1 = a.sk1 + pbase;
             double *gv1 = a.sv1 + pbase;
-            int64_t rows_before = 0;
             int64_t prod_before = 0;
-            for (int64_t t0 = h0; t0 < eend; t0 += kEntCap) {
-                const int ne = (int)((eend - t0) < kEntCap ? (eend - t0) : kEntCap);
-                int32_t len_i[kEntCap / kCT];
-                int32_t head_i[kEntCap / kCT];
-                int64_t row_i[kEntCap / kCT];
-                int64_t lsum = 0;
-                int32_t hsum = 0;
-#pragma unroll
-                for (int q = 0; q < kEntCap / kCT; ++q) {
-                    const int j = tid * (kEntCap / kCT) + q;
-                    len_i[q] = 0;
-                    head_i[q] = 0;
-                    row_i[q] = 0;
-                    if (j < ne) {
-                        const int64_t e = t0 + j;
-                        const uint64_t liv = (uint64_t)a.l_liv[e];
-                        const uint64_t row = divu(a.div_k, liv);
-                        const int64_t c = (int64_t)(liv - row * (uint64_t)a.k);
-                        int64_t b0, len;
-                        mdt_lookup(a.mdt, c, b0, len);
-                        S.b0[j] = b0;
-                        S.aval[j] = a.l_val[e];
-                        len_i[q] = (int32_t)len;
-                        row_i[q] = (int64_t)row;
-                        head_i[q] = (e == h0) || ((int64_t)row != row_of(a, e - 1));
-                    }
-                    lsum += len_i[q];
-                    hsum += head_i[q];
+            for (int64_t t0 = h0; t0 < eend; t0 += kCT) {
+                const int64_t e = t0 + tid;
+                int64_t b0 = 0, len = 0;
+                double av = 0.0;
+                int64_t c = 0;
+                if (e < eend) {
+                    const uint64_t liv = (uint64_t)a.l_liv[e];
+                    const uint64_t row = divu(a.div_k, liv);
+                    c = (int64_t)(liv - row * (uint64_t)a.k);
+                    mdt_lookup(a.mdt, c, b0, len);
+                    av = a.l_val[e];
                 }
                 int64_t ltot;
-                int32_t htot;
-                int64_t lex = block_excl<int64_t>(lsum, S.tmp64, &ltot);
-                int32_t hex = block_excl<int32_t>(hsum, S.tmp32, &htot);
-#pragma unroll
-                for (int q = 0; q < kEntCap / kCT; ++q) {
-                    const int j = tid * (kEntCap / kCT) + q;
-                    if (j < ne) {
-                        hex += head_i[q];
-                        const int64_t lr = rows_before + hex - 1;
-                        S.lrow[j] = (uint16_t)lr;   // rows per chunk < kChunkWork
-                        if (head_i[q]) S.gid[lr] = row_i[q];
-                        // expand this entry's products directly (contiguous R row)
-                        const int64_t po = prod_before + lex;
-                        for (int32_t t = 0; t < len_i[q]; ++t) {
-                            const int64_t b = S.b0[j] + t;
-                            const uint64_t rl = (uint64_t)a.r_liv[b];
-                            const uint64_t col = rl - divu(a.div_n, rl) * (uint64_t)a.nR;
-                            gk0[po + t] = ((uint64_t)lr << a.colbits) | col;
-                            gv0[po + t] = S.aval[j] * a.r_val[b];
-                        }
-                    }
-                    lex += len_i[q];
+                const int64_t lex = block_excl<int64_t>(len, S.tmp64, &ltot);
+                for (int64_t t = 0; t < len; ++t) {
+                    const int64_t rl = a.r_liv[b0 + t];
+                    gk0[prod_before + lex + t] = (uint64_t)(rl - c * a.nR);
+                    gv0[prod_before + lex + t] = av * a.r_val[b0 + t];
                 }
-                rows_before += htot;
                 prod_before += ltot;
-                __syncthreads();
             }
-            const int kbits = a.colbits + bits_for((uint64_t)(rows_before > 0 ? rows_before : 1));
-            const int r = cta_sort(gk0, gv0, gk1, gv1, nprod, kbits, S.whist, S.run, S.tmp64);
-            uint64_t *k = r ? gk1 : gk0;
-            double *v = r ? gv1 : gv0;
-            uint64_t *ok = r ? gk0 : gk1;
-            double *ov = r ? gv0 : gv1;
-            // reduce runs of equal keys into the other buffer, in tiles
+            __syncthreads();
+            const int rs = cta_sort(gk0, gv0, gk1, gv1, nprod, a.colbits, S.whist, S.run, S.tmp64);
+            const uint64_t *k = rs ? gk1 : gk0;
+            const double *v = rs ? gv1 : gv0;
+            uint64_t *ok = rs ? gk0 : gk1;
+            double *ov = rs ? gv0 : gv1;
             int64_t outc = 0;
             for (int64_t t0 = 0; t0 < nprod; t0 += kCT) {
                 const int64_t i = t0 + tid;
                 const int hd = (i < nprod) && (i == 0 || k[i] != k[i - 1]);
                 int32_t tot;
-                int32_t o = block_excl<int32_t>(hd, S.tmp32, &tot);
+                const int32_t o = block_excl<int32_t>(hd, S.tmp32, &tot);
                 if (hd) {
                     double s = v[i];
                     for (int64_t t = i + 1; t < nprod && k[t] == k[i]; ++t) s += v[t];
@@ -736,47 +698,344 @@ __global__ void __launch_bounds__(kCT, 1) k_chunk(const __grid_constant__ ChunkA
                 outc += tot;
             }
             __syncthreads();
-            nout = outc;
-            // remember which global buffer holds the reduced output
-            if (tid == 0) S.tmp64[kCW + 1] = r;
+            if (tid == 0) a.row_hout[r] = outc | (rs ? 0ll : (1ll << 62));
             __syncthreads();
         }
+    }
+}
 
-        // ---- place the chunk's output: decoupled look-back over chunks ----
-        if (tid == 0) {
+// ------------------------------------------------------------------------
+// Light rows: one warp per chunk of kWarpWork work units, no block barriers.
+// The chunk's products are gathered into shared memory in (row, entry, B
+// entry) order, so every row is a list of runs sorted by column (one run
+// per L entry: the B row it selects).  A lane merges one row's runs (up to
+// kMergeRuns at once), summing equal columns in run order: the merge is at
+// the same time the accumulation and the per-row sort of Table 6.  Rows with
+// more runs are sorted by the whole warp (bitonic network) and reduced.  A
+// first merge counts each row's outputs; after the chunk's offset is known
+// (decoupled look-back over chunks) a second merge writes C.
+// ------------------------------------------------------------------------
+struct WarpArgs {
+    const int64_t *l_liv;
+    const double *l_val;
+    const int64_t *r_liv;
+    const double *r_val;
+    DivU64 div_k;
+    int64_t k;
+    int64_t nR;
+    Mdt mdt;
+    const int64_t *row_start;
+    const int64_t *row_id;
+    const int64_t *row_work;
+    const int64_t *row_hout;
+    const int64_t *chunk_row;
+    int64_t *c_liv;
+    double *c_val;
+    int64_t cap;
+    const uint64_t *sk0;
+    const double *sv0;
+    const uint64_t *sk1;
+    const double *sv1;
+    uint64_t *chunk_state;
+    uint32_t *chunk_ctr;
+    WsHeader *hdr;
+};
+
+struct WarpSmem {
+    uint64_t pcol[kWarpProd];
+    double pval[kWarpProd];
+    int16_t epoff[kWarpEnt + 1];   // product offset of each entry (run starts)
+    int16_t rent[kWarpRows + 1];   // first entry of each row
+    int64_t rout[kWarpRows + 1];   // output count, then output offset, of each row
+    uint8_t rcomplex[kWarpRows];
+};
+
+__device__ __forceinline__ int warp_excl_i32(int v, int *total) {
+    const int lane = threadIdx.x & 31;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += u;
+    }
+    *total = __shfl_sync(kFull, x, 31);
+    return x - v;
+}
+
+// k-way merge of up to kMergeRuns sorted runs [cur[i], end[i]) of (col, val)
+// held in shared memory, summing equal columns in run order.  With `out`
+// set, writes (base + col, sum) to out_liv/out_val[o]; returns the count.
+template <bool kWrite>
+__device__ __forceinline__ int lane_merge(const uint64_t *pcol, const double *pval, int (&cur)[kMergeRuns],
+                                          const int (&end)[kMergeRuns], int64_t base, int64_t *out_liv,
+                                          double *out_val) {
+    uint64_t hk[kMergeRuns];
+#pragma unroll
+    for (int i = 0; i < kMergeRuns; ++i) hk[i] = cur[i] < end[i] ? pcol[cur[i]] : kEmpty;
+    int o = 0;
+    for (;;) {
+        uint64_t m = hk[0];
+#pragma unroll
+        for (int i = 1; i < kMergeRuns; ++i) m = hk[i] < m ? hk[i] : m;
+        if (m == kEmpty) break;
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < kMergeRuns; ++i) {
+            if (hk[i] == m) {
+                if (kWrite) s += pval[cur[i]];
+                ++cur[i];
+                hk[i] = cur[i] < end[i] ? pcol[cur[i]] : kEmpty;
+            }
+        }
+        if (kWrite) {
+            out_liv[o] = base + (int64_t)m;
+            out_val[o] = s;
+        }
+        ++o;
+    }
+    return o;
+}
+
+// Sort n (col, val) pairs in place with a bitonic network (elements at
+// n..pow2 are treated as +infinity), then sum runs of equal columns and
+// compact them to the front.  Whole warp; returns the distinct count.
+__device__ int warp_sort_reduce(uint64_t *col, double *val, int n) {
+    const int lane = threadIdx.x & 31;
+    int n2 = 1;
+    while (n2 < n) n2 <<= 1;
+    for (int kk = 2; kk <= n2; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int t = lane; t < (n2 >> 1); t += 32) {
+                const int i = 2 * j * (t / j) + (t % j);
+                const int l = (j == (kk >> 1)) ? (i ^ (kk - 1)) : (i + j);
+                const int lo = i < l ? i : l, hi = i < l ? l : i;
+                if (hi < n && col[lo] > col[hi]) {
+                    const uint64_t tc = col[lo];
+                    col[lo] = col[hi];
+                    col[hi] = tc;
+                    const double tv = val[lo];
+                    val[lo] = val[hi];
+                    val[hi] = tv;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    int outc = 0;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+        const int i = c0 + lane;
+        const bool head = i < n && (i == 0 || col[i] != col[i - 1]);
+        double s = 0.0;
+        uint64_t key = 0;
+        if (head) {
+            key = col[i];
+            s = val[i];
+            for (int t = i + 1; t < n && col[t] == key; ++t) s += val[t];
+        }
+        const unsigned hb = __ballot_sync(kFull, head);
+        __syncwarp();
+        if (head) {
+            const int o = outc + __popc(hb & lanemask_lt());
+            col[o] = key;
+            val[o] = s;
+        }
+        outc += __popc(hb);
+        __syncwarp();
+    }
+    return outc;
+}
+
+__global__ void __launch_bounds__(kWarpThreads) k_wchunk(const __grid_constant__ WarpArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpSmem &S = reinterpret_cast<WarpSmem *>(smem_raw)[warp];
+    if (a.hdr->f > a.cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            set_error(&a.hdr->status, LCO_ERR_CAPACITY);
+            a.hdr->nnz_c = 0;
+        }
+        return;
+    }
+    const int64_t nchunks = a.hdr->nchunks;
+    for (;;) {
+        int64_t g = 0;
+        if (lane == 0) g = atomicAdd(a.chunk_ctr, 1u);
+        g = __shfl_sync(kFull, g, 0);
+        if (g >= nchunks) break;
+        const int64_t r0 = a.chunk_row[g], r1 = a.chunk_row[g + 1];
+        const int nrows = (int)(r1 - r0);
+        int64_t nout = 0;
+        int heavy_last = 0;
+        int64_t heavy_info = 0;
+        if (nrows > 0) {
+            const int64_t es = a.row_start[r0];
+            // the last row of a chunk may be heavy (work > kHeavyWork); it was reduced earlier
+            heavy_last = (a.row_work[r1] - a.row_work[r1 - 1]) > kHeavyWork;
+            const int nlight = nrows - heavy_last;
+            const int64_t ee_light = a.row_start[r0 + nlight];
+            const int nent = (int)(ee_light - es);
+            for (int q = lane; q <= nlight; q += 32) S.rent[q] = (int16_t)(a.row_start[r0 + q] - es);
+            // ---- gather the light rows' products (lane per L entry) ----
+            int carry = 0;
+            for (int b = 0; b < nent; b += 32) {
+                const int j = b + lane;
+                int64_t b0 = 0, len = 0, c = 0;
+                double av = 0.0;
+                if (j < nent) {
+                    const uint64_t liv = (uint64_t)a.l_liv[es + j];
+                    const uint64_t row = divu(a.div_k, liv);
+                    c = (int64_t)(liv - row * (uint64_t)a.k);
+                    mdt_lookup(a.mdt, c, b0, len);
+                    av = a.l_val[es + j];
+                }
+                int tot;
+                const int off = carry + warp_excl_i32((int)len, &tot);
+                if (j < nent) S.epoff[j] = (int16_t)off;
+                const bool lng = len > kLaneCopy;
+                if (!lng) {
+                    for (int t = 0; t < (int)len; ++t) {
+                        const int64_t rl = a.r_liv[b0 + t];
+                        S.pcol[off + t] = (uint64_t)(rl - c * a.nR);
+                        S.pval[off + t] = av * a.r_val[b0 + t];
+                    }
+                }
+                unsigned lm = __ballot_sync(kFull, lng);
+                while (lm) {
+                    const int src = __ffs(lm) - 1;
+                    lm &= lm - 1;
+                    const int64_t sb0 = __shfl_sync(kFull, b0, src);
+                    const int slen = __shfl_sync(kFull, (int)len, src);
+                    const int soff = __shfl_sync(kFull, off, src);
+                    const int64_t sc = __shfl_sync(kFull, c, src);
+                    const double sav = __shfl_sync(kFull, av, src);
+                    for (int t = lane; t < slen; t += 32) {
+                        const int64_t rl = a.r_liv[sb0 + t];
+                        S.pcol[soff + t] = (uint64_t)(rl - sc * a.nR);
+                        S.pval[soff + t] = sav * a.r_val[sb0 + t];
+                    }
+                }
+                carry += tot;
+            }
+            if (lane == 0) S.epoff[nent] = (int16_t)carry;
+            __syncwarp();
+            // ---- count each light row's outputs ----
+            for (int q = lane; q < nlight; q += 32) {
+                const int j0 = S.rent[q], j1 = S.rent[q + 1];
+                int cur[kMergeRuns], end[kMergeRuns];
+                int nr = 0;
+#pragma unroll
+                for (int i = 0; i < kMergeRuns; ++i) cur[i] = end[i] = 0;
+                bool complex = false;
+                for (int jj = j0; jj < j1; ++jj) {
+                    const int s0 = S.epoff[jj], s1 = S.epoff[jj + 1];
+                    if (s0 < s1) {
+                        if (nr == kMergeRuns) { complex = true; break; }
+#pragma unroll
+                        for (int i = 0; i < kMergeRuns; ++i)
+                            if (i == nr) { cur[i] = s0; end[i] = s1; }
+                        ++nr;
+                    }
+                }
+                int cnt = 0;
+                if (!complex) cnt = lane_merge<false>(S.pcol, S.pval, cur, end, 0, nullptr, nullptr);
+                S.rcomplex[q] = complex;
+                S.rout[q] = cnt;
+            }
+            __syncwarp();
+            // rows with more runs than a lane merges: sorted by the whole warp
+            for (int q0 = 0; q0 < nlight; q0 += 32) {
+                const int q = q0 + lane;
+                unsigned cm = __ballot_sync(kFull, q < nlight && S.rcomplex[q]);
+                while (cm) {
+                    const int src = q0 + __ffs(cm) - 1;
+                    cm &= cm - 1;
+                    const int p0 = S.epoff[S.rent[src]], p1 = S.epoff[S.rent[src + 1]];
+                    const int cnt = warp_sort_reduce(S.pcol + p0, S.pval + p0, p1 - p0);
+                    if (lane == 0) S.rout[src] = cnt;
+                    __syncwarp();
+                }
+            }
+            if (heavy_last) {
+                heavy_info = a.row_hout[r1 - 1];
+                if (lane == 0) S.rout[nlight] = heavy_info & ((1ll << 62) - 1);
+            }
+            __syncwarp();
+            // ---- exclusive scan of the row output counts ----
+            int64_t run = 0;
+            for (int q0 = 0; q0 < nrows; q0 += 32) {
+                const int q = q0 + lane;
+                const int64_t v = q < nrows ? S.rout[q] : 0;
+                int64_t x = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int64_t u = __shfl_up_sync(kFull, x, o);
+                    if (lane >= o) x += u;
+                }
+                const int64_t tot = __shfl_sync(kFull, x, 31);
+                if (q < nrows) S.rout[q] = run + x - v;
+                run += tot;
+            }
+            nout = run;
+            if (lane == 0) S.rout[nrows] = run;
+            __syncwarp();
+        }
+        // ---- chunk placement: decoupled look-back over chunks ----
+        int64_t goff = 0;
+        if (lane == 0) {
             lb_store(a.chunk_state + g, (g == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)nout);
-            int64_t ex = 0;
             if (g > 0) {
-                ex = (int64_t)lookback(a.chunk_state, g, 1, &a.hdr->status);
-                lb_store(a.chunk_state + g, kFlagIncl | (uint64_t)(ex + nout));
+                goff = (int64_t)lookback(a.chunk_state, g, 1, &a.hdr->status);
+                lb_store(a.chunk_state + g, kFlagIncl | (uint64_t)(goff + nout));
             }
-            s_off = ex;
-            if (g == nchunks - 1) a.hdr->nnz_c = ex + nout;
+            if (g == nchunks - 1) a.hdr->nnz_c = goff + nout;
         }
-        __syncthreads();
-        const int64_t off = s_off;
-        if (s_fast) {
-            const uint64_t *ok = reinterpret_cast<const uint64_t *>(S.b0);
-            const double *ov = S.aval;
-            for (int64_t i = tid; i < nout; i += kCT) {
-                const uint64_t key = ok[i];
-                const int64_t lr = (int64_t)(key >> a.colbits);
-                a.c_liv[off + i] = S.gid[lr] * a.nR + (int64_t)(key & colmask);
-                a.c_val[off + i] = ov[i];
-            }
-        } else {
-            const int r = (int)S.tmp64[kCW + 1];
-            const int64_t pbase = s_pbase;
-            const uint64_t *ok = (r ? a.sk0 : a.sk1) + pbase;
-            const double *ov = (r ? a.sv0 : a.sv1) + pbase;
-            for (int64_t i = tid; i < nout; i += kCT) {
-                const uint64_t key = ok[i];
-                const int64_t lr = (int64_t)(key >> a.colbits);
-                a.c_liv[off + i] = S.gid[lr] * a.nR + (int64_t)(key & colmask);
-                a.c_val[off + i] = ov[i];
+        goff = __shfl_sync(kFull, goff, 0);
+        if (nrows == 0) continue;
+        // ---- write C ----
+        const int nlight = nrows - heavy_last;
+        for (int q = lane; q < nlight; q += 32) {
+            const int64_t obase = goff + S.rout[q];
+            const int64_t rbase = a.row_id[r0 + q] * a.nR;
+            const int j0 = S.rent[q], j1 = S.rent[q + 1];
+            if (!S.rcomplex[q]) {
+                int cur[kMergeRuns], end[kMergeRuns];
+                int nr = 0;
+#pragma unroll
+                for (int i = 0; i < kMergeRuns; ++i) cur[i] = end[i] = 0;
+                for (int jj = j0; jj < j1; ++jj) {
+                    const int s0 = S.epoff[jj], s1 = S.epoff[jj + 1];
+                    if (s0 < s1) {
+#pragma unroll
+                        for (int i = 0; i < kMergeRuns; ++i)
+                            if (i == nr) { cur[i] = s0; end[i] = s1; }
+                        ++nr;
+                    }
+                }
+                lane_merge<true>(S.pcol, S.pval, cur, end, rbase, a.c_liv + obase, a.c_val + obase);
+            } else {
+                const int p0 = S.epoff[j0];
+                const int cnt = (int)(S.rout[q + 1] - S.rout[q]);
+                for (int t = 0; t < cnt; ++t) {
+                    a.c_liv[obase + t] = rbase + (int64_t)S.pcol[p0 + t];
+                    a.c_val[obase + t] = S.pval[p0 + t];
+                }
             }
         }
-        __syncthreads();
+        if (heavy_last) {
+            const int64_t r = r1 - 1;
+            const int64_t pb = a.row_work[r] - a.row_start[r];
+            const bool second = (heavy_info >> 62) & 1;
+            const uint64_t *hk = (second ? a.sk1 : a.sk0) + pb;
+            const double *hv = (second ? a.sv1 : a.sv0) + pb;
+            const int64_t obase = goff + S.rout[nlight];
+            const int64_t cnt = S.rout[nlight + 1] - S.rout[nlight];
+            const int64_t rbase = a.row_id[r] * a.nR;
+            for (int64_t t = lane; t < cnt; t += 32) {
+                a.c_liv[obase + t] = rbase + (int64_t)hk[t];
+                a.c_val[obase + t] = hv[t];
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -923,7 +1182,8 @@ struct lco_plan {
     size_t off_l_liv, off_l_val, off_r_liv, off_r_val, off_rp;
     size_t off_p1state, p1state_bytes;
     size_t off_mdt_rowptr, off_mdt_rowid, off_mdt_aux;
-    size_t off_P;
+    size_t off_P;                    // per-entry work prefix (SOP only)
+    size_t off_row_start, off_row_id, off_row_work, off_row_hout, off_heavy;
     size_t phase1_end;
 };
 
@@ -955,7 +1215,7 @@ bool same_sig(int order, const int32_t *a, const int32_t *b) {
 // Phase-2 workspace layout (offsets from the end of the phase-1 region).
 struct P2Layout {
     int64_t capc, nchunks_max;
-    size_t chunk_state, chunk_ctr, reduce_state, zero_bytes;
+    size_t chunk_state, chunk_ctr, reduce_state, zero_bytes, chunk_row;
     size_t arr[6];          // cap-sized scratch arrays (8 bytes per entry)
     size_t sop_radix;
     int sop_D, sop_P;
@@ -1122,8 +1382,8 @@ int32_t lco_contract_plan(const lco_shape *a, const lco_shape *b, int32_t ncontr
     }
     const size_t scan_tiles = (size_t)((nl + kScanTile - 1) / kScanTile) + 1;
     const size_t dcsr_tiles = (size_t)((nr + kScanTile - 1) / kScanTile) + 1;
-    p->off_p1state = take((scan_tiles + dcsr_tiles) * 8);
-    p->p1state_bytes = align_up((scan_tiles + dcsr_tiles) * 8);
+    p->off_p1state = take((2 * scan_tiles + dcsr_tiles) * 8);
+    p->p1state_bytes = align_up((2 * scan_tiles + dcsr_tiles) * 8);
     if (p->lookup == kLookupCsr) {
         p->off_mdt_rowptr = take((size_t)(k + 1) * 8);
     } else {
@@ -1131,7 +1391,12 @@ int32_t lco_contract_plan(const lco_shape *a, const lco_shape *b, int32_t ncontr
         p->off_mdt_rowid = take((size_t)nr * 8);
         p->off_mdt_aux = take((size_t)(p->naux + 1) * 8);
     }
-    p->off_P = take((size_t)(nl + 1) * 8);
+    p->off_P = p->acc == 2 ? take((size_t)(nl + 1) * 8) : 0;
+    p->off_row_start = take((size_t)(nl + 1) * 8);
+    p->off_row_id = take((size_t)nl * 8);
+    p->off_row_work = take((size_t)(nl + 1) * 8);
+    p->off_row_hout = take((size_t)nl * 8);
+    p->off_heavy = take((size_t)nl * 8);
     p->phase1_end = off;
     *plan_out = p;
     return LCO_OK;
@@ -1234,7 +1499,7 @@ int32_t symbolic_enqueue(const lco_plan *p, const int64_t *a_liv, const double *
     Mdt mdt = make_mdt(p, ws);
     const DivU64 div_n = make_div((uint64_t)p->nR);
     uint64_t *scan_state = reinterpret_cast<uint64_t *>(ws + p->off_p1state);
-    uint64_t *dcsr_state = scan_state + ((p->nnz_l + kScanTile - 1) / kScanTile) + 1;
+    uint64_t *dcsr_state = scan_state + 2 * (((p->nnz_l + kScanTile - 1) / kScanTile) + 1);
     if (p->lookup == kLookupCsr) {
         int64_t grid = (std::max<int64_t>(p->nnz_r, p->k + 1) + 255) / 256;
         if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
@@ -1263,8 +1528,12 @@ int32_t symbolic_enqueue(const lco_plan *p, const int64_t *a_liv, const double *
     sa.div_k = make_div((uint64_t)p->k);
     sa.k = p->k;
     sa.mdt = mdt;
-    sa.P = reinterpret_cast<int64_t *>(ws + p->off_P);
-    sa.state = scan_state;
+    sa.P = p->acc == 2 ? reinterpret_cast<int64_t *>(ws + p->off_P) : nullptr;
+    sa.row_start = reinterpret_cast<int64_t *>(ws + p->off_row_start);
+    sa.row_id = reinterpret_cast<int64_t *>(ws + p->off_row_id);
+    sa.row_work = reinterpret_cast<int64_t *>(ws + p->off_row_work);
+    sa.state_w = scan_state;
+    sa.state_h = scan_state + ((p->nnz_l + kScanTile - 1) / kScanTile) + 1;
     sa.hdr = hdr;
     const int64_t tiles = (p->nnz_l + kScanTile - 1) / kScanTile;
     LCO_LAUNCH("k_work_scan", s, k_work_scan<<<(unsigned)tiles, kCT, 0, s>>>(sa));
@@ -1299,37 +1568,86 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
     const int sms = sm_count();
     const int64_t *P = reinterpret_cast<const int64_t *>(ws + p->off_P);
     if (p->acc != 2) {
-        ChunkArgs ca{};
-        ca.l_liv = o.l_liv;
-        ca.l_val = o.l_val;
-        ca.r_liv = o.r_liv;
-        ca.r_val = o.r_val;
-        ca.nnz_l = p->nnz_l;
-        ca.div_k = make_div((uint64_t)p->k);
-        ca.k = p->k;
-        ca.div_n = make_div((uint64_t)p->nR);
-        ca.nR = p->nR;
-        ca.colbits = p->colbits;
-        ca.acc = p->acc;
-        ca.mdt = mdt;
-        ca.P = P;
-        ca.c_liv = c_liv;
-        ca.c_val = c_val;
-        ca.cap = cap;
-        ca.chunk_state = chunk_state;
-        ca.chunk_ctr = chunk_ctr;
-        ca.sk0 = sk0;
-        ca.sv0 = sv0;
-        ca.sk1 = sk1;
-        ca.sv1 = sv1;
-        ca.hdr = hdr;
+        int64_t *row_start = reinterpret_cast<int64_t *>(ws + p->off_row_start);
+        int64_t *row_id = reinterpret_cast<int64_t *>(ws + p->off_row_id);
+        int64_t *row_work = reinterpret_cast<int64_t *>(ws + p->off_row_work);
+        int64_t *row_hout = reinterpret_cast<int64_t *>(ws + p->off_row_hout);
+        int64_t *heavy = reinterpret_cast<int64_t *>(ws + p->off_heavy);
+        int64_t *chunk_row = reinterpret_cast<int64_t *>(p2 + L.chunk_row);
+        unsigned long long *nheavy = reinterpret_cast<unsigned long long *>(chunk_ctr + 4);
+        TableArgs ta{};
+        ta.row_work = row_work;
+        ta.chunk_row = chunk_row;
+        ta.heavy_list = heavy;
+        ta.nheavy = nheavy;
+        ta.cap_rows = p->nnz_l;
+        ta.cap = cap;
+        ta.hdr = hdr;
+        {
+            int64_t grid = (p->nnz_l + 1 + 255) / 256;
+            if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
+            LCO_LAUNCH("k_row_table", s, k_row_table<<<(unsigned)grid, 256, 0, s>>>(ta));
+        }
+        HeavyArgs ha{};
+        ha.l_liv = o.l_liv;
+        ha.l_val = o.l_val;
+        ha.r_liv = o.r_liv;
+        ha.r_val = o.r_val;
+        ha.div_k = make_div((uint64_t)p->k);
+        ha.k = p->k;
+        ha.div_n = make_div((uint64_t)p->nR);
+        ha.nR = p->nR;
+        ha.colbits = p->colbits;
+        ha.acc = p->acc;
+        ha.mdt = mdt;
+        ha.row_start = row_start;
+        ha.row_work = row_work;
+        ha.heavy_list = heavy;
+        ha.nheavy = nheavy;
+        ha.row_hout = row_hout;
+        ha.cap = cap;
+        ha.sk0 = sk0;
+        ha.sv0 = sv0;
+        ha.sk1 = sk1;
+        ha.sv1 = sv1;
+        ha.ctr = chunk_ctr + 2;
+        ha.hdr = hdr;
         static bool attr = false;
         if (!attr) {
-            cudaFuncSetAttribute(k_chunk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ChunkSmem));
+            cudaFuncSetAttribute(k_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(HeavySmem));
+            cudaFuncSetAttribute(k_wchunk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(WarpSmem) * (kWarpThreads / 32)));
             attr = true;
         }
-        int64_t grid = nchunks_max < (int64_t)sms ? nchunks_max : (int64_t)sms;
-        LCO_LAUNCH("k_chunk", s, k_chunk<<<(unsigned)grid, kCT, sizeof(ChunkSmem), s>>>(ca));
+        LCO_LAUNCH("k_heavy", s, k_heavy<<<(unsigned)sms, kCT, sizeof(HeavySmem), s>>>(ha));
+        WarpArgs wa{};
+        wa.l_liv = o.l_liv;
+        wa.l_val = o.l_val;
+        wa.r_liv = o.r_liv;
+        wa.r_val = o.r_val;
+        wa.div_k = make_div((uint64_t)p->k);
+        wa.k = p->k;
+        wa.nR = p->nR;
+        wa.mdt = mdt;
+        wa.row_start = row_start;
+        wa.row_id = row_id;
+        wa.row_work = row_work;
+        wa.row_hout = row_hout;
+        wa.chunk_row = chunk_row;
+        wa.c_liv = c_liv;
+        wa.c_val = c_val;
+        wa.cap = cap;
+        wa.sk0 = sk0;
+        wa.sv0 = sv0;
+        wa.sk1 = sk1;
+        wa.sv1 = sv1;
+        wa.chunk_state = chunk_state;
+        wa.chunk_ctr = chunk_ctr;
+        wa.hdr = hdr;
+        const int warps = kWarpThreads / 32;
+        int64_t grid = (nchunks_max + warps - 1) / warps;
+        if (grid > (int64_t)sms * 4) grid = (int64_t)sms * 4;
+        LCO_LAUNCH("k_wchunk", s, k_wchunk<<<(unsigned)grid, kWarpThreads, sizeof(WarpSmem) * warps, s>>>(wa));
     } else {
         SopArgs sa{};
         sa.l_liv = o.l_liv;
@@ -1387,14 +1705,16 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
 P2Layout p2_layout(const lco_plan *p, int64_t cap) {
     P2Layout L{};
     L.capc = cap > 0 ? cap : 1;
-    L.nchunks_max = (p->nnz_l + L.capc + kChunkWork - 1) / kChunkWork + 2;
+    L.nchunks_max = (p->nnz_l + L.capc + kWarpWork - 1) / kWarpWork + 2;
     size_t off = 0;
     L.chunk_state = off;
-    L.chunk_ctr = (size_t)L.nchunks_max * 8;
+    L.chunk_ctr = (size_t)L.nchunks_max * 8;   // [0] chunks, [1] reduce tiles, [2] heavy rows, [4..5] heavy count
     off += align_up((size_t)L.nchunks_max * 8 + 64);
     L.reduce_state = off;
     off += align_up((size_t)((L.capc + kScanTile - 1) / kScanTile + 2) * 8);
     L.zero_bytes = off;
+    L.chunk_row = off;
+    off += align_up((size_t)(L.nchunks_max + 1) * 8);
     for (int i = 0; i < 6; ++i) {
         L.arr[i] = off;
         off += align_up((size_t)L.capc * 8);

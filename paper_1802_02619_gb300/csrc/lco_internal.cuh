@@ -103,6 +103,7 @@ struct WsHeader {
     int64_t nzr_b;
     int64_t nchunks;
     int64_t work_total;
+    int64_t nrows_l;         // non-empty rows of the left matrix operand
     uint32_t counters[32];   // tile/chunk counters and "last block" counters
 };
 static_assert(sizeof(WsHeader) <= kWsHeaderBytes, "header too large");
@@ -131,21 +132,31 @@ __device__ __forceinline__ uint64_t lb_load(const uint64_t *p) {
 
 // Exclusive prefix of the tiles before `tile` for one counter column; `state`
 // is laid out [tile][stride].  Waits (bounded) for predecessors to publish.
+// The predecessors' words are fetched kLookbackBatch at a time (independent
+// loads in flight) and consumed nearest first until an inclusive prefix is met.
+constexpr int kLookbackBatch = 8;
+
 __device__ __forceinline__ uint64_t lookback(const uint64_t *state, int64_t tile, int64_t stride,
                                              int32_t *status) {
     uint64_t excl = 0;
-    long long t0 = clock64();
-    for (int64_t t = tile - 1; t >= 0; --t) {
-        uint64_t s = lb_load(state + t * stride);
-        while ((s >> 62) == 0) {
-            if (clock64() - t0 > kSpinBudgetCycles) {
-                set_error(status, LCO_ERR_TIMEOUT);
-                return excl;
+    const long long t0 = clock64();
+    for (int64_t t = tile - 1; t >= 0; t -= kLookbackBatch) {
+        uint64_t s[kLookbackBatch];
+#pragma unroll
+        for (int i = 0; i < kLookbackBatch; ++i) s[i] = t - i >= 0 ? lb_load(state + (t - i) * stride) : 0;
+#pragma unroll
+        for (int i = 0; i < kLookbackBatch; ++i) {
+            if (t - i < 0) return excl;
+            while ((s[i] >> 62) == 0) {
+                if (clock64() - t0 > kSpinBudgetCycles) {
+                    set_error(status, LCO_ERR_TIMEOUT);
+                    return excl;
+                }
+                s[i] = lb_load(state + (t - i) * stride);
             }
-            s = lb_load(state + t * stride);
+            excl += s[i] & kValueMask;
+            if ((s[i] >> 62) == 2) return excl;
         }
-        excl += s & kValueMask;
-        if ((s >> 62) == 2) break;
     }
     return excl;
 }

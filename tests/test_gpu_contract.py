@@ -174,3 +174,61 @@ def test_rmat_dcsr_reduced_size_against_oracle():
     C, info = _run(cfg["A"], cfg["B"], cfg["modes_a"], cfg["modes_b"])
     assert info["alg"] == "DCSR" and info["permute_b"] == 1
     assert_contract_matches(C, cfg["A"], cfg["B"], cfg["modes_a"], cfg["modes_b"])
+
+
+def _matrix_pair(rows_spec, n_cols_r=4000, seed=50):
+    """A: one row per spec entry (n_entries, products per entry) over a shared
+    contracted range; B: rows with the requested lengths.  Returns host dicts."""
+    rng = np.random.default_rng(seed)
+    k = sum(ne for ne, _ in rows_spec) + 1
+    a_co, b_rows = [], {}
+    c = 0
+    for r, (ne, pl) in enumerate(rows_spec):
+        for _ in range(ne):
+            a_co.append((r, c))
+            b_rows[c] = np.sort(rng.choice(n_cols_r, size=min(pl, n_cols_r), replace=False))
+            c += 1
+    a_co = np.array(a_co, dtype=np.int64)
+    A = {"dims": [len(rows_spec), k], "sig": [1, 0],
+         "liv": np.ravel_multi_index(tuple(a_co.T), (len(rows_spec), k)).astype(np.int64),
+         "val": rng.uniform(-1, 1, len(a_co))}
+    b_co = np.array([(cc, j) for cc, js in b_rows.items() for j in js], dtype=np.int64)
+    b_liv = np.sort(np.ravel_multi_index(tuple(b_co.T), (k, n_cols_r))).astype(np.int64)
+    B = {"dims": [k, n_cols_r], "sig": [1, 0], "liv": b_liv, "val": rng.uniform(-1, 1, len(b_liv))}
+    return A, B
+
+
+@pytest.mark.parametrize("alg", ["CSR", "CSRNA", "DCSR"])
+def test_row_kinds_in_one_product(alg):
+    """Light rows merged by a lane (<= 8 runs), light rows with more runs
+    (sorted by the whole warp), heavy rows reduced in shared memory and a
+    heavy row reduced in global scratch, mixed in one contraction."""
+    spec = ([(5, 3)] * 40 + [(12, 3)] * 10 + [(20, 15)] * 3 + [(1, 1)] * 30 +
+            [(40, 40)] * 2 + [(3, 2)] * 20 + [(30, 120)] + [(6, 2)] * 50)
+    A, B = _matrix_pair(spec, n_cols_r=50, seed=51)     # few columns: many duplicates
+    C, info = _run(A, B, [1], [0], alg)
+    assert_contract_matches(C, A, B, [1], [0])
+    A, B = _matrix_pair(spec, n_cols_r=100000, seed=52)  # many columns: few duplicates
+    C, info = _run(A, B, [1], [0], alg)
+    assert_contract_matches(C, A, B, [1], [0])
+
+
+def test_plan_reuse_gives_identical_results():
+    """Running the same plan twice (as the benchmark does) reproduces C bit-for-bit."""
+    cfg = synth.config_fd3d(n=24, seed=2)
+    A, B = dev(cfg["A"]), dev(cfg["B"])
+    plan = lco.ContractPlan(A.dims, A.sig, A.nnz, B.dims, B.sig, B.nnz, cfg["modes_a"], cfg["modes_b"])
+    plan.ensure_workspace(0)
+    plan.symbolic(A, B)
+    f = plan.result()["f"]
+    plan.ensure_workspace(f)
+    outs = []
+    for _ in range(2):
+        c_liv = torch.empty(f, dtype=torch.int64, device="cuda")
+        c_val = torch.empty(f, dtype=torch.float64, device="cuda")
+        plan.run(A, B, c_liv, c_val)
+        r = plan.result()
+        assert r["status"] == 0
+        outs.append((c_liv[:r["nnz_c"]].clone(), c_val[:r["nnz_c"]].clone()))
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert torch.equal(outs[0][1].view(torch.int64), outs[1][1].view(torch.int64))
