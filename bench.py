@@ -42,7 +42,7 @@ WORKLOAD = "fd3d_laplacian7_64^3_x_dx_uniform + permute_to_klmijn"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "roofline_traffic.md")
 KERNEL_SOURCES = {
-    "k_wchunk": "paper_1802_02619_gb300/csrc/lco_contract.cu",
+    "k_rows": "paper_1802_02619_gb300/csrc/lco_contract.cu",
     "k_heavy": "paper_1802_02619_gb300/csrc/lco_contract.cu",
     "k_row_table": "paper_1802_02619_gb300/csrc/lco_contract.cu",
     "k_work_scan": "paper_1802_02619_gb300/csrc/lco_contract.cu",
@@ -367,7 +367,7 @@ def run_lco(args):
 def algorithmic_bytes(kernel, step):
     """Bytes the method must move per launch of `kernel` (lower bound)."""
     nA, nB, nC = step.A.nnz, step.B.nnz, step.nnz_c
-    if kernel == "k_wchunk":
+    if kernel == "k_rows":
         return 16 * (nA + nB + nC)            # read L and R once, write C
     if kernel == "k_row_table":
         return 8 * nA                         # row work offsets (upper bound: one row per entry)

@@ -18,11 +18,10 @@
 // one CTA per row, either with a shared-memory hash accumulator and a sort of
 // the nnz_C(i) distinct outputs (the accumulator branches, Table 6 rows
 // CSC/DCSC) or by sorting all f(i) products and summing duplicates (the
-// no-accumulator branch, Sec. 5.2.4).  The remaining (light) rows are cut
-// into chunks of kWarpWork work units, one warp per chunk: a lane merges a
-// row's sorted B rows, which accumulates and sorts in one go.  Every chunk
-// places its output with decoupled look-back, so C is written once, in
-// order.  SOP (Sec. 5.2.5) expands all f products, sorts them by output LIV
+// no-accumulator branch, Sec. 5.2.4).  The remaining (light) rows go one
+// lane per row, 32 rows per warp: a lane merges a row's sorted B rows, which
+// accumulates and sorts in one go.  Every tile of rows places its output
+// with decoupled look-back, so C is written once, in order.  SOP (Sec. 5.2.5) expands all f products, sorts them by output LIV
 // with the radix engine and sums runs.
 #include <algorithm>
 #include <cstdlib>
@@ -47,15 +46,9 @@ constexpr int kScanItems = 8;
 constexpr int kScanTile = kCT * kScanItems;
 constexpr uint64_t kEmpty = ~0ull;
 
-// warp-chunk kernel (light rows)
-constexpr int kWarpWork = 256;              // work units per warp chunk
+// light-row kernel
 constexpr int kHeavyWork = 256;             // rows above this work go to the heavy-row kernel
-constexpr int kWarpProd = kWarpWork + kHeavyWork;   // products of a chunk's light rows
-constexpr int kWarpEnt = kWarpWork + kHeavyWork;    // L entries of a chunk's light rows
-constexpr int kWarpRows = kWarpWork;        // rows starting in a chunk
 constexpr int kMergeRuns = 8;               // runs a lane merges at once
-constexpr int kLaneCopy = 8;                // B rows longer than this are copied by the whole warp
-constexpr int kWarpThreads = 128;           // 4 warps per CTA
 
 // header counter slots
 constexpr int kCtrDcsr = 10;
@@ -409,7 +402,7 @@ __global__ void __launch_bounds__(kCT) k_work_scan(const __grid_constant__ ScanA
             a.hdr->work_total = W;
             a.hdr->f = W - a.nnz_l;
             a.hdr->nrows_l = R;
-            a.hdr->nchunks = (W + kWarpWork - 1) / kWarpWork;
+            a.hdr->nchunks = 0;
             a.hdr->alg = a.alg;
         }
     }
@@ -432,13 +425,10 @@ __global__ void __launch_bounds__(kCT) k_work_scan(const __grid_constant__ ScanA
     }
 }
 
-// Chunk table and heavy rows.  Chunk g of the warp kernel holds the rows
-// whose work offset lies in [g * kWarpWork, (g + 1) * kWarpWork):
-// chunk_row[g] = first row r with row_work[r] >= g * kWarpWork.  Rows whose
-// work exceeds kHeavyWork are listed for the CTA-level heavy-row kernel.
+// Heavy rows: rows whose work exceeds kHeavyWork are listed for the
+// CTA-level heavy-row kernel.
 struct TableArgs {
     const int64_t *row_work;
-    int64_t *chunk_row;    // [nchunks + 1]
     int64_t *heavy_list;   // [nrows]
     unsigned long long *nheavy;
     int64_t cap_rows;      // upper bound on nrows (array sizes)
@@ -449,14 +439,9 @@ struct TableArgs {
 __global__ void __launch_bounds__(256) k_row_table(const __grid_constant__ TableArgs a) {
     if (a.hdr->f > a.cap) return;
     const int64_t nrows = a.hdr->nrows_l;
-    const int64_t nchunks = a.hdr->nchunks;
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= nrows && r <= a.cap_rows; r += gsz) {
-        const int64_t wr = a.row_work[r];
-        const int64_t g_lo = r == 0 ? 0 : a.row_work[r - 1] / kWarpWork + 1;
-        const int64_t g_hi = r == nrows ? nchunks : wr / kWarpWork;
-        for (int64_t g = g_lo; g <= g_hi && g <= nchunks; ++g) a.chunk_row[g] = r;
-        if (r < nrows && a.row_work[r + 1] - wr > kHeavyWork) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows && r < a.cap_rows; r += gsz) {
+        if (a.row_work[r + 1] - a.row_work[r] > kHeavyWork) {
             const unsigned long long h = atomicAdd(a.nheavy, 1ull);
             a.heavy_list[h] = r;
         }
@@ -705,73 +690,72 @@ __global__ void __launch_bounds__(kCT, 1) k_heavy(const __grid_constant__ HeavyA
 }
 
 // ------------------------------------------------------------------------
-// Light rows: one warp per chunk of kWarpWork work units, no block barriers.
-// The chunk's products are gathered into shared memory in (row, entry, B
-// entry) order, so every row is a list of runs sorted by column (one run
-// per L entry: the B row it selects).  A lane merges one row's runs (up to
-// kMergeRuns at once), summing equal columns in run order: the merge is at
-// the same time the accumulation and the per-row sort of Table 6.  Rows with
-// more runs are sorted by the whole warp (bitonic network) and reduced.  A
-// first merge counts each row's outputs; after the chunk's offset is known
-// (decoupled look-back over chunks) a second merge writes C.
+// Light rows (work <= kHeavyWork): one warp per tile of 32 consecutive rows
+// of L, one lane per row, no block barriers.  A lane collects its row's
+// non-empty runs -- the B rows selected by the row's L entries, each sorted
+// by column -- and merges them (k-way, up to kMergeRuns at once), summing
+// equal columns in run order: the merge is at the same time the
+// accumulation and the per-row sort of Table 6.  The B rows are read from
+// L1/L2 directly.  Rows a lane does not merge are taken by the whole warp:
+// a row with a single run is copied (coalesced, scaled) and a row with more
+// runs or more products is gathered into shared memory, sorted (bitonic) and
+// reduced into scratch.  Heavy rows were reduced by k_heavy.  A first pass
+// counts each row's outputs; after the tile's offset is known (decoupled
+// look-back over tiles) a second pass writes C.
 // ------------------------------------------------------------------------
-struct WarpArgs {
+constexpr int kLaneProd = 64;          // products a lane merges by itself
+constexpr int kRowsThreads = 256;      // 8 warps per CTA
+constexpr int kWarpSortCap = kHeavyWork;   // products of a warp-sorted row
+
+struct RowsArgs {
     const int64_t *l_liv;
     const double *l_val;
     const int64_t *r_liv;
     const double *r_val;
-    DivU64 div_k;
     int64_t k;
+    DivU64 div_n;
     int64_t nR;
     Mdt mdt;
     const int64_t *row_start;
     const int64_t *row_id;
     const int64_t *row_work;
     const int64_t *row_hout;
-    const int64_t *chunk_row;
     int64_t *c_liv;
     double *c_val;
     int64_t cap;
-    const uint64_t *sk0;
-    const double *sv0;
+    uint64_t *sk0;
+    double *sv0;
     const uint64_t *sk1;
     const double *sv1;
-    uint64_t *chunk_state;
-    uint32_t *chunk_ctr;
+    uint64_t *tile_state;
+    uint32_t *tile_ctr;
     WsHeader *hdr;
 };
 
-struct WarpSmem {
-    uint64_t pcol[kWarpProd];
-    double pval[kWarpProd];
-    int16_t epoff[kWarpEnt + 1];   // product offset of each entry (run starts)
-    int16_t rent[kWarpRows + 1];   // first entry of each row
-    int64_t rout[kWarpRows + 1];   // output count, then output offset, of each row
-    uint8_t rcomplex[kWarpRows];
+struct RowsSmem {
+    uint64_t pcol[kWarpSortCap];
+    double pval[kWarpSortCap];
 };
 
-__device__ __forceinline__ int warp_excl_i32(int v, int *total) {
-    const int lane = threadIdx.x & 31;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int u = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += u;
-    }
-    *total = __shfl_sync(kFull, x, 31);
-    return x - v;
+__device__ __forceinline__ uint64_t col_of(const DivU64 &div_n, uint64_t nR, int64_t liv) {
+    const uint64_t x = (uint64_t)liv;
+    return x - divu(div_n, x) * nR;
 }
 
-// k-way merge of up to kMergeRuns sorted runs [cur[i], end[i]) of (col, val)
-// held in shared memory, summing equal columns in run order.  With `out`
-// set, writes (base + col, sum) to out_liv/out_val[o]; returns the count.
+// k-way merge of up to kMergeRuns runs [st[i], en[i]) of B entries (columns
+// ascending within a run); with kWrite, writes (base + col, sum of av[i]*b)
+// to out; returns the number of distinct columns.
 template <bool kWrite>
-__device__ __forceinline__ int lane_merge(const uint64_t *pcol, const double *pval, int (&cur)[kMergeRuns],
-                                          const int (&end)[kMergeRuns], int64_t base, int64_t *out_liv,
-                                          double *out_val) {
+__device__ __forceinline__ int lane_merge_g(const RowsArgs &a, const int64_t (&st)[kMergeRuns],
+                                            const int64_t (&en)[kMergeRuns], const double (&av)[kMergeRuns],
+                                            int64_t base, int64_t *out_liv, double *out_val) {
+    int64_t cur[kMergeRuns];
     uint64_t hk[kMergeRuns];
 #pragma unroll
-    for (int i = 0; i < kMergeRuns; ++i) hk[i] = cur[i] < end[i] ? pcol[cur[i]] : kEmpty;
+    for (int i = 0; i < kMergeRuns; ++i) {
+        cur[i] = st[i];
+        hk[i] = cur[i] < en[i] ? col_of(a.div_n, (uint64_t)a.nR, a.r_liv[cur[i]]) : kEmpty;
+    }
     int o = 0;
     for (;;) {
         uint64_t m = hk[0];
@@ -782,9 +766,9 @@ __device__ __forceinline__ int lane_merge(const uint64_t *pcol, const double *pv
 #pragma unroll
         for (int i = 0; i < kMergeRuns; ++i) {
             if (hk[i] == m) {
-                if (kWrite) s += pval[cur[i]];
+                if (kWrite) s += av[i] * a.r_val[cur[i]];
                 ++cur[i];
-                hk[i] = cur[i] < end[i] ? pcol[cur[i]] : kEmpty;
+                hk[i] = cur[i] < en[i] ? col_of(a.div_n, (uint64_t)a.nR, a.r_liv[cur[i]]) : kEmpty;
             }
         }
         if (kWrite) {
@@ -845,10 +829,12 @@ __device__ int warp_sort_reduce(uint64_t *col, double *val, int n) {
     return outc;
 }
 
-__global__ void __launch_bounds__(kWarpThreads) k_wchunk(const __grid_constant__ WarpArgs a) {
+enum RowKind { kRowNone = -1, kRowLane = 0, kRowCopy = 1, kRowSort = 2, kRowHeavy = 3 };
+
+__global__ void __launch_bounds__(kRowsThreads) k_rows(const __grid_constant__ RowsArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpSmem &S = reinterpret_cast<WarpSmem *>(smem_raw)[warp];
+    RowsSmem &S = reinterpret_cast<RowsSmem *>(smem_raw)[warp];
     if (a.hdr->f > a.cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             set_error(&a.hdr->status, LCO_ERR_CAPACITY);
@@ -856,186 +842,164 @@ __global__ void __launch_bounds__(kWarpThreads) k_wchunk(const __grid_constant__
         }
         return;
     }
-    const int64_t nchunks = a.hdr->nchunks;
+    const int64_t nrows = a.hdr->nrows_l;
+    const int64_t ntiles = (nrows + 31) / 32;
+    const uint64_t nR = (uint64_t)a.nR;
     for (;;) {
-        int64_t g = 0;
-        if (lane == 0) g = atomicAdd(a.chunk_ctr, 1u);
-        g = __shfl_sync(kFull, g, 0);
-        if (g >= nchunks) break;
-        const int64_t r0 = a.chunk_row[g], r1 = a.chunk_row[g + 1];
-        const int nrows = (int)(r1 - r0);
-        int64_t nout = 0;
-        int heavy_last = 0;
-        int64_t heavy_info = 0;
-        if (nrows > 0) {
-            const int64_t es = a.row_start[r0];
-            // the last row of a chunk may be heavy (work > kHeavyWork); it was reduced earlier
-            heavy_last = (a.row_work[r1] - a.row_work[r1 - 1]) > kHeavyWork;
-            const int nlight = nrows - heavy_last;
-            const int64_t ee_light = a.row_start[r0 + nlight];
-            const int nent = (int)(ee_light - es);
-            for (int q = lane; q <= nlight; q += 32) S.rent[q] = (int16_t)(a.row_start[r0 + q] - es);
-            // ---- gather the light rows' products (lane per L entry) ----
-            int carry = 0;
-            for (int b = 0; b < nent; b += 32) {
-                const int j = b + lane;
-                int64_t b0 = 0, len = 0, c = 0;
-                double av = 0.0;
-                if (j < nent) {
-                    const uint64_t liv = (uint64_t)a.l_liv[es + j];
-                    const uint64_t row = divu(a.div_k, liv);
-                    c = (int64_t)(liv - row * (uint64_t)a.k);
+        int64_t t = 0;
+        if (lane == 0) t = atomicAdd(a.tile_ctr, 1u);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= ntiles) break;
+        const int64_t r = t * 32 + lane;
+        int kind = kRowNone;
+        int64_t es = 0, ee = 0, rid = 0, pb = 0, work = 0;
+        int64_t st[kMergeRuns], en[kMergeRuns];
+        double av[kMergeRuns];
+#pragma unroll
+        for (int i = 0; i < kMergeRuns; ++i) {
+            st[i] = en[i] = 0;
+            av[i] = 0.0;
+        }
+        int64_t cnt = 0;
+        if (r < nrows) {
+            es = a.row_start[r];
+            ee = a.row_start[r + 1];
+            const int64_t w0 = a.row_work[r];
+            work = a.row_work[r + 1] - w0;
+            rid = a.row_id[r];
+            pb = w0 - es;
+            if (work > kHeavyWork) {
+                kind = kRowHeavy;
+                cnt = a.row_hout[r] & ((1ll << 62) - 1);
+            } else {
+                // collect the non-empty runs (B rows) of this row
+                int nr = 0;
+                const int64_t rbase = rid * a.k;
+                for (int64_t e = es; e < ee; ++e) {
+                    const int64_t c = a.l_liv[e] - rbase;
+                    int64_t b0, len;
                     mdt_lookup(a.mdt, c, b0, len);
-                    av = a.l_val[es + j];
-                }
-                int tot;
-                const int off = carry + warp_excl_i32((int)len, &tot);
-                if (j < nent) S.epoff[j] = (int16_t)off;
-                const bool lng = len > kLaneCopy;
-                if (!lng) {
-                    for (int t = 0; t < (int)len; ++t) {
-                        const int64_t rl = a.r_liv[b0 + t];
-                        S.pcol[off + t] = (uint64_t)(rl - c * a.nR);
-                        S.pval[off + t] = av * a.r_val[b0 + t];
+                    if (len > 0) {
+                        if (nr < kMergeRuns) {
+                            const double v = a.l_val[e];
+#pragma unroll
+                            for (int i = 0; i < kMergeRuns; ++i)
+                                if (i == nr) {
+                                    st[i] = b0;
+                                    en[i] = b0 + len;
+                                    av[i] = v;
+                                }
+                        }
+                        ++nr;
                     }
                 }
-                unsigned lm = __ballot_sync(kFull, lng);
-                while (lm) {
-                    const int src = __ffs(lm) - 1;
-                    lm &= lm - 1;
-                    const int64_t sb0 = __shfl_sync(kFull, b0, src);
-                    const int slen = __shfl_sync(kFull, (int)len, src);
-                    const int soff = __shfl_sync(kFull, off, src);
-                    const int64_t sc = __shfl_sync(kFull, c, src);
-                    const double sav = __shfl_sync(kFull, av, src);
-                    for (int t = lane; t < slen; t += 32) {
-                        const int64_t rl = a.r_liv[sb0 + t];
-                        S.pcol[soff + t] = (uint64_t)(rl - sc * a.nR);
-                        S.pval[soff + t] = sav * a.r_val[sb0 + t];
-                    }
+                const int64_t frow = work - (ee - es);
+                if (nr <= kMergeRuns && frow <= kLaneProd) {
+                    kind = kRowLane;
+                    cnt = lane_merge_g<false>(a, st, en, av, 0, nullptr, nullptr);
+                } else if (nr == 1) {
+                    kind = kRowCopy;
+                    cnt = en[0] - st[0];
+                } else {
+                    kind = kRowSort;
+                }
+            }
+        }
+        // rows sorted by the whole warp (more runs or products than a lane merges)
+        unsigned sm = __ballot_sync(kFull, kind == kRowSort);
+        while (sm) {
+            const int src = __ffs(sm) - 1;
+            sm &= sm - 1;
+            const int64_t ses = __shfl_sync(kFull, es, src);
+            const int64_t see = __shfl_sync(kFull, ee, src);
+            const int64_t srb = __shfl_sync(kFull, rid, src) * a.k;
+            const int64_t spb = __shfl_sync(kFull, pb, src);
+            int carry = 0;
+            for (int64_t e0 = ses; e0 < see; e0 += 32) {
+                const int64_t e = e0 + lane;
+                int64_t b0 = 0, len = 0;
+                double v = 0.0;
+                if (e < see) {
+                    mdt_lookup(a.mdt, a.l_liv[e] - srb, b0, len);
+                    v = a.l_val[e];
+                }
+                int x = (int)len, tot;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(kFull, x, o);
+                    if (lane >= o) x += u;
+                }
+                tot = __shfl_sync(kFull, x, 31);
+                const int off = carry + x - (int)len;
+                for (int64_t q = 0; q < len; ++q) {
+                    S.pcol[off + q] = col_of(a.div_n, nR, a.r_liv[b0 + q]);
+                    S.pval[off + q] = v * a.r_val[b0 + q];
                 }
                 carry += tot;
             }
-            if (lane == 0) S.epoff[nent] = (int16_t)carry;
             __syncwarp();
-            // ---- count each light row's outputs ----
-            for (int q = lane; q < nlight; q += 32) {
-                const int j0 = S.rent[q], j1 = S.rent[q + 1];
-                int cur[kMergeRuns], end[kMergeRuns];
-                int nr = 0;
-#pragma unroll
-                for (int i = 0; i < kMergeRuns; ++i) cur[i] = end[i] = 0;
-                bool complex = false;
-                for (int jj = j0; jj < j1; ++jj) {
-                    const int s0 = S.epoff[jj], s1 = S.epoff[jj + 1];
-                    if (s0 < s1) {
-                        if (nr == kMergeRuns) { complex = true; break; }
-#pragma unroll
-                        for (int i = 0; i < kMergeRuns; ++i)
-                            if (i == nr) { cur[i] = s0; end[i] = s1; }
-                        ++nr;
-                    }
-                }
-                int cnt = 0;
-                if (!complex) cnt = lane_merge<false>(S.pcol, S.pval, cur, end, 0, nullptr, nullptr);
-                S.rcomplex[q] = complex;
-                S.rout[q] = cnt;
+            const int n = warp_sort_reduce(S.pcol, S.pval, carry);
+            for (int i = lane; i < n; i += 32) {
+                a.sk0[spb + i] = S.pcol[i];
+                a.sv0[spb + i] = S.pval[i];
             }
-            __syncwarp();
-            // rows with more runs than a lane merges: sorted by the whole warp
-            for (int q0 = 0; q0 < nlight; q0 += 32) {
-                const int q = q0 + lane;
-                unsigned cm = __ballot_sync(kFull, q < nlight && S.rcomplex[q]);
-                while (cm) {
-                    const int src = q0 + __ffs(cm) - 1;
-                    cm &= cm - 1;
-                    const int p0 = S.epoff[S.rent[src]], p1 = S.epoff[S.rent[src + 1]];
-                    const int cnt = warp_sort_reduce(S.pcol + p0, S.pval + p0, p1 - p0);
-                    if (lane == 0) S.rout[src] = cnt;
-                    __syncwarp();
-                }
-            }
-            if (heavy_last) {
-                heavy_info = a.row_hout[r1 - 1];
-                if (lane == 0) S.rout[nlight] = heavy_info & ((1ll << 62) - 1);
-            }
-            __syncwarp();
-            // ---- exclusive scan of the row output counts ----
-            int64_t run = 0;
-            for (int q0 = 0; q0 < nrows; q0 += 32) {
-                const int q = q0 + lane;
-                const int64_t v = q < nrows ? S.rout[q] : 0;
-                int64_t x = v;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int64_t u = __shfl_up_sync(kFull, x, o);
-                    if (lane >= o) x += u;
-                }
-                const int64_t tot = __shfl_sync(kFull, x, 31);
-                if (q < nrows) S.rout[q] = run + x - v;
-                run += tot;
-            }
-            nout = run;
-            if (lane == 0) S.rout[nrows] = run;
+            if (lane == src) cnt = n;
             __syncwarp();
         }
-        // ---- chunk placement: decoupled look-back over chunks ----
+        // exclusive scan of the row counts, then the tile's place in C
+        int64_t x = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t u = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += u;
+        }
+        const int64_t tot = __shfl_sync(kFull, x, 31);
+        const int64_t off = x - cnt;
         int64_t goff = 0;
         if (lane == 0) {
-            lb_store(a.chunk_state + g, (g == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)nout);
-            if (g > 0) {
-                goff = (int64_t)lookback(a.chunk_state, g, 1, &a.hdr->status);
-                lb_store(a.chunk_state + g, kFlagIncl | (uint64_t)(goff + nout));
+            lb_store(a.tile_state + t, (t == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
+            if (t > 0) {
+                goff = (int64_t)lookback(a.tile_state, t, 1, &a.hdr->status);
+                lb_store(a.tile_state + t, kFlagIncl | (uint64_t)(goff + tot));
             }
-            if (g == nchunks - 1) a.hdr->nnz_c = goff + nout;
+            if (t == ntiles - 1) a.hdr->nnz_c = goff + tot;
         }
         goff = __shfl_sync(kFull, goff, 0);
-        if (nrows == 0) continue;
-        // ---- write C ----
-        const int nlight = nrows - heavy_last;
-        for (int q = lane; q < nlight; q += 32) {
-            const int64_t obase = goff + S.rout[q];
-            const int64_t rbase = a.row_id[r0 + q] * a.nR;
-            const int j0 = S.rent[q], j1 = S.rent[q + 1];
-            if (!S.rcomplex[q]) {
-                int cur[kMergeRuns], end[kMergeRuns];
-                int nr = 0;
-#pragma unroll
-                for (int i = 0; i < kMergeRuns; ++i) cur[i] = end[i] = 0;
-                for (int jj = j0; jj < j1; ++jj) {
-                    const int s0 = S.epoff[jj], s1 = S.epoff[jj + 1];
-                    if (s0 < s1) {
-#pragma unroll
-                        for (int i = 0; i < kMergeRuns; ++i)
-                            if (i == nr) { cur[i] = s0; end[i] = s1; }
-                        ++nr;
-                    }
+        const int64_t obase = goff + off;
+        const int64_t cbase = rid * a.nR;
+        if (kind == kRowLane) lane_merge_g<true>(a, st, en, av, cbase, a.c_liv + obase, a.c_val + obase);
+        // copies done by the whole warp
+        unsigned wm = __ballot_sync(kFull, kind == kRowCopy || kind == kRowSort || kind == kRowHeavy);
+        while (wm) {
+            const int src = __ffs(wm) - 1;
+            wm &= wm - 1;
+            const int skind = __shfl_sync(kFull, kind, src);
+            const int64_t sob = __shfl_sync(kFull, obase, src);
+            const int64_t scnt = __shfl_sync(kFull, cnt, src);
+            const int64_t scb = __shfl_sync(kFull, cbase, src);
+            if (skind == kRowCopy) {
+                const int64_t b0 = __shfl_sync(kFull, st[0], src);
+                const double v = __shfl_sync(kFull, av[0], src);
+                for (int64_t i = lane; i < scnt; i += 32) {
+                    const int64_t rl = a.r_liv[b0 + i];
+                    a.c_liv[sob + i] = scb + (int64_t)col_of(a.div_n, nR, rl);
+                    a.c_val[sob + i] = v * a.r_val[b0 + i];
                 }
-                lane_merge<true>(S.pcol, S.pval, cur, end, rbase, a.c_liv + obase, a.c_val + obase);
             } else {
-                const int p0 = S.epoff[j0];
-                const int cnt = (int)(S.rout[q + 1] - S.rout[q]);
-                for (int t = 0; t < cnt; ++t) {
-                    a.c_liv[obase + t] = rbase + (int64_t)S.pcol[p0 + t];
-                    a.c_val[obase + t] = S.pval[p0 + t];
+                const int64_t spb = __shfl_sync(kFull, pb, src);
+                bool second = false;
+                if (skind == kRowHeavy) {
+                    const int64_t rr = t * 32 + src;
+                    second = (a.row_hout[rr] >> 62) & 1;
+                }
+                const uint64_t *hk = (second ? a.sk1 : a.sk0) + spb;
+                const double *hv = (second ? a.sv1 : a.sv0) + spb;
+                for (int64_t i = lane; i < scnt; i += 32) {
+                    a.c_liv[sob + i] = scb + (int64_t)hk[i];
+                    a.c_val[sob + i] = hv[i];
                 }
             }
         }
-        if (heavy_last) {
-            const int64_t r = r1 - 1;
-            const int64_t pb = a.row_work[r] - a.row_start[r];
-            const bool second = (heavy_info >> 62) & 1;
-            const uint64_t *hk = (second ? a.sk1 : a.sk0) + pb;
-            const double *hv = (second ? a.sv1 : a.sv0) + pb;
-            const int64_t obase = goff + S.rout[nlight];
-            const int64_t cnt = S.rout[nlight + 1] - S.rout[nlight];
-            const int64_t rbase = a.row_id[r] * a.nR;
-            for (int64_t t = lane; t < cnt; t += 32) {
-                a.c_liv[obase + t] = rbase + (int64_t)hk[t];
-                a.c_val[obase + t] = hv[t];
-            }
-        }
-        __syncwarp();
     }
 }
 
@@ -1215,7 +1179,7 @@ bool same_sig(int order, const int32_t *a, const int32_t *b) {
 // Phase-2 workspace layout (offsets from the end of the phase-1 region).
 struct P2Layout {
     int64_t capc, nchunks_max;
-    size_t chunk_state, chunk_ctr, reduce_state, zero_bytes, chunk_row;
+    size_t chunk_state, chunk_ctr, reduce_state, zero_bytes;
     size_t arr[6];          // cap-sized scratch arrays (8 bytes per entry)
     size_t sop_radix;
     int sop_D, sop_P;
@@ -1573,11 +1537,9 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         int64_t *row_work = reinterpret_cast<int64_t *>(ws + p->off_row_work);
         int64_t *row_hout = reinterpret_cast<int64_t *>(ws + p->off_row_hout);
         int64_t *heavy = reinterpret_cast<int64_t *>(ws + p->off_heavy);
-        int64_t *chunk_row = reinterpret_cast<int64_t *>(p2 + L.chunk_row);
         unsigned long long *nheavy = reinterpret_cast<unsigned long long *>(chunk_ctr + 4);
         TableArgs ta{};
         ta.row_work = row_work;
-        ta.chunk_row = chunk_row;
         ta.heavy_list = heavy;
         ta.nheavy = nheavy;
         ta.cap_rows = p->nnz_l;
@@ -1615,39 +1577,36 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(k_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(HeavySmem));
-            cudaFuncSetAttribute(k_wchunk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(WarpSmem) * (kWarpThreads / 32)));
             attr = true;
         }
         LCO_LAUNCH("k_heavy", s, k_heavy<<<(unsigned)sms, kCT, sizeof(HeavySmem), s>>>(ha));
-        WarpArgs wa{};
-        wa.l_liv = o.l_liv;
-        wa.l_val = o.l_val;
-        wa.r_liv = o.r_liv;
-        wa.r_val = o.r_val;
-        wa.div_k = make_div((uint64_t)p->k);
-        wa.k = p->k;
-        wa.nR = p->nR;
-        wa.mdt = mdt;
-        wa.row_start = row_start;
-        wa.row_id = row_id;
-        wa.row_work = row_work;
-        wa.row_hout = row_hout;
-        wa.chunk_row = chunk_row;
-        wa.c_liv = c_liv;
-        wa.c_val = c_val;
-        wa.cap = cap;
-        wa.sk0 = sk0;
-        wa.sv0 = sv0;
-        wa.sk1 = sk1;
-        wa.sv1 = sv1;
-        wa.chunk_state = chunk_state;
-        wa.chunk_ctr = chunk_ctr;
-        wa.hdr = hdr;
-        const int warps = kWarpThreads / 32;
+        RowsArgs ra{};
+        ra.l_liv = o.l_liv;
+        ra.l_val = o.l_val;
+        ra.r_liv = o.r_liv;
+        ra.r_val = o.r_val;
+        ra.k = p->k;
+        ra.div_n = make_div((uint64_t)p->nR);
+        ra.nR = p->nR;
+        ra.mdt = mdt;
+        ra.row_start = row_start;
+        ra.row_id = row_id;
+        ra.row_work = row_work;
+        ra.row_hout = row_hout;
+        ra.c_liv = c_liv;
+        ra.c_val = c_val;
+        ra.cap = cap;
+        ra.sk0 = sk0;
+        ra.sv0 = sv0;
+        ra.sk1 = sk1;
+        ra.sv1 = sv1;
+        ra.tile_state = chunk_state;
+        ra.tile_ctr = chunk_ctr;
+        ra.hdr = hdr;
+        const int warps = kRowsThreads / 32;
         int64_t grid = (nchunks_max + warps - 1) / warps;
-        if (grid > (int64_t)sms * 4) grid = (int64_t)sms * 4;
-        LCO_LAUNCH("k_wchunk", s, k_wchunk<<<(unsigned)grid, kWarpThreads, sizeof(WarpSmem) * warps, s>>>(wa));
+        if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
+        LCO_LAUNCH("k_rows", s, k_rows<<<(unsigned)grid, kRowsThreads, sizeof(RowsSmem) * warps, s>>>(ra));
     } else {
         SopArgs sa{};
         sa.l_liv = o.l_liv;
@@ -1705,16 +1664,14 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
 P2Layout p2_layout(const lco_plan *p, int64_t cap) {
     P2Layout L{};
     L.capc = cap > 0 ? cap : 1;
-    L.nchunks_max = (p->nnz_l + L.capc + kWarpWork - 1) / kWarpWork + 2;
+    L.nchunks_max = (p->nnz_l + 31) / 32 + 2;   // row tiles of the light-row kernel
     size_t off = 0;
     L.chunk_state = off;
-    L.chunk_ctr = (size_t)L.nchunks_max * 8;   // [0] chunks, [1] reduce tiles, [2] heavy rows, [4..5] heavy count
+    L.chunk_ctr = (size_t)L.nchunks_max * 8;   // [0] row tiles, [1] reduce tiles, [2] heavy rows, [4..5] heavy count
     off += align_up((size_t)L.nchunks_max * 8 + 64);
     L.reduce_state = off;
     off += align_up((size_t)((L.capc + kScanTile - 1) / kScanTile + 2) * 8);
     L.zero_bytes = off;
-    L.chunk_row = off;
-    off += align_up((size_t)(L.nchunks_max + 1) * 8);
     for (int i = 0; i < 6; ++i) {
         L.arr[i] = off;
         off += align_up((size_t)L.capc * 8);
