@@ -49,6 +49,7 @@ KERNEL_SOURCES = {
     "k_csr_rowptr": "paper_1802_02619_gb300/csrc/lco_contract.cu",
     "k_radix_scatter": "paper_1802_02619_gb300/csrc/lco_radix.cu",
     "k_radix_upsweep": "paper_1802_02619_gb300/csrc/lco_radix.cu",
+    "k_radix_hist": "paper_1802_02619_gb300/csrc/lco_radix.cu",
 }
 
 
@@ -373,7 +374,7 @@ def algorithmic_bytes(kernel, step):
         return 8 * nA                         # row work offsets (upper bound: one row per entry)
     if kernel == "k_radix_scatter":
         return 32 * nC                        # read key+value, write key+value
-    if kernel == "k_radix_upsweep":
+    if kernel in ("k_radix_upsweep", "k_radix_hist"):
         return 8 * nC                         # read keys
     if kernel == "k_work_scan":
         return 16 * nA                        # read L's LIVs, write the work prefix

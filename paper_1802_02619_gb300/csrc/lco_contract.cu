@@ -381,18 +381,27 @@ __global__ void __launch_bounds__(kCT) k_work_scan(const __grid_constant__ ScanA
     int64_t wtot, htot;
     const int64_t wex = block_excl<int64_t>(wsum, s_tmp, &wtot);
     const int64_t hex = block_excl<int64_t>(hsum, s_tmp, &htot);
+    // the two look-backs (work, row heads) run in different warps
     if (threadIdx.x == 0) {
         lb_store(a.state_w + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)wtot);
-        lb_store(a.state_h + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)htot);
-        int64_t ew = 0, eh = 0;
+        int64_t ew = 0;
         if (tile > 0) {
             ew = (int64_t)lookback(a.state_w, tile, 1, &a.hdr->status);
             lb_store(a.state_w + tile, kFlagIncl | (uint64_t)(ew + wtot));
+        }
+        s_ew = ew;
+    } else if (threadIdx.x == 32) {
+        lb_store(a.state_h + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)htot);
+        int64_t eh = 0;
+        if (tile > 0) {
             eh = (int64_t)lookback(a.state_h, tile, 1, &a.hdr->status);
             lb_store(a.state_h + tile, kFlagIncl | (uint64_t)(eh + htot));
         }
-        s_ew = ew;
         s_eh = eh;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int64_t ew = s_ew, eh = s_eh;
         const int64_t ntiles = (a.nnz_l + kScanTile - 1) / kScanTile;
         if (tile == ntiles - 1) {
             const int64_t W = ew + wtot, R = eh + htot;

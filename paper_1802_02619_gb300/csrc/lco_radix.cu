@@ -97,13 +97,53 @@ __device__ __forceinline__ int64_t job_n(const RadixJob &j) {
     return n < j.n_cap ? n : j.n_cap;
 }
 
+// Range r of the G ranges: a whole number of tiles, the last one ragged.
+__device__ __forceinline__ void range_of(const RadixJob &j, int64_t n, int64_t r, int64_t &lo, int64_t &hi) {
+    int64_t per = (n + j.G - 1) / j.G;
+    per = (per + kRadixTile - 1) / kRadixTile * kRadixTile;
+    lo = r * per;
+    hi = lo + per;
+    if (lo > n) lo = n;
+    if (hi > n) hi = n;
+}
+
+// Which buffers a pass reads and writes.  Active passes ping-pong between
+// dst and tmp so that the last active pass writes dst; the first active pass
+// reads the source (and re-linearises it).  With no active pass, the last
+// pass copies the re-linearised source to dst.
+struct PassIO {
+    const int64_t *sl;
+    const double *sv;
+    int64_t *dl;
+    double *dv;
+    bool run, first, copy;
+};
+
+__device__ __forceinline__ PassIO pass_io(const RadixJob &j, int pass) {
+    PassIO io{};
+    const int Q = j.active[16];
+    const bool act = j.active[pass] != 0;
+    io.copy = (Q == 0) && (pass == j.P - 1);
+    io.run = act || io.copy;
+    int q = 0;
+    for (int p = 0; p < pass; ++p) q += j.active[p] != 0;
+    io.first = io.copy || q == 0;
+    const bool prev_in_dst = q > 0 && ((Q - 1 - (q - 1)) & 1) == 0;
+    io.sl = io.first ? j.src_liv : (prev_in_dst ? j.dst_liv : j.tmp_liv);
+    io.sv = io.first ? j.src_val : (prev_in_dst ? j.dst_val : j.tmp_val);
+    const bool to_dst = io.copy || ((Q - 1 - q) & 1) == 0;
+    io.dl = to_dst ? j.dst_liv : j.tmp_liv;
+    io.dv = to_dst ? j.dst_val : j.tmp_val;
+    return io;
+}
+
 // ---------------------------------------------------------------------------
-// One read of the keys: every pass's digit histogram.  Also clears the
-// look-back state of all passes.  The last block to finish turns the
-// histograms into exclusive digit offsets, flags passes whose digit is
-// constant (nothing to do), and resets the counters for the next call.
+// One read of the source keys: every pass's digit histogram, per range
+// (counts_src) and in total (ghist).  The last block to finish turns the
+// totals into exclusive digit offsets, flags passes whose digit is constant
+// (nothing to do) and leaves ghist zeroed for the next call.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const __grid_constant__ RadixJob j, int64_t state_words) {
+__global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const __grid_constant__ RadixJob j) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem_raw);
     __shared__ int s_last;
@@ -113,21 +153,21 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const __grid_co
     __syncthreads();
 
     const int64_t n = job_n(j);
-    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    int64_t lo, hi;
+    range_of(j, n, blockIdx.x, lo, hi);
     const uint32_t mask = (uint32_t)NB - 1;
-    for (int64_t e = gtid; e < n; e += gsz) {
-        int64_t liv = relin(j.relin, j.src_liv[e]);
-        uint64_t key = divu(j.key_div, (uint64_t)liv);
+    for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+        const int64_t liv = relin(j.relin, j.src_liv[e]);
+        const uint64_t key = divu(j.key_div, (uint64_t)liv);
         for (int p = 0; p < j.P; ++p)
             atomicAdd(&s_hist[p * NB + (uint32_t)((key >> (p * j.D)) & mask)], 1u);
     }
-    // clear look-back state for the scatter passes
-    for (int64_t w = gtid; w < state_words; w += gsz) j.state[w] = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < nh; i += blockDim.x)
-        if (s_hist[i]) atomicAdd(reinterpret_cast<unsigned long long *>(&j.ghist[i]),
-                                 (unsigned long long)s_hist[i]);
+    for (int i = threadIdx.x; i < nh; i += blockDim.x) {
+        const int p = i / NB, d = i - p * NB;
+        j.counts_src[((int64_t)p * j.G + blockIdx.x) * NB + d] = s_hist[i];
+        if (s_hist[i]) atomicAdd(reinterpret_cast<unsigned long long *>(&j.ghist[i]), (unsigned long long)s_hist[i]);
+    }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = (atomicAdd(&j.counters[8], 1u) == gridDim.x - 1);
@@ -158,162 +198,185 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const __grid_co
     }
     if (threadIdx.x == 0) {
         j.active[16] = nactive;
-        for (int p = 0; p < kMaxPasses; ++p) j.counters[p] = 0;
         j.counters[8] = 0;
     }
 }
 
-// ---------------------------------------------------------------------------
-// One stable scatter pass over a tile of kRadixTile elements.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kRadixThreads, 1) k_radix_scatter(const __grid_constant__ RadixJob j, int pass, int64_t tiles_cap) {
+// Per-range digit histogram of the buffer a later pass reads.
+__global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const __grid_constant__ RadixJob j, int pass) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem_raw);
+    const PassIO io = pass_io(j, pass);
+    if (!io.run || io.first) return;
+    const int NB = 1 << j.D;
+    for (int i = threadIdx.x; i < NB; i += blockDim.x) s_hist[i] = 0;
+    __syncthreads();
+    const int64_t n = job_n(j);
+    int64_t lo, hi;
+    range_of(j, n, blockIdx.x, lo, hi);
+    const uint32_t mask = (uint32_t)NB - 1;
+    const int shift = pass * j.D;
+    for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+        const uint64_t key = divu(j.key_div, (uint64_t)io.sl[e]);
+        atomicAdd(&s_hist[(uint32_t)(key >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < NB; d += blockDim.x) j.counts_hist[(int64_t)blockIdx.x * NB + d] = s_hist[d];
+}
+
+// roffs[r][d] = offs[pass][d] + sum of counts[r'][d] over ranges r' < r.
+// One warp per digit.
+__global__ void __launch_bounds__(kRadixThreads) k_radix_offsets(const __grid_constant__ RadixJob j, int pass) {
+    const PassIO io = pass_io(j, pass);
+    if (!io.run || io.copy) return;
+    const int NB = 1 << j.D;
+    const int lane = threadIdx.x & 31;
+    const int d = blockIdx.x * kRadixWarps + (threadIdx.x >> 5);
+    if (d >= NB) return;
+    const uint32_t *cnt = io.first ? j.counts_src + (int64_t)pass * j.G * NB : j.counts_hist;
+    uint64_t carry = j.offs[pass * NB + d];
+    for (int r0 = 0; r0 < j.G; r0 += 32) {
+        const int r = r0 + lane;
+        const uint64_t c = r < j.G ? cnt[(int64_t)r * NB + d] : 0;
+        uint64_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t u = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += u;
+        }
+        if (r < j.G) j.roffs[(int64_t)r * NB + d] = carry + x - c;
+        carry += __shfl_sync(kFull, x, 31);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One stable scatter pass: CTA r walks range r tile by tile (kRadixTile
+// elements), ranking each tile with warp ballots and placing it from running
+// per-digit offsets; the tile is staged in shared memory so that the writes
+// of each digit's run are contiguous.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRadixThreads, 2) k_radix_scatter(const __grid_constant__ RadixJob j, int pass) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const PassIO io = pass_io(j, pass);
+    if (!io.run) return;
     const int NB = 1 << j.D;
     int64_t *s_key = reinterpret_cast<int64_t *>(smem_raw);
     double *s_val = reinterpret_cast<double *>(s_key + kRadixTile);
-    int64_t *s_gbase = reinterpret_cast<int64_t *>(s_val + kRadixTile);
+    int64_t *s_run = reinterpret_cast<int64_t *>(s_val + kRadixTile);
+    int64_t *s_gbase = s_run + NB;
     uint32_t *s_whist = reinterpret_cast<uint32_t *>(s_gbase + NB);
     uint32_t *s_tstart = s_whist + kRadixWarps * NB;
     uint16_t *s_dig = reinterpret_cast<uint16_t *>(s_tstart + NB);
-    __shared__ int64_t s_tile;
-
-    const int Q = j.active[16];
-    const bool act = j.active[pass] != 0;
-    const bool copy_mode = (Q == 0) && (pass == j.P - 1);
-    if (!act && !copy_mode) return;
-    int q = 0;
-    for (int p = 0; p < pass; ++p) q += j.active[p] != 0;
 
     const int64_t n = job_n(j);
-    const int64_t ntiles = (n + kRadixTile - 1) / kRadixTile;
-    if (threadIdx.x == 0) s_tile = atomicAdd(&j.counters[pass], 1u);
-    __syncthreads();
-    const int64_t tile = s_tile;
-    if (tile >= ntiles) return;
-
-    const bool first = copy_mode || q == 0;
-    const int64_t *src_liv = first ? j.src_liv : (((Q - 1 - (q - 1)) & 1) == 0 ? j.dst_liv : j.tmp_liv);
-    const double *src_val = first ? j.src_val : (((Q - 1 - (q - 1)) & 1) == 0 ? j.dst_val : j.tmp_val);
-    int64_t *dst_liv = copy_mode || (((Q - 1 - q) & 1) == 0) ? j.dst_liv : j.tmp_liv;
-    double *dst_val = copy_mode || (((Q - 1 - q) & 1) == 0) ? j.dst_val : j.tmp_val;
-
-    const int64_t tile_base = tile * kRadixTile;
-    const int tile_n = (int)((n - tile_base) < (int64_t)kRadixTile ? (n - tile_base) : (int64_t)kRadixTile);
-
-    if (copy_mode) {
-        for (int i = threadIdx.x; i < tile_n; i += blockDim.x) {
-            int64_t e = tile_base + i;
-            dst_liv[e] = relin(j.relin, src_liv[e]);
-            dst_val[e] = src_val[e];
+    int64_t lo, hi;
+    range_of(j, n, blockIdx.x, lo, hi);
+    if (io.copy) {
+        for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+            io.dl[e] = relin(j.relin, io.sl[e]);
+            io.dv[e] = io.sv[e];
         }
         return;
     }
-
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t mask = (uint32_t)NB - 1;
     const int shift = pass * j.D;
-
-    for (int i = tid; i < kRadixWarps * NB; i += kRadixThreads) s_whist[i] = 0;
-
-    int64_t keys[kRadixItems];
-    double vals[kRadixItems];
-    uint32_t digs[kRadixItems];
-    const int64_t wbase = tile_base + warp * (32 * kRadixItems);
-#pragma unroll
-    for (int i = 0; i < kRadixItems; ++i) {
-        int64_t e = wbase + i * 32 + lane;
-        if (e < n) {
-            int64_t k = src_liv[e];
-            if (first) k = relin(j.relin, k);
-            keys[i] = k;
-            vals[i] = src_val[e];
-            digs[i] = (uint32_t)((divu(j.key_div, (uint64_t)k) >> shift) & mask);
-        } else {
-            keys[i] = 0;
-            vals[i] = 0.0;
-            digs[i] = 0;
-        }
-    }
-    __syncthreads();
-
-    // warp-level stable ranking (multi-split by ballots); the rank is packed
-    // above the digit (digit < 2^11, rank < 2^13) to keep registers low
-    uint32_t *wh = s_whist + warp * NB;
+    for (int d = tid; d < NB; d += kRadixThreads) s_run[d] = (int64_t)j.roffs[(int64_t)blockIdx.x * NB + d];
     const unsigned lt = lanemask_lt();
-#pragma unroll
-    for (int i = 0; i < kRadixItems; ++i) {
-        const int64_t e = wbase + i * 32 + lane;
-        const bool valid = e < n;
-        const unsigned vmask = __ballot_sync(kFull, valid);
-        unsigned peers = vmask;
-        const uint32_t d = digs[i];
-        for (int b = 0; b < j.D; ++b) {
-            const unsigned bit = (d >> b) & 1u;
-            const unsigned bal = __ballot_sync(kFull, bit);
-            peers &= bit ? bal : ~bal;
-        }
-        const int leader = valid ? (__ffs(peers) - 1) : lane;
-        uint32_t basev = 0;
-        if (valid && lane == leader) {
-            basev = wh[d];
-            wh[d] = basev + (uint32_t)__popc(peers);
-        }
-        basev = __shfl_sync(kFull, basev, leader);
-        digs[i] = d | ((basev + (uint32_t)__popc(peers & lt)) << 16);
-        __syncwarp();
-    }
-    __syncthreads();
+    uint32_t *wh = s_whist + warp * NB;
 
-    // per-digit counts: exclusive over warps, total per tile; publish aggregates
-    uint64_t *st_pass = j.state + (int64_t)pass * tiles_cap * NB;
-    for (int d = tid; d < NB; d += kRadixThreads) {
-        uint32_t run = 0;
-        for (int w = 0; w < kRadixWarps; ++w) {
-            uint32_t c = s_whist[w * NB + d];
-            s_whist[w * NB + d] = run;
-            run += c;
-        }
-        s_tstart[d] = run;
-        lb_store(st_pass + tile * NB + d, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)run);
-    }
-    __syncthreads();
-    for (int d = tid; d < NB; d += kRadixThreads) {
-        uint64_t excl = 0;
-        if (tile > 0) {
-            excl = lookback(st_pass + d, tile, NB, j.status);
-            lb_store(st_pass + tile * NB + d, kFlagIncl | (excl + s_tstart[d]));
-        }
-        s_gbase[d] = (int64_t)(j.offs[pass * NB + d] + excl);
-    }
-    __syncthreads();
-    block_exscan_u32(s_tstart, NB);
-    for (int d = tid; d < NB; d += kRadixThreads) s_gbase[d] -= (int64_t)s_tstart[d];
-    __syncthreads();
-
+    for (int64_t tile_base = lo; tile_base < hi; tile_base += kRadixTile) {
+        const int tile_n = (int)((hi - tile_base) < (int64_t)kRadixTile ? (hi - tile_base) : (int64_t)kRadixTile);
+        for (int i = tid; i < kRadixWarps * NB; i += kRadixThreads) s_whist[i] = 0;
+        int64_t keys[kRadixItems];
+        double vals[kRadixItems];
+        uint32_t digs[kRadixItems];
+        const int64_t wbase = tile_base + warp * (32 * kRadixItems);
 #pragma unroll
-    for (int i = 0; i < kRadixItems; ++i) {
-        const int64_t e = wbase + i * 32 + lane;
-        if (e < n) {
-            const uint32_t d = digs[i] & 0xffffu;
-            const uint32_t lp = s_tstart[d] + wh[d] + (digs[i] >> 16);
-            s_key[lp] = keys[i];
-            s_val[lp] = vals[i];
-            s_dig[lp] = (uint16_t)d;
+        for (int i = 0; i < kRadixItems; ++i) {
+            const int64_t e = wbase + i * 32 + lane;
+            if (e < hi) {
+                int64_t k = io.sl[e];
+                if (io.first) k = relin(j.relin, k);
+                keys[i] = k;
+                vals[i] = io.sv[e];
+                digs[i] = (uint32_t)((divu(j.key_div, (uint64_t)k) >> shift) & mask);
+            } else {
+                keys[i] = 0;
+                vals[i] = 0.0;
+                digs[i] = 0;
+            }
         }
-    }
-    __syncthreads();
-    for (int i = tid; i < tile_n; i += kRadixThreads) {
-        const uint32_t d = s_dig[i];
-        const int64_t g = s_gbase[d] + i;
-        dst_liv[g] = s_key[i];
-        dst_val[g] = s_val[i];
+        __syncthreads();
+        // warp-level stable ranking (multi-split by ballots); the rank is packed
+        // above the digit (digit < 2^11, rank < 2^13) to keep registers low
+#pragma unroll
+        for (int i = 0; i < kRadixItems; ++i) {
+            const int64_t e = wbase + i * 32 + lane;
+            const bool valid = e < hi;
+            unsigned peers = __ballot_sync(kFull, valid);
+            const uint32_t d = digs[i];
+            for (int b = 0; b < j.D; ++b) {
+                const unsigned bit = (d >> b) & 1u;
+                const unsigned bal = __ballot_sync(kFull, bit);
+                peers &= bit ? bal : ~bal;
+            }
+            const int leader = valid ? (__ffs(peers) - 1) : lane;
+            uint32_t basev = 0;
+            if (valid && lane == leader) {
+                basev = wh[d];
+                wh[d] = basev + (uint32_t)__popc(peers);
+            }
+            basev = __shfl_sync(kFull, basev, leader);
+            digs[i] = d | ((basev + (uint32_t)__popc(peers & lt)) << 16);
+            __syncwarp();
+        }
+        __syncthreads();
+        // per digit: exclusive offsets of the warps, tile count
+        for (int d = tid; d < NB; d += kRadixThreads) {
+            uint32_t run = 0;
+            for (int w = 0; w < kRadixWarps; ++w) {
+                const uint32_t c = s_whist[w * NB + d];
+                s_whist[w * NB + d] = run;
+                run += c;
+            }
+            s_tstart[d] = run;
+        }
+        __syncthreads();
+        // global start of each digit's run in this tile, then local starts
+        for (int d = tid; d < NB; d += kRadixThreads) {
+            s_gbase[d] = s_run[d];
+            s_run[d] += s_tstart[d];
+        }
+        __syncthreads();
+        block_exscan_u32(s_tstart, NB);
+        for (int d = tid; d < NB; d += kRadixThreads) s_gbase[d] -= (int64_t)s_tstart[d];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kRadixItems; ++i) {
+            const int64_t e = wbase + i * 32 + lane;
+            if (e < hi) {
+                const uint32_t d = digs[i] & 0xffffu;
+                const uint32_t lp = s_tstart[d] + wh[d] + (digs[i] >> 16);
+                s_key[lp] = keys[i];
+                s_val[lp] = vals[i];
+                s_dig[lp] = (uint16_t)d;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < tile_n; i += kRadixThreads) {
+            const uint32_t d = s_dig[i];
+            const int64_t g = s_gbase[d] + i;
+            io.dl[g] = s_key[i];
+            io.dv[g] = s_val[i];
+        }
+        __syncthreads();
     }
 }
 
 size_t scatter_smem_bytes(int D) {
     size_t NB = (size_t)1 << D;
-    return (size_t)kRadixTile * 16 + NB * 8 + (size_t)kRadixWarps * NB * 4 + NB * 4 +
-           (size_t)kRadixTile * 2;
+    return (size_t)kRadixTile * 16 + NB * 16 + (size_t)kRadixWarps * NB * 4 + NB * 4 + (size_t)kRadixTile * 2;
 }
 
 size_t upsweep_smem_bytes(int D, int P) {
@@ -340,25 +403,41 @@ int radix_sm_count() {
 // the histogram table zeroed, and a zero-filled region starts that way.
 constexpr size_t kHistTableBytes = (size_t)kMaxPasses * ((size_t)1 << kMaxDigitBits) * 8;
 
+int radix_ranges(int64_t n_cap) {
+    const int64_t tiles = (n_cap + kRadixTile - 1) / kRadixTile;
+    int64_t g = (tiles + 3) / 4;                 // at least four tiles per range
+    const int64_t gmax = 2 * (int64_t)radix_sm_count();
+    if (g > gmax) g = gmax;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
 size_t radix_state_bytes(int64_t n_cap, int D, int P) {
     const size_t NB = (size_t)1 << D;
-    const size_t tiles = (size_t)((n_cap + kRadixTile - 1) / kRadixTile);
+    const size_t G = (size_t)radix_ranges(n_cap);
     size_t b = 0;
     b += align_up(kHistTableBytes);      // ghist
     b += align_up(kHistTableBytes);      // offs
     b += align_up(32 * 4);               // active
-    b += align_up((size_t)P * (tiles ? tiles : 1) * NB * 8);   // look-back state
+    b += align_up((size_t)P * G * NB * 4);   // counts_src
+    b += align_up(G * NB * 4);           // counts_hist
+    b += align_up(G * NB * 8);           // roffs
     return b;
 }
 
 size_t radix_hist_table_bytes() { return align_up(kHistTableBytes); }
 
 void radix_carve(RadixJob &job, char *region) {
+    const size_t NB = (size_t)1 << job.D;
+    job.G = radix_ranges(job.n_cap);
+    const size_t G = (size_t)job.G;
     char *p = region;
     job.ghist = reinterpret_cast<uint64_t *>(p); p += align_up(kHistTableBytes);
     job.offs = reinterpret_cast<uint64_t *>(p); p += align_up(kHistTableBytes);
     job.active = reinterpret_cast<int32_t *>(p); p += align_up(32 * 4);
-    job.state = reinterpret_cast<uint64_t *>(p);
+    job.counts_src = reinterpret_cast<uint32_t *>(p); p += align_up((size_t)job.P * G * NB * 4);
+    job.counts_hist = reinterpret_cast<uint32_t *>(p); p += align_up(G * NB * 4);
+    job.roffs = reinterpret_cast<uint64_t *>(p);
 }
 
 cudaError_t radix_enqueue(const RadixJob &job, cudaStream_t stream) {
@@ -371,17 +450,21 @@ cudaError_t radix_enqueue(const RadixJob &job, cudaStream_t stream) {
         attr_done = true;
     }
     if (job.n_cap <= 0) return cudaSuccess;
-    const int64_t tiles_cap = (job.n_cap + kRadixTile - 1) / kRadixTile;
-    const int64_t NB = (int64_t)1 << job.D;
-    const int64_t state_words = (int64_t)job.P * tiles_cap * NB;
-    int up_grid = radix_sm_count() * kUpsweepCtasPerSm;
-    const int64_t want = (job.n_cap + kRadixThreads * 8 - 1) / (kRadixThreads * 8);
-    if (want < up_grid) up_grid = (int)(want > 0 ? want : 1);
-    LCO_LAUNCH("k_radix_upsweep", stream, k_radix_upsweep<<<up_grid, kRadixThreads, upsweep_smem_bytes(job.D, job.P), stream>>>(job, state_words));
+    const unsigned G = (unsigned)job.G;
+    const int NB = 1 << job.D;
+    LCO_LAUNCH("k_radix_upsweep", stream,
+               k_radix_upsweep<<<G, kRadixThreads, upsweep_smem_bytes(job.D, job.P), stream>>>(job));
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     for (int p = 0; p < job.P; ++p) {
-        LCO_LAUNCH("k_radix_scatter", stream, k_radix_scatter<<<(unsigned)tiles_cap, kRadixThreads, scatter_smem_bytes(job.D), stream>>>(job, p, tiles_cap));
+        if (p > 0) {
+            LCO_LAUNCH("k_radix_hist", stream,
+                       k_radix_hist<<<G, kRadixThreads, (size_t)NB * 4, stream>>>(job, p));
+        }
+        LCO_LAUNCH("k_radix_offsets", stream,
+                   k_radix_offsets<<<(unsigned)((NB + kRadixWarps - 1) / kRadixWarps), kRadixThreads, 0, stream>>>(job, p));
+        LCO_LAUNCH("k_radix_scatter", stream,
+                   k_radix_scatter<<<G, kRadixThreads, scatter_smem_bytes(job.D), stream>>>(job, p));
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
     }

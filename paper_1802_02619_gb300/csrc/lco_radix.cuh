@@ -2,12 +2,15 @@
 //
 // Used for the permutation of Sec. 4 (keys are re-linearised LIVs shaved by
 // the resting suffix, Sec. 4.1) and for sorting product lists by output LIV
-// (SOP, Sec. 5.2.5).  One launch computes every digit histogram in a single
-// read; each following launch is one stable scatter pass.  Tiles are ranked
-// with warp ballots (a multi-split) and placed with decoupled look-back
-// (Merrill & Garland 2016; the single-pass "Onesweep" arrangement of Adinets
-// & Merrill 2022).  Passes whose digit is the same for every element are
-// detected on the device and skipped.
+// (SOP, Sec. 5.2.5).  The input is cut into G contiguous ranges, one CTA
+// each.  One launch reads the keys once and computes every pass's digit
+// histogram, globally and per range.  A pass is then: per-range digit
+// offsets (a scan down each digit column), and a scatter in which each CTA
+// walks its range tile by tile, ranking a tile with warp ballots (a
+// multi-split) and advancing running per-digit offsets, so no CTA waits on
+// another.  Passes after the first non-skipped one histogram the
+// intermediate buffer first.  Passes whose digit is the same for every
+// element are detected on the device and skipped.
 #pragma once
 
 #include "lco_internal.cuh"
@@ -15,7 +18,7 @@
 namespace lco {
 
 constexpr int kRadixThreads = 256;
-constexpr int kRadixItems = 16;
+constexpr int kRadixItems = 8;
 constexpr int kRadixTile = kRadixThreads * kRadixItems;
 constexpr int kRadixWarps = kRadixThreads / 32;
 constexpr int kMaxDigitBits = 11;
@@ -27,9 +30,10 @@ struct RadixJob {
     DivU64 key_div;        // key = relin(liv) div key_div
     int32_t D;             // digit bits
     int32_t P;             // passes
+    int32_t G;             // input ranges (one CTA each), fixed from n_cap
     int64_t n_host;        // element count, or
     const int64_t *n_dev;  // device element count (overrides n_host when set)
-    int64_t n_cap;         // upper bound on the element count (sizes grids and state)
+    int64_t n_cap;         // upper bound on the element count (sizes grids and tables)
     const int64_t *src_liv;
     const double *src_val;
     int64_t *dst_liv;
@@ -37,11 +41,13 @@ struct RadixJob {
     int64_t *tmp_liv;
     double *tmp_val;
     // workspace pieces
-    uint64_t *ghist;       // [P][NB]
-    uint64_t *offs;        // [P][NB]
+    uint64_t *ghist;       // [P][NB] global digit counts (left zeroed after use)
+    uint64_t *offs;        // [P][NB] exclusive digit offsets
     int32_t *active;       // [kMaxPasses] + count at [16]
-    uint64_t *state;       // [P][tiles][NB]
-    uint32_t *counters;    // [kMaxPasses] tile counters + [8] done counter
+    uint32_t *counts_src;  // [P][G][NB] per-range counts over the source order
+    uint32_t *counts_hist; // [G][NB] per-range counts before a later pass
+    uint64_t *roffs;       // [G][NB] start of each (range, digit) in the output of a pass
+    uint32_t *counters;    // [8] "last block" counter
     int32_t *status;
 };
 
@@ -54,6 +60,8 @@ inline void radix_digits(int key_bits, int *D, int *P) {
     *P = p;
 }
 
+// Number of input ranges for up to n_cap elements.
+int radix_ranges(int64_t n_cap);
 // Bytes of workspace the engine needs for up to n_cap elements (excluding the
 // header and excluding the tmp buffers when those are supplied elsewhere).
 size_t radix_state_bytes(int64_t n_cap, int D, int P);
