@@ -281,18 +281,18 @@ __global__ void __launch_bounds__(kCT) k_dcsr_build(const __grid_constant__ Dcsr
     }
     int64_t tot;
     int64_t ex = block_excl<int64_t>((int64_t)heads, s_tmp, &tot);
-    if (threadIdx.x == 0) {
-        lb_store(a.state + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
+    if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) lb_store(a.state + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
         int64_t e = 0;
-        if (tile > 0) {
-            e = (int64_t)lookback(a.state, tile, 1, &a.hdr->status);
-            lb_store(a.state + tile, kFlagIncl | (uint64_t)(e + tot));
-        }
-        s_excl = e;
-        const int64_t ntiles = (a.nnz + kScanTile - 1) / kScanTile;
-        if (tile == ntiles - 1) {
-            a.row_ptr[e + tot] = a.nnz;
-            a.hdr->nzr_b = e + tot;
+        if (tile > 0) e = (int64_t)lookback_warp(a.state, tile, &a.hdr->status);
+        if (threadIdx.x == 0) {
+            if (tile > 0) lb_store(a.state + tile, kFlagIncl | (uint64_t)(e + tot));
+            s_excl = e;
+            const int64_t ntiles = (a.nnz + kScanTile - 1) / kScanTile;
+            if (tile == ntiles - 1) {
+                a.row_ptr[e + tot] = a.nnz;
+                a.hdr->nzr_b = e + tot;
+            }
         }
     }
     __syncthreads();
@@ -381,23 +381,18 @@ __global__ void __launch_bounds__(kCT) k_work_scan(const __grid_constant__ ScanA
     int64_t wtot, htot;
     const int64_t wex = block_excl<int64_t>(wsum, s_tmp, &wtot);
     const int64_t hex = block_excl<int64_t>(hsum, s_tmp, &htot);
-    // the two look-backs (work, row heads) run in different warps
-    if (threadIdx.x == 0) {
-        lb_store(a.state_w + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)wtot);
-        int64_t ew = 0;
-        if (tile > 0) {
-            ew = (int64_t)lookback(a.state_w, tile, 1, &a.hdr->status);
-            lb_store(a.state_w + tile, kFlagIncl | (uint64_t)(ew + wtot));
+    // the two look-backs (work, row heads) run in warps 0 and 1
+    if (threadIdx.x < 64) {
+        const bool hw = threadIdx.x >= 32;
+        uint64_t *st = hw ? a.state_h : a.state_w;
+        const int64_t tv = hw ? htot : wtot;
+        if ((threadIdx.x & 31) == 0) lb_store(st + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tv);
+        int64_t ex = 0;
+        if (tile > 0) ex = (int64_t)lookback_warp(st, tile, &a.hdr->status);
+        if ((threadIdx.x & 31) == 0) {
+            if (tile > 0) lb_store(st + tile, kFlagIncl | (uint64_t)(ex + tv));
+            if (hw) s_eh = ex; else s_ew = ex;
         }
-        s_ew = ew;
-    } else if (threadIdx.x == 32) {
-        lb_store(a.state_h + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)htot);
-        int64_t eh = 0;
-        if (tile > 0) {
-            eh = (int64_t)lookback(a.state_h, tile, 1, &a.hdr->status);
-            lb_store(a.state_h + tile, kFlagIncl | (uint64_t)(eh + htot));
-        }
-        s_eh = eh;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -838,9 +833,74 @@ __device__ int warp_sort_reduce(uint64_t *col, double *val, int n) {
     return outc;
 }
 
-enum RowKind { kRowNone = -1, kRowLane = 0, kRowCopy = 1, kRowSort = 2, kRowHeavy = 3 };
+enum RowKind { kRowNone = -1, kRowLane = 0, kRowCopy = 1, kRowSort = 2, kRowHeavy = 3, kRowNet = 4 };
 
-__global__ void __launch_bounds__(kRowsThreads) k_rows(const __grid_constant__ RowsArgs a) {
+// Small rows (at most kNetEnt L entries and kNetProd products) are sorted in
+// registers: the products are gathered into kNetProd slots (independent
+// loads), sorted by an unrolled bitonic network and kept in registers until
+// the row's place in C is known.  KeyT is uint32_t when every column fits.
+constexpr int kNetEnt = 8;
+constexpr int kNetProd = 16;
+
+template <typename KeyT>
+__device__ __forceinline__ void net_sort(KeyT (&k)[kNetProd], double (&v)[kNetProd]) {
+#pragma unroll
+    for (int kk = 2; kk <= kNetProd; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int i = 0; i < kNetProd; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & kk) == 0;
+                    const bool sw = up ? (k[i] > k[l]) : (k[i] < k[l]);
+                    const KeyT tk = sw ? k[l] : k[i];
+                    k[l] = sw ? k[i] : k[l];
+                    k[i] = tk;
+                    const double tv = sw ? v[l] : v[i];
+                    v[l] = sw ? v[i] : v[l];
+                    v[i] = tv;
+                }
+            }
+        }
+    }
+}
+
+// Collects the non-empty runs (the B rows selected by the L entries
+// [es, ee) of row rid); returns the number of non-empty runs (the first
+// kMergeRuns are stored).
+__device__ __forceinline__ int collect_runs(const RowsArgs &a, int64_t es, int64_t ee, int64_t rid,
+                                            int64_t (&st)[kMergeRuns], int64_t (&en)[kMergeRuns],
+                                            double (&av)[kMergeRuns]) {
+    int nr = 0;
+    const int64_t rbase = rid * a.k;
+#pragma unroll
+    for (int i = 0; i < kMergeRuns; ++i) {
+        st[i] = en[i] = 0;
+        av[i] = 0.0;
+    }
+    for (int64_t e = es; e < ee; ++e) {
+        int64_t b0, len;
+        mdt_lookup(a.mdt, a.l_liv[e] - rbase, b0, len);
+        if (len > 0) {
+            if (nr < kMergeRuns) {
+                const double v = a.l_val[e];
+#pragma unroll
+                for (int i = 0; i < kMergeRuns; ++i)
+                    if (i == nr) {
+                        st[i] = b0;
+                        en[i] = b0 + len;
+                        av[i] = v;
+                    }
+            }
+            ++nr;
+        }
+    }
+    return nr;
+}
+
+template <typename KeyT>
+__global__ void __launch_bounds__(kRowsThreads, 2) k_rows(const __grid_constant__ RowsArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     RowsSmem &S = reinterpret_cast<RowsSmem *>(smem_raw)[warp];
@@ -851,6 +911,7 @@ __global__ void __launch_bounds__(kRowsThreads) k_rows(const __grid_constant__ R
         }
         return;
     }
+    constexpr KeyT kNone = (KeyT)~(KeyT)0;
     const int64_t nrows = a.hdr->nrows_l;
     const int64_t ntiles = (nrows + 31) / 32;
     const uint64_t nR = (uint64_t)a.nR;
@@ -862,13 +923,10 @@ __global__ void __launch_bounds__(kRowsThreads) k_rows(const __grid_constant__ R
         const int64_t r = t * 32 + lane;
         int kind = kRowNone;
         int64_t es = 0, ee = 0, rid = 0, pb = 0, work = 0;
-        int64_t st[kMergeRuns], en[kMergeRuns];
-        double av[kMergeRuns];
-#pragma unroll
-        for (int i = 0; i < kMergeRuns; ++i) {
-            st[i] = en[i] = 0;
-            av[i] = 0.0;
-        }
+        int64_t copy_b0 = 0;
+        double copy_a = 0.0;
+        KeyT nk[kNetProd];
+        double nv[kNetProd];
         int64_t cnt = 0;
         if (r < nrows) {
             es = a.row_start[r];
@@ -877,38 +935,74 @@ __global__ void __launch_bounds__(kRowsThreads) k_rows(const __grid_constant__ R
             work = a.row_work[r + 1] - w0;
             rid = a.row_id[r];
             pb = w0 - es;
+            const int64_t nent = ee - es;
+            const int64_t frow = work - nent;
             if (work > kHeavyWork) {
                 kind = kRowHeavy;
                 cnt = a.row_hout[r] & ((1ll << 62) - 1);
-            } else {
-                // collect the non-empty runs (B rows) of this row
-                int nr = 0;
+            } else if (nent <= kNetEnt && frow <= kNetProd) {
+                // ---- register network path ----
+                kind = kRowNet;
                 const int64_t rbase = rid * a.k;
-                for (int64_t e = es; e < ee; ++e) {
-                    const int64_t c = a.l_liv[e] - rbase;
-                    int64_t b0, len;
-                    mdt_lookup(a.mdt, c, b0, len);
-                    if (len > 0) {
-                        if (nr < kMergeRuns) {
-                            const double v = a.l_val[e];
+                int64_t b0[kNetEnt];
+                int pre[kNetEnt + 1];
 #pragma unroll
-                            for (int i = 0; i < kMergeRuns; ++i)
-                                if (i == nr) {
-                                    st[i] = b0;
-                                    en[i] = b0 + len;
-                                    av[i] = v;
-                                }
-                        }
-                        ++nr;
+                for (int s2 = 0; s2 < kNetEnt; ++s2) {
+                    b0[s2] = 0;
+                    pre[s2] = 0;
+                }
+                pre[kNetEnt] = 0;
+                int64_t lv[kNetEnt];
+#pragma unroll
+                for (int s2 = 0; s2 < kNetEnt; ++s2) lv[s2] = s2 < nent ? a.l_liv[es + s2] : 0;
+                int run = 0;
+#pragma unroll
+                for (int s2 = 0; s2 < kNetEnt; ++s2) {
+                    int64_t len = 0;
+                    if (s2 < nent) mdt_lookup(a.mdt, lv[s2] - rbase, b0[s2], len);
+                    pre[s2] = run;
+                    run += (int)len;
+                }
+                pre[kNetEnt] = run;
+#pragma unroll
+                for (int q = 0; q < kNetProd; ++q) {
+                    nk[q] = kNone;
+                    nv[q] = 0.0;
+                    if (q < run) {
+                        int sel = 0;
+#pragma unroll
+                        for (int s2 = 1; s2 < kNetEnt; ++s2) sel = (pre[s2] <= q) ? s2 : sel;
+                        int64_t bsel = b0[0];
+                        int psel = pre[0];
+#pragma unroll
+                        for (int s2 = 1; s2 < kNetEnt; ++s2)
+                            if (s2 == sel) {
+                                bsel = b0[s2];
+                                psel = pre[s2];
+                            }
+                        const int64_t b = bsel + (q - psel);
+                        nk[q] = (KeyT)col_of(a.div_n, nR, a.r_liv[b]);
+                        nv[q] = a.l_val[es + sel] * a.r_val[b];
                     }
                 }
-                const int64_t frow = work - (ee - es);
+                net_sort<KeyT>(nk, nv);
+                int u = 0;
+#pragma unroll
+                for (int q = 0; q < kNetProd; ++q)
+                    u += (nk[q] != kNone) && (q == 0 || nk[q] != nk[q - 1]);
+                cnt = u;
+            } else {
+                int64_t st[kMergeRuns], en[kMergeRuns];
+                double av[kMergeRuns];
+                const int nr = collect_runs(a, es, ee, rid, st, en, av);
                 if (nr <= kMergeRuns && frow <= kLaneProd) {
                     kind = kRowLane;
                     cnt = lane_merge_g<false>(a, st, en, av, 0, nullptr, nullptr);
                 } else if (nr == 1) {
                     kind = kRowCopy;
                     cnt = en[0] - st[0];
+                    copy_b0 = st[0];
+                    copy_a = av[0];
                 } else {
                     kind = kRowSort;
                 }
@@ -935,8 +1029,8 @@ __global__ void __launch_bounds__(kRowsThreads) k_rows(const __grid_constant__ R
                 int x = (int)len, tot;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const int u = __shfl_up_sync(kFull, x, o);
-                    if (lane >= o) x += u;
+                    const int u2 = __shfl_up_sync(kFull, x, o);
+                    if (lane >= o) x += u2;
                 }
                 tot = __shfl_sync(kFull, x, 31);
                 const int off = carry + x - (int)len;
@@ -959,24 +1053,50 @@ __global__ void __launch_bounds__(kRowsThreads) k_rows(const __grid_constant__ R
         int64_t x = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int64_t u = __shfl_up_sync(kFull, x, o);
-            if (lane >= o) x += u;
+            const int64_t u2 = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += u2;
         }
         const int64_t tot = __shfl_sync(kFull, x, 31);
         const int64_t off = x - cnt;
+        if (lane == 0) lb_store(a.tile_state + t, (t == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
         int64_t goff = 0;
+        if (t > 0) goff = (int64_t)lookback_warp(a.tile_state, t, &a.hdr->status);
         if (lane == 0) {
-            lb_store(a.tile_state + t, (t == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
-            if (t > 0) {
-                goff = (int64_t)lookback(a.tile_state, t, 1, &a.hdr->status);
-                lb_store(a.tile_state + t, kFlagIncl | (uint64_t)(goff + tot));
-            }
+            if (t > 0) lb_store(a.tile_state + t, kFlagIncl | (uint64_t)(goff + tot));
             if (t == ntiles - 1) a.hdr->nnz_c = goff + tot;
         }
-        goff = __shfl_sync(kFull, goff, 0);
         const int64_t obase = goff + off;
         const int64_t cbase = rid * a.nR;
-        if (kind == kRowLane) lane_merge_g<true>(a, st, en, av, cbase, a.c_liv + obase, a.c_val + obase);
+        if (kind == kRowNet) {
+            int o = -1;
+            KeyT ck = kNone;
+            double acc = 0.0;
+#pragma unroll
+            for (int q = 0; q < kNetProd; ++q) {
+                if (nk[q] != kNone) {
+                    if (q == 0 || nk[q] != ck) {
+                        if (o >= 0) {
+                            a.c_liv[obase + o] = cbase + (int64_t)ck;
+                            a.c_val[obase + o] = acc;
+                        }
+                        ++o;
+                        ck = nk[q];
+                        acc = nv[q];
+                    } else {
+                        acc += nv[q];
+                    }
+                }
+            }
+            if (o >= 0) {
+                a.c_liv[obase + o] = cbase + (int64_t)ck;
+                a.c_val[obase + o] = acc;
+            }
+        } else if (kind == kRowLane) {
+            int64_t st[kMergeRuns], en[kMergeRuns];
+            double av[kMergeRuns];
+            collect_runs(a, es, ee, rid, st, en, av);
+            lane_merge_g<true>(a, st, en, av, cbase, a.c_liv + obase, a.c_val + obase);
+        }
         // copies done by the whole warp
         unsigned wm = __ballot_sync(kFull, kind == kRowCopy || kind == kRowSort || kind == kRowHeavy);
         while (wm) {
@@ -987,8 +1107,8 @@ __global__ void __launch_bounds__(kRowsThreads) k_rows(const __grid_constant__ R
             const int64_t scnt = __shfl_sync(kFull, cnt, src);
             const int64_t scb = __shfl_sync(kFull, cbase, src);
             if (skind == kRowCopy) {
-                const int64_t b0 = __shfl_sync(kFull, st[0], src);
-                const double v = __shfl_sync(kFull, av[0], src);
+                const int64_t b0 = __shfl_sync(kFull, copy_b0, src);
+                const double v = __shfl_sync(kFull, copy_a, src);
                 for (int64_t i = lane; i < scnt; i += 32) {
                     const int64_t rl = a.r_liv[b0 + i];
                     a.c_liv[sob + i] = scb + (int64_t)col_of(a.div_n, nR, rl);
@@ -1088,15 +1208,15 @@ __global__ void __launch_bounds__(kCT) k_reduce_by_key(const __grid_constant__ R
     }
     int64_t tot;
     int64_t ex = block_excl<int64_t>((int64_t)heads, s_tmp, &tot);
-    if (threadIdx.x == 0) {
-        lb_store(a.state + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
+    if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) lb_store(a.state + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
         int64_t e = 0;
-        if (tile > 0) {
-            e = (int64_t)lookback(a.state, tile, 1, &a.hdr->status);
-            lb_store(a.state + tile, kFlagIncl | (uint64_t)(e + tot));
+        if (tile > 0) e = (int64_t)lookback_warp(a.state, tile, &a.hdr->status);
+        if (threadIdx.x == 0) {
+            if (tile > 0) lb_store(a.state + tile, kFlagIncl | (uint64_t)(e + tot));
+            s_excl = e;
+            if (tile == ntiles - 1) a.hdr->nnz_c = e + tot;
         }
-        s_excl = e;
-        if (tile == ntiles - 1) a.hdr->nnz_c = e + tot;
     }
     __syncthreads();
     int64_t o = s_excl + ex;
@@ -1615,7 +1735,11 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         const int warps = kRowsThreads / 32;
         int64_t grid = (nchunks_max + warps - 1) / warps;
         if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
-        LCO_LAUNCH("k_rows", s, k_rows<<<(unsigned)grid, kRowsThreads, sizeof(RowsSmem) * warps, s>>>(ra));
+        if (p->nR <= (int64_t)0xfffffffell) {
+            LCO_LAUNCH("k_rows", s, k_rows<uint32_t><<<(unsigned)grid, kRowsThreads, sizeof(RowsSmem) * warps, s>>>(ra));
+        } else {
+            LCO_LAUNCH("k_rows", s, k_rows<uint64_t><<<(unsigned)grid, kRowsThreads, sizeof(RowsSmem) * warps, s>>>(ra));
+        }
     } else {
         SopArgs sa{};
         sa.l_liv = o.l_liv;

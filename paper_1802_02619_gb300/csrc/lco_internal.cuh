@@ -161,6 +161,55 @@ __device__ __forceinline__ uint64_t lookback(const uint64_t *state, int64_t tile
     return excl;
 }
 
+// The same exclusive prefix computed by a whole warp (all 32 lanes must
+// call it; every lane gets the result).  Each round fetches 32 x
+// kLookbackBlocks predecessor words at once; the nearest inclusive word ends
+// the walk.  A word that is needed but not yet published is re-read (bounded
+// wait).  Positions before tile 0 count as an inclusive prefix of zero.
+constexpr int kLookbackBlocks = 4;
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint64_t lookback_warp(const uint64_t *state, int64_t tile, int32_t *status) {
+    const int lane = threadIdx.x & 31;
+    uint64_t excl = 0;
+    const long long t0 = clock64();
+    for (int64_t base = tile - 1; base >= 0; base -= 32 * kLookbackBlocks) {
+        uint64_t w[kLookbackBlocks];
+#pragma unroll
+        for (int j = 0; j < kLookbackBlocks; ++j) {
+            const int64_t idx = base - 32 * j - lane;
+            w[j] = idx >= 0 ? lb_load(state + idx) : kFlagIncl;
+        }
+#pragma unroll
+        for (int j = 0; j < kLookbackBlocks; ++j) {
+            const int64_t idx = base - 32 * j - lane;
+            for (;;) {
+                const unsigned incl = __ballot_sync(0xffffffffu, (w[j] >> 62) == 2);
+                const int first = incl ? __ffs(incl) - 1 : 31;
+                const unsigned need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
+                const unsigned notready = __ballot_sync(0xffffffffu, (w[j] >> 62) == 0) & need;
+                if (!notready) {
+                    excl += warp_sum_u64(lane <= first ? (w[j] & kValueMask) : 0);
+                    if (incl) return excl;
+                    break;
+                }
+                // warp-uniform decision, so that all lanes leave together
+                if (__any_sync(0xffffffffu, clock64() - t0 > kSpinBudgetCycles)) {
+                    if (lane == 0) set_error(status, LCO_ERR_TIMEOUT);
+                    return excl;
+                }
+                if ((notready >> lane) & 1u) w[j] = lb_load(state + idx);
+            }
+        }
+    }
+    return excl;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
