@@ -708,7 +708,7 @@ __global__ void __launch_bounds__(kCT, 1) k_heavy(const __grid_constant__ HeavyA
 // look-back over tiles) a second pass writes C.
 // ------------------------------------------------------------------------
 constexpr int kLaneProd = 64;          // products a lane merges by itself
-constexpr int kRowsThreads = 256;      // 8 warps per CTA
+constexpr int kRowsThreads = 128;      // 4 warps per CTA
 constexpr int kWarpSortCap = kHeavyWork;   // products of a warp-sorted row
 
 struct RowsArgs {
@@ -736,9 +736,21 @@ struct RowsArgs {
     WsHeader *hdr;
 };
 
-struct RowsSmem {
-    uint64_t pcol[kWarpSortCap];
-    double pval[kWarpSortCap];
+constexpr int kStage = 32 * 16;           // staged outputs of a tile's register-sorted rows
+
+// Per warp: the warp-sort buffer, later reused to stage the outputs of the
+// register-sorted rows so that they reach C as coalesced stores.
+union RowsSmem {
+    struct {
+        uint64_t pcol[kWarpSortCap];
+        double pval[kWarpSortCap];
+    } sort;
+    struct {
+        int64_t liv[kStage];
+        double val[kStage];
+        int32_t soff[33];   // staged start of each lane's row
+        int32_t doff[32];   // tile-local output offset of each lane's row
+    } stage;
 };
 
 __device__ __forceinline__ uint64_t col_of(const DivU64 &div_n, uint64_t nR, int64_t liv) {
@@ -746,33 +758,35 @@ __device__ __forceinline__ uint64_t col_of(const DivU64 &div_n, uint64_t nR, int
     return x - divu(div_n, x) * nR;
 }
 
-// k-way merge of up to kMergeRuns runs [st[i], en[i]) of B entries (columns
-// ascending within a run); with kWrite, writes (base + col, sum of av[i]*b)
-// to out; returns the number of distinct columns.
-template <bool kWrite>
+// k-way merge of up to kMergeRuns runs of B entries (columns ascending
+// within a run): run i is [st[i], st[i] + ln[i]).  With kWrite, writes
+// (base + col, sum of av[i] * b) to out; returns the number of distinct
+// columns.  KeyT holds a column (uint32_t when every column fits).
+template <bool kWrite, typename KeyT>
 __device__ __forceinline__ int lane_merge_g(const RowsArgs &a, const int64_t (&st)[kMergeRuns],
-                                            const int64_t (&en)[kMergeRuns], const double (&av)[kMergeRuns],
+                                            const int32_t (&ln)[kMergeRuns], const double (&av)[kMergeRuns],
                                             int64_t base, int64_t *out_liv, double *out_val) {
-    int64_t cur[kMergeRuns];
-    uint64_t hk[kMergeRuns];
+    constexpr KeyT kNone = (KeyT)~(KeyT)0;
+    int32_t pos[kMergeRuns];
+    KeyT hk[kMergeRuns];
 #pragma unroll
     for (int i = 0; i < kMergeRuns; ++i) {
-        cur[i] = st[i];
-        hk[i] = cur[i] < en[i] ? col_of(a.div_n, (uint64_t)a.nR, a.r_liv[cur[i]]) : kEmpty;
+        pos[i] = 0;
+        hk[i] = ln[i] > 0 ? (KeyT)col_of(a.div_n, (uint64_t)a.nR, a.r_liv[st[i]]) : kNone;
     }
     int o = 0;
     for (;;) {
-        uint64_t m = hk[0];
+        KeyT m = hk[0];
 #pragma unroll
         for (int i = 1; i < kMergeRuns; ++i) m = hk[i] < m ? hk[i] : m;
-        if (m == kEmpty) break;
+        if (m == kNone) break;
         double s = 0.0;
 #pragma unroll
         for (int i = 0; i < kMergeRuns; ++i) {
             if (hk[i] == m) {
-                if (kWrite) s += av[i] * a.r_val[cur[i]];
-                ++cur[i];
-                hk[i] = cur[i] < en[i] ? col_of(a.div_n, (uint64_t)a.nR, a.r_liv[cur[i]]) : kEmpty;
+                if (kWrite) s += av[i] * a.r_val[st[i] + pos[i]];
+                ++pos[i];
+                hk[i] = pos[i] < ln[i] ? (KeyT)col_of(a.div_n, (uint64_t)a.nR, a.r_liv[st[i] + pos[i]]) : kNone;
             }
         }
         if (kWrite) {
@@ -870,13 +884,14 @@ __device__ __forceinline__ void net_sort(KeyT (&k)[kNetProd], double (&v)[kNetPr
 // [es, ee) of row rid); returns the number of non-empty runs (the first
 // kMergeRuns are stored).
 __device__ __forceinline__ int collect_runs(const RowsArgs &a, int64_t es, int64_t ee, int64_t rid,
-                                            int64_t (&st)[kMergeRuns], int64_t (&en)[kMergeRuns],
+                                            int64_t (&st)[kMergeRuns], int32_t (&ln)[kMergeRuns],
                                             double (&av)[kMergeRuns]) {
     int nr = 0;
     const int64_t rbase = rid * a.k;
 #pragma unroll
     for (int i = 0; i < kMergeRuns; ++i) {
-        st[i] = en[i] = 0;
+        st[i] = 0;
+        ln[i] = 0;
         av[i] = 0.0;
     }
     for (int64_t e = es; e < ee; ++e) {
@@ -889,7 +904,7 @@ __device__ __forceinline__ int collect_runs(const RowsArgs &a, int64_t es, int64
                 for (int i = 0; i < kMergeRuns; ++i)
                     if (i == nr) {
                         st[i] = b0;
-                        en[i] = b0 + len;
+                        ln[i] = (int32_t)len;
                         av[i] = v;
                     }
             }
@@ -900,7 +915,7 @@ __device__ __forceinline__ int collect_runs(const RowsArgs &a, int64_t es, int64
 }
 
 template <typename KeyT>
-__global__ void __launch_bounds__(kRowsThreads, 2) k_rows(const __grid_constant__ RowsArgs a) {
+__global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant__ RowsArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     RowsSmem &S = reinterpret_cast<RowsSmem *>(smem_raw)[warp];
@@ -992,15 +1007,16 @@ __global__ void __launch_bounds__(kRowsThreads, 2) k_rows(const __grid_constant_
                     u += (nk[q] != kNone) && (q == 0 || nk[q] != nk[q - 1]);
                 cnt = u;
             } else {
-                int64_t st[kMergeRuns], en[kMergeRuns];
+                int64_t st[kMergeRuns];
+                int32_t ln[kMergeRuns];
                 double av[kMergeRuns];
-                const int nr = collect_runs(a, es, ee, rid, st, en, av);
+                const int nr = collect_runs(a, es, ee, rid, st, ln, av);
                 if (nr <= kMergeRuns && frow <= kLaneProd) {
                     kind = kRowLane;
-                    cnt = lane_merge_g<false>(a, st, en, av, 0, nullptr, nullptr);
+                    cnt = lane_merge_g<false, KeyT>(a, st, ln, av, 0, nullptr, nullptr);
                 } else if (nr == 1) {
                     kind = kRowCopy;
-                    cnt = en[0] - st[0];
+                    cnt = ln[0];
                     copy_b0 = st[0];
                     copy_a = av[0];
                 } else {
@@ -1035,16 +1051,16 @@ __global__ void __launch_bounds__(kRowsThreads, 2) k_rows(const __grid_constant_
                 tot = __shfl_sync(kFull, x, 31);
                 const int off = carry + x - (int)len;
                 for (int64_t q = 0; q < len; ++q) {
-                    S.pcol[off + q] = col_of(a.div_n, nR, a.r_liv[b0 + q]);
-                    S.pval[off + q] = v * a.r_val[b0 + q];
+                    S.sort.pcol[off + q] = col_of(a.div_n, nR, a.r_liv[b0 + q]);
+                    S.sort.pval[off + q] = v * a.r_val[b0 + q];
                 }
                 carry += tot;
             }
             __syncwarp();
-            const int n = warp_sort_reduce(S.pcol, S.pval, carry);
+            const int n = warp_sort_reduce(S.sort.pcol, S.sort.pval, carry);
             for (int i = lane; i < n; i += 32) {
-                a.sk0[spb + i] = S.pcol[i];
-                a.sv0[spb + i] = S.pval[i];
+                a.sk0[spb + i] = S.sort.pcol[i];
+                a.sv0[spb + i] = S.sort.pval[i];
             }
             if (lane == src) cnt = n;
             __syncwarp();
@@ -1058,6 +1074,48 @@ __global__ void __launch_bounds__(kRowsThreads, 2) k_rows(const __grid_constant_
         }
         const int64_t tot = __shfl_sync(kFull, x, 31);
         const int64_t off = x - cnt;
+        // register-sorted rows: stage their outputs (row-local LIV, value)
+        __syncwarp();
+        {
+            const int ncnt = kind == kRowNet ? (int)cnt : 0;
+            int y = ncnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u2 = __shfl_up_sync(kFull, y, o);
+                if (lane >= o) y += u2;
+            }
+            const int soff = y - ncnt;
+            S.stage.soff[lane] = soff;
+            S.stage.doff[lane] = (int32_t)off;
+            if (lane == 31) S.stage.soff[32] = y;
+            if (kind == kRowNet) {
+                const int64_t cb = rid * a.nR;
+                int o = -1;
+                KeyT ck = kNone;
+                double acc = 0.0;
+#pragma unroll
+                for (int q = 0; q < kNetProd; ++q) {
+                    if (nk[q] != kNone) {
+                        if (q == 0 || nk[q] != ck) {
+                            if (o >= 0) {
+                                S.stage.liv[soff + o] = cb + (int64_t)ck;
+                                S.stage.val[soff + o] = acc;
+                            }
+                            ++o;
+                            ck = nk[q];
+                            acc = nv[q];
+                        } else {
+                            acc += nv[q];
+                        }
+                    }
+                }
+                if (o >= 0) {
+                    S.stage.liv[soff + o] = cb + (int64_t)ck;
+                    S.stage.val[soff + o] = acc;
+                }
+            }
+        }
+        __syncwarp();
         if (lane == 0) lb_store(a.tile_state + t, (t == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
         int64_t goff = 0;
         if (t > 0) goff = (int64_t)lookback_warp(a.tile_state, t, &a.hdr->status);
@@ -1067,35 +1125,27 @@ __global__ void __launch_bounds__(kRowsThreads, 2) k_rows(const __grid_constant_
         }
         const int64_t obase = goff + off;
         const int64_t cbase = rid * a.nR;
-        if (kind == kRowNet) {
-            int o = -1;
-            KeyT ck = kNone;
-            double acc = 0.0;
-#pragma unroll
-            for (int q = 0; q < kNetProd; ++q) {
-                if (nk[q] != kNone) {
-                    if (q == 0 || nk[q] != ck) {
-                        if (o >= 0) {
-                            a.c_liv[obase + o] = cbase + (int64_t)ck;
-                            a.c_val[obase + o] = acc;
-                        }
-                        ++o;
-                        ck = nk[q];
-                        acc = nv[q];
-                    } else {
-                        acc += nv[q];
-                    }
+        {
+            // coalesced copy of the staged outputs: entry i belongs to the
+            // lane whose staged range holds it (binary search over 32 starts)
+            const int ns = S.stage.soff[32];
+            for (int i = lane; i < ns; i += 32) {
+                int lo = 0, hi = 32;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (S.stage.soff[mid] <= i) lo = mid; else hi = mid;
                 }
+                const int64_t g = goff + S.stage.doff[lo] + (i - S.stage.soff[lo]);
+                a.c_liv[g] = S.stage.liv[i];
+                a.c_val[g] = S.stage.val[i];
             }
-            if (o >= 0) {
-                a.c_liv[obase + o] = cbase + (int64_t)ck;
-                a.c_val[obase + o] = acc;
-            }
-        } else if (kind == kRowLane) {
-            int64_t st[kMergeRuns], en[kMergeRuns];
+        }
+        if (kind == kRowLane) {
+            int64_t st[kMergeRuns];
+            int32_t ln[kMergeRuns];
             double av[kMergeRuns];
-            collect_runs(a, es, ee, rid, st, en, av);
-            lane_merge_g<true>(a, st, en, av, cbase, a.c_liv + obase, a.c_val + obase);
+            collect_runs(a, es, ee, rid, st, ln, av);
+            lane_merge_g<true, KeyT>(a, st, ln, av, cbase, a.c_liv + obase, a.c_val + obase);
         }
         // copies done by the whole warp
         unsigned wm = __ballot_sync(kFull, kind == kRowCopy || kind == kRowSort || kind == kRowHeavy);
@@ -1734,7 +1784,7 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         ra.hdr = hdr;
         const int warps = kRowsThreads / 32;
         int64_t grid = (nchunks_max + warps - 1) / warps;
-        if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
+        if (grid > (int64_t)sms * 16) grid = (int64_t)sms * 16;
         if (p->nR <= (int64_t)0xfffffffell) {
             LCO_LAUNCH("k_rows", s, k_rows<uint32_t><<<(unsigned)grid, kRowsThreads, sizeof(RowsSmem) * warps, s>>>(ra));
         } else {

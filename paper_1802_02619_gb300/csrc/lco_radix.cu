@@ -6,6 +6,8 @@ namespace lco {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kUpItems = 8;   // histogram kernels: loads in flight per thread
+constexpr int kOffItems = 16; // offsets kernel: ranges per lane (G <= 512)
 
 // In-place exclusive scan of n (<= 256 * 8) 32-bit values held in shared
 // memory, by a block of kRadixThreads threads.  Returns the total.
@@ -156,11 +158,22 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const __grid_co
     int64_t lo, hi;
     range_of(j, n, blockIdx.x, lo, hi);
     const uint32_t mask = (uint32_t)NB - 1;
-    for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-        const int64_t liv = relin(j.relin, j.src_liv[e]);
-        const uint64_t key = divu(j.key_div, (uint64_t)liv);
-        for (int p = 0; p < j.P; ++p)
-            atomicAdd(&s_hist[p * NB + (uint32_t)((key >> (p * j.D)) & mask)], 1u);
+    // kUpItems independent loads in flight per thread
+    for (int64_t e0 = lo; e0 < hi; e0 += (int64_t)kUpItems * kRadixThreads) {
+        int64_t v[kUpItems];
+#pragma unroll
+        for (int i = 0; i < kUpItems; ++i) {
+            const int64_t e = e0 + i * kRadixThreads + threadIdx.x;
+            v[i] = e < hi ? j.src_liv[e] : -1;
+        }
+#pragma unroll
+        for (int i = 0; i < kUpItems; ++i) {
+            if (v[i] >= 0) {
+                const uint64_t key = divu(j.key_div, (uint64_t)relin(j.relin, v[i]));
+                for (int p = 0; p < j.P; ++p)
+                    atomicAdd(&s_hist[p * NB + (uint32_t)((key >> (p * j.D)) & mask)], 1u);
+            }
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nh; i += blockDim.x) {
@@ -216,9 +229,16 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const __grid_const
     range_of(j, n, blockIdx.x, lo, hi);
     const uint32_t mask = (uint32_t)NB - 1;
     const int shift = pass * j.D;
-    for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-        const uint64_t key = divu(j.key_div, (uint64_t)io.sl[e]);
-        atomicAdd(&s_hist[(uint32_t)(key >> shift) & mask], 1u);
+    for (int64_t e0 = lo; e0 < hi; e0 += (int64_t)kUpItems * kRadixThreads) {
+        int64_t v[kUpItems];
+#pragma unroll
+        for (int i = 0; i < kUpItems; ++i) {
+            const int64_t e = e0 + i * kRadixThreads + threadIdx.x;
+            v[i] = e < hi ? io.sl[e] : -1;
+        }
+#pragma unroll
+        for (int i = 0; i < kUpItems; ++i)
+            if (v[i] >= 0) atomicAdd(&s_hist[(uint32_t)(divu(j.key_div, (uint64_t)v[i]) >> shift) & mask], 1u);
     }
     __syncthreads();
     for (int d = threadIdx.x; d < NB; d += blockDim.x) j.counts_hist[(int64_t)blockIdx.x * NB + d] = s_hist[d];
@@ -234,18 +254,29 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_offsets(const __grid_co
     const int d = blockIdx.x * kRadixWarps + (threadIdx.x >> 5);
     if (d >= NB) return;
     const uint32_t *cnt = io.first ? j.counts_src + (int64_t)pass * j.G * NB : j.counts_hist;
-    uint64_t carry = j.offs[pass * NB + d];
-    for (int r0 = 0; r0 < j.G; r0 += 32) {
-        const int r = r0 + lane;
-        const uint64_t c = r < j.G ? cnt[(int64_t)r * NB + d] : 0;
-        uint64_t x = c;
+    // lane l owns ranges [l * per, (l + 1) * per): all its loads are issued
+    // before the scan (G <= 32 * kOffItems)
+    const int per = (j.G + 31) / 32;
+    uint32_t c[kOffItems];
+    uint64_t local = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint64_t u = __shfl_up_sync(kFull, x, o);
-            if (lane >= o) x += u;
-        }
-        if (r < j.G) j.roffs[(int64_t)r * NB + d] = carry + x - c;
-        carry += __shfl_sync(kFull, x, 31);
+    for (int i = 0; i < kOffItems; ++i) {
+        const int r = lane * per + i;
+        c[i] = (i < per && r < j.G) ? cnt[(int64_t)r * NB + d] : 0u;
+        local += c[i];
+    }
+    uint64_t x = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t u = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += u;
+    }
+    uint64_t run = j.offs[pass * NB + d] + x - local;
+#pragma unroll
+    for (int i = 0; i < kOffItems; ++i) {
+        const int r = lane * per + i;
+        if (i < per && r < j.G) j.roffs[(int64_t)r * NB + d] = run;
+        run += c[i];
     }
 }
 
@@ -255,7 +286,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_offsets(const __grid_co
 // per-digit offsets; the tile is staged in shared memory so that the writes
 // of each digit's run are contiguous.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kRadixThreads, 2) k_radix_scatter(const __grid_constant__ RadixJob j, int pass) {
+__global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(const __grid_constant__ RadixJob j, int pass) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const PassIO io = pass_io(j, pass);
     if (!io.run) return;
@@ -406,7 +437,8 @@ constexpr size_t kHistTableBytes = (size_t)kMaxPasses * ((size_t)1 << kMaxDigitB
 int radix_ranges(int64_t n_cap) {
     const int64_t tiles = (n_cap + kRadixTile - 1) / kRadixTile;
     int64_t g = (tiles + 3) / 4;                 // at least four tiles per range
-    const int64_t gmax = 2 * (int64_t)radix_sm_count();
+    int64_t gmax = 3 * (int64_t)radix_sm_count();  // three scatter CTAs per SM
+    if (gmax > 32 * kOffItems) gmax = 32 * kOffItems;
     if (g > gmax) g = gmax;
     if (g < 1) g = 1;
     return (int)g;
