@@ -267,6 +267,77 @@ int32_t lco_contract(const lco_plan *plan,
 /* Synchronises `stream` and copies the result header of `ws` to *out. */
 int32_t lco_contract_result_get(const void *ws, lco_contract_result *out, void *stream);
 
+/* ------------------------------------------------------------------ */
+/* Tuning hints (planner inputs chosen by an autotuner; no paper        */
+/* counterpart beyond Table 4's choice, which they may override)        */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t alg;             /* LCO_ALG_AUTO (Table 4) or a forced lco_alg */
+    int32_t max_digit_bits;  /* radix digit width cap for operand permutations, 4..11 (0 = 11) */
+} lco_tune;
+
+/* lco_contract_plan with tuning hints (tune may be NULL = defaults). */
+int32_t lco_contract_plan_ex(const lco_shape *a, const lco_shape *b, int32_t ncontract,
+                             const int32_t *modes_a, const int32_t *modes_b,
+                             const lco_tune *tune, lco_plan **plan);
+
+/* ------------------------------------------------------------------ */
+/* Batched contractions (many independent, uneven problems per call)    */
+/* ------------------------------------------------------------------ */
+
+/* One problem of a batch: operand shapes, the contracted mode pairs and
+ * the algorithm (LCO_ALG_AUTO or a tuner's choice). */
+typedef struct {
+    lco_shape a;
+    lco_shape b;
+    int32_t ncontract;
+    int32_t modes_a[LCO_MAX_ORDER];
+    int32_t modes_b[LCO_MAX_ORDER];
+    int32_t alg;             /* LCO_ALG_AUTO or a forced algorithm */
+    int32_t max_digit_bits;  /* radix digit width cap (0 = default), see lco_tune */
+} lco_problem;
+
+/* Device pointers of one problem's operands and output (C with room for
+ * caps[i] entries). */
+typedef struct {
+    const int64_t *a_liv;
+    const double *a_val;
+    const int64_t *b_liv;
+    const double *b_val;
+    int64_t *c_liv;
+    double *c_val;
+} lco_operands;
+
+typedef struct lco_batch lco_batch;   /* opaque host object */
+
+/* Plans nprob problems and creates `nstreams` (1..64) worker streams.  Each
+ * problem is planned exactly as lco_contract_plan does (host only). */
+int32_t lco_batch_plan(int32_t nprob, const lco_problem *probs, int32_t nstreams, lco_batch **batch);
+int32_t lco_batch_destroy(lco_batch *batch);
+int32_t lco_batch_info(const lco_batch *batch, int32_t i, lco_plan_info *info);
+
+/* Bytes of the single batch workspace for output capacities caps[nprob]
+ * (caps = NULL: enough for lco_batch_symbolic only). */
+int32_t lco_batch_workspace(const lco_batch *batch, const int64_t *caps, size_t *ws_bytes);
+
+/* Phase 1 / phase 2 / both for every problem, as lco_contract_symbolic /
+ * _numeric / lco_contract do for one.  Work is forked from `stream` onto
+ * the batch's worker streams (events) and joined back into `stream`, so a
+ * whole call can be captured into one CUDA graph.  ops[nprob]: device
+ * pointers; caps must be the same array (values) the workspace was sized
+ * with.  No host synchronisation. */
+int32_t lco_batch_symbolic(lco_batch *batch, const lco_operands *ops, const int64_t *caps,
+                           void *ws, size_t ws_bytes, void *stream);
+int32_t lco_batch_numeric(lco_batch *batch, const lco_operands *ops, const int64_t *caps,
+                          void *ws, size_t ws_bytes, void *stream);
+int32_t lco_batch_contract(lco_batch *batch, const lco_operands *ops, const int64_t *caps,
+                           void *ws, size_t ws_bytes, void *stream);
+
+/* Synchronises `stream` and reads every problem's result (out[nprob]). */
+int32_t lco_batch_results(const lco_batch *batch, const int64_t *caps, const void *ws,
+                          lco_contract_result *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -65,6 +65,21 @@ class TimingRecord(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("ms", ctypes.c_float)]
 
 
+class Tune(ctypes.Structure):
+    _fields_ = [("alg", ctypes.c_int32), ("max_digit_bits", ctypes.c_int32)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("a", Shape), ("b", Shape), ("ncontract", ctypes.c_int32),
+                ("modes_a", ctypes.c_int32 * MAX_ORDER), ("modes_b", ctypes.c_int32 * MAX_ORDER),
+                ("alg", ctypes.c_int32), ("max_digit_bits", ctypes.c_int32)]
+
+
+class Operands(ctypes.Structure):
+    _fields_ = [("a_liv", ctypes.c_void_p), ("a_val", ctypes.c_void_p), ("b_liv", ctypes.c_void_p),
+                ("b_val", ctypes.c_void_p), ("c_liv", ctypes.c_void_p), ("c_val", ctypes.c_void_p)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -102,6 +117,22 @@ _SIGNATURES = {
                                                                  ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int32),
     "lco_contract_result_get": ([ctypes.c_void_p, ctypes.POINTER(ContractResult), ctypes.c_void_p],
                                 ctypes.c_int32),
+    "lco_contract_plan_ex": ([ctypes.POINTER(Shape), ctypes.POINTER(Shape), ctypes.c_int32, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.POINTER(Tune), ctypes.POINTER(ctypes.c_void_p)],
+                             ctypes.c_int32),
+    "lco_batch_plan": ([ctypes.c_int32, ctypes.POINTER(Problem), ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)],
+                       ctypes.c_int32),
+    "lco_batch_destroy": ([ctypes.c_void_p], ctypes.c_int32),
+    "lco_batch_info": ([ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(PlanInfo)], ctypes.c_int32),
+    "lco_batch_workspace": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int32),
+    "lco_batch_symbolic": ([ctypes.c_void_p, ctypes.POINTER(Operands), ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int32),
+    "lco_batch_numeric": ([ctypes.c_void_p, ctypes.POINTER(Operands), ctypes.c_void_p, ctypes.c_void_p,
+                          ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int32),
+    "lco_batch_contract": ([ctypes.c_void_p, ctypes.POINTER(Operands), ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int32),
+    "lco_batch_results": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ContractResult),
+                          ctypes.c_void_p], ctypes.c_int32),
 }
 
 
@@ -298,10 +329,18 @@ def radix_permute(t: LcoTensor, new_sig, stream=None) -> LcoTensor:
 # Contraction
 # ---------------------------------------------------------------------------
 
-class ContractPlan:
-    """Plan for C = A x_modes B (Sec. 5.2 poly-algorithm, Table 4 dispatch)."""
+def _alg_code(alg):
+    return -1 if alg is None else (ALG[alg] if isinstance(alg, str) else int(alg))
 
-    def __init__(self, a_dims, a_sig, a_nnz, b_dims, b_sig, b_nnz, modes_a, modes_b, alg=None):
+
+class ContractPlan:
+    """Plan for C = A x_modes B (Sec. 5.2 poly-algorithm, Table 4 dispatch).
+
+    alg forces an algorithm (name or code); max_digit_bits caps the radix
+    digit width of operand permutations (tuning hints)."""
+
+    def __init__(self, a_dims, a_sig, a_nnz, b_dims, b_sig, b_nnz, modes_a, modes_b, alg=None,
+                 max_digit_bits=0):
         self.lib = load()
         self.sa = make_shape(a_dims, a_sig, a_nnz)
         self.sb = make_shape(b_dims, b_sig, b_nnz)
@@ -310,10 +349,10 @@ class ContractPlan:
         nc = len(modes_a)
         self._ma = (ctypes.c_int32 * max(1, nc))(*[int(x) for x in modes_a])
         self._mb = (ctypes.c_int32 * max(1, nc))(*[int(x) for x in modes_b])
-        force = -1 if alg is None else (ALG[alg] if isinstance(alg, str) else int(alg))
+        tune = Tune(_alg_code(alg), int(max_digit_bits))
         h = ctypes.c_void_p()
-        _check(self.lib.lco_contract_plan(ctypes.byref(self.sa), ctypes.byref(self.sb), nc, self._ma, self._mb,
-                                          force, ctypes.byref(h)), "lco_contract_plan")
+        _check(self.lib.lco_contract_plan_ex(ctypes.byref(self.sa), ctypes.byref(self.sb), nc, self._ma, self._mb,
+                                             ctypes.byref(tune), ctypes.byref(h)), "lco_contract_plan_ex")
         self.handle = h
         info = PlanInfo()
         _check(self.lib.lco_plan_get_info(h, ctypes.byref(info)), "lco_plan_get_info")
@@ -401,3 +440,105 @@ def contract(A: LcoTensor, B: LcoTensor, modes_a, modes_b, alg=None, stream=None
     if return_info:
         return C, dict(plan.info, **r)
     return C
+
+
+# ---------------------------------------------------------------------------
+# Batched contractions
+# ---------------------------------------------------------------------------
+
+def _problem(A: LcoTensor, B: LcoTensor, modes_a, modes_b, alg=None, max_digit_bits=0) -> Problem:
+    p = Problem()
+    p.a = A.shape()
+    p.b = B.shape()
+    p.ncontract = len(modes_a)
+    for i, (x, y) in enumerate(zip(modes_a, modes_b)):
+        p.modes_a[i] = int(x)
+        p.modes_b[i] = int(y)
+    p.alg = _alg_code(alg)
+    p.max_digit_bits = int(max_digit_bits or 0)
+    return p
+
+
+class Batch:
+    """Many independent contractions enqueued together (see lco_batch_* in
+    include/lco.h).  items: list of (A, B, modes_a, modes_b[, alg[, max_digit_bits]]).  The
+    first call sizes every output by its product count f; `run()` then
+    enqueues the whole batch with no host synchronisation and can be
+    captured into a CUDA graph."""
+
+    def __init__(self, items, nstreams: int = 16, device="cuda"):
+        self.lib = load()
+        self.items = [tuple(it) + (None,) * (6 - len(it)) for it in items]
+        n = len(self.items)
+        self.n = n
+        self._probs = (Problem * n)(*[_problem(A, B, ma, mb, alg, bits)
+                                      for A, B, ma, mb, alg, bits in self.items])
+        h = ctypes.c_void_p()
+        _check(self.lib.lco_batch_plan(n, self._probs, int(nstreams), ctypes.byref(h)), "lco_batch_plan")
+        self.handle = h
+        self.device = device
+        self._ops = (Operands * n)()
+        for i, (A, B, *_rest) in enumerate(self.items):
+            self._ops[i].a_liv = A.liv.data_ptr() if A.nnz else None
+            self._ops[i].a_val = A.val.data_ptr() if A.nnz else None
+            self._ops[i].b_liv = B.liv.data_ptr() if B.nnz else None
+            self._ops[i].b_val = B.val.data_ptr() if B.nnz else None
+        # phase 1 once to learn every f
+        nb = ctypes.c_size_t()
+        _check(self.lib.lco_batch_workspace(h, None, ctypes.byref(nb)), "lco_batch_workspace")
+        ws = workspace(nb.value, device)
+        _check(self.lib.lco_batch_symbolic(h, self._ops, None, _ptr(ws), ctypes.c_size_t(ws.numel()),
+                                           _stream(None)), "lco_batch_symbolic")
+        res = (ContractResult * n)()
+        _check(self.lib.lco_batch_results(h, None, _ptr(ws), res, _stream(None)), "lco_batch_results")
+        for i in range(n):
+            if res[i].status != 0:
+                raise LcoError(res[i].status, f"batch problem {i} (symbolic)")
+        self.f = [int(res[i].f) for i in range(n)]
+        self._caps = (ctypes.c_int64 * n)(*self.f)
+        del ws
+        total = sum(self.f)
+        self.c_liv_all = torch.empty(max(total, 1), dtype=torch.int64, device=device)
+        self.c_val_all = torch.empty(max(total, 1), dtype=torch.float64, device=device)
+        self.c_off = []
+        off = 0
+        for i in range(n):
+            self.c_off.append(off)
+            self._ops[i].c_liv = self.c_liv_all.data_ptr() + 8 * off if self.f[i] else None
+            self._ops[i].c_val = self.c_val_all.data_ptr() + 8 * off if self.f[i] else None
+            off += self.f[i]
+        _check(self.lib.lco_batch_workspace(h, self._caps, ctypes.byref(nb)), "lco_batch_workspace")
+        self.ws = workspace(nb.value, device)
+        self.info = []
+        for i in range(n):
+            pi = PlanInfo()
+            _check(self.lib.lco_batch_info(h, i, ctypes.byref(pi)), "lco_batch_info")
+            cs = pi.c_shape
+            self.info.append({"alg": ALG_NAMES[pi.alg], "c_dims": [cs.dims[k] for k in range(cs.order)],
+                              "c_sig": [cs.sig[k] for k in range(cs.order)]})
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None) is not None and self.handle.value:
+                self.lib.lco_batch_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+    def run(self, stream=None):
+        _check(self.lib.lco_batch_contract(self.handle, self._ops, self._caps, _ptr(self.ws),
+                                           ctypes.c_size_t(self.ws.numel()), _stream(stream)), "lco_batch_contract")
+
+    def results(self, stream=None):
+        res = (ContractResult * self.n)()
+        _check(self.lib.lco_batch_results(self.handle, self._caps, _ptr(self.ws), res, _stream(stream)),
+               "lco_batch_results")
+        out = []
+        for i in range(self.n):
+            r = res[i]
+            if r.status != 0:
+                raise LcoError(r.status, f"batch problem {i}")
+            o, nc = self.c_off[i], int(r.nnz_c)
+            out.append(LcoTensor(self.info[i]["c_dims"], self.info[i]["c_sig"], self.c_liv_all[o:o + nc],
+                                 self.c_val_all[o:o + nc]))
+        return out

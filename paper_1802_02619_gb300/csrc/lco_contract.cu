@@ -15,10 +15,12 @@
 // and scan the work 1 + |R row| of every L entry, which gives f and L's row
 // table.
 // Phase 2 (numeric): rows whose work exceeds kHeavyWork are multiplied first,
-// one CTA per row, either with a shared-memory hash accumulator and a sort of
-// the nnz_C(i) distinct outputs (the accumulator branches, Table 6 rows
-// CSC/DCSC) or by sorting all f(i) products and summing duplicates (the
-// no-accumulator branch, Sec. 5.2.4).  The remaining (light) rows go one
+// one CTA per row, by a stable sort of the row's f(i) products by column and
+// a sum of each run (the no-accumulator scheme of Sec. 5.2.4; on the GPU it
+// also serves the accumulator branches, because an atomic accumulator would
+// make the summation order, and so the rounding, vary from run to run).
+// Every product is therefore summed in generation order on every path, and
+// results are bit-identical across runs.  The remaining (light) rows go one
 // lane per row, 32 rows per warp: a lane merges a row's sorted B rows, which
 // accumulates and sorts in one go.  Every tile of rows places its output
 // with decoupled look-back, so C is written once, in order.  SOP (Sec. 5.2.5) expands all f products, sorts them by output LIV
@@ -39,12 +41,10 @@ constexpr int kCT = 256;                    // threads of the chunk / scan kerne
 constexpr int kCW = kCT / 32;
 constexpr int kEntCap = 2048;               // heavy rows, shared-memory path: L entries
 constexpr int kProdCap = 2048;              // heavy rows, shared-memory path: products
-constexpr int kHashSlots = 2 * kProdCap;
 constexpr int kSortItems = 8;               // CTA sort: items per thread
 constexpr int kSortTile = kCT * kSortItems; // == kProdCap
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kCT * kScanItems;
-constexpr uint64_t kEmpty = ~0ull;
 
 // light-row kernel
 constexpr int kHeavyWork = 256;             // rows above this work go to the heavy-row kernel
@@ -453,11 +453,9 @@ __global__ void __launch_bounds__(256) k_row_table(const __grid_constant__ Table
 }
 
 // ------------------------------------------------------------------------
-// Heavy rows (work > kHeavyWork): one CTA per row.  Products are
-// accumulated in a shared-memory hash and the distinct entries sorted (the
-// accumulator branches), or sorted and summed (no-accumulator branch); rows
-// whose products exceed shared memory are sorted and reduced in global
-// scratch.  The reduced row is left at the row's product offset in scratch
+// Heavy rows (work > kHeavyWork): one CTA per row.  The row's products are
+// sorted stably by column and each run summed in generation order, in shared
+// memory when they fit, else in global scratch.  The reduced row is left at the row's product offset in scratch
 // and its length in row_hout[r] (bit 62 set when it lies in the second
 // scratch buffer).
 // ------------------------------------------------------------------------
@@ -471,7 +469,6 @@ struct HeavyArgs {
     DivU64 div_n;
     int64_t nR;
     int32_t colbits;
-    int32_t acc;
     Mdt mdt;
     const int64_t *row_start;
     const int64_t *row_work;
@@ -491,9 +488,9 @@ struct HeavySmem {
     int32_t poff[kEntCap + 1];
     int64_t b0[kEntCap];
     double aval[kEntCap];
-    uint64_t pk0[kProdCap];   // ACC: kHashSlots hash keys over pk0..pk1
+    uint64_t pk0[kProdCap];
     uint64_t pk1[kProdCap];
-    double pv0[kProdCap];     // ACC: hash values over pv0..pv1
+    double pv0[kProdCap];
     double pv1[kProdCap];
     uint64_t ok[kProdCap];
     double ov[kProdCap];
@@ -550,12 +547,6 @@ __global__ void __launch_bounds__(kCT, 1) k_heavy(const __grid_constant__ HeavyA
                 lex += (int32_t)len_i[q];
             }
             if (tid == 0) S.poff[nent] = ltot;
-            if (a.acc) {
-                for (int i = tid; i < kHashSlots; i += kCT) {
-                    S.pk0[i] = kEmpty;   // pk0|pk1 contiguous
-                    S.pv0[i] = 0.0;      // pv0|pv1 contiguous
-                }
-            }
             __syncthreads();
             const int np = ltot;
             for (int p = tid; p < np; p += kCT) {
@@ -568,69 +559,32 @@ __global__ void __launch_bounds__(kCT, 1) k_heavy(const __grid_constant__ HeavyA
                 const uint64_t rl = (uint64_t)a.r_liv[b];
                 const uint64_t col = rl - divu(a.div_n, rl) * (uint64_t)a.nR;
                 const double v = S.aval[lo] * a.r_val[b];
-                if (!a.acc) {
-                    S.pk0[p] = col;
-                    S.pv0[p] = v;
-                } else {
-                    uint32_t slot = (uint32_t)((col * 0x9E3779B97F4A7C15ull) >> 52) & (kHashSlots - 1);
-                    for (;;) {
-                        const unsigned long long old =
-                            atomicCAS(reinterpret_cast<unsigned long long *>(&S.pk0[slot]), kEmpty, col);
-                        if (old == kEmpty || old == col) {
-                            atomicAdd(&S.pv0[slot], v);
-                            break;
-                        }
-                        slot = (slot + 1) & (kHashSlots - 1);
-                    }
-                }
+                S.pk0[p] = col;
+                S.pv0[p] = v;
             }
             __syncthreads();
-            int64_t nout = 0;
-            if (!a.acc) {
-                const int rs = cta_sort(S.pk0, S.pv0, S.pk1, S.pv1, np, a.colbits, S.whist, S.run, S.tmp64);
-                const uint64_t *k = rs ? S.pk1 : S.pk0;
-                const double *v = rs ? S.pv1 : S.pv0;
-                int32_t hc = 0;
-                for (int q = 0; q < kProdCap / kCT; ++q) {
-                    const int i = tid * (kProdCap / kCT) + q;
-                    if (i < np && (i == 0 || k[i] != k[i - 1])) ++hc;
-                }
-                int32_t htot;
-                int32_t o = block_excl<int32_t>(hc, S.tmp32, &htot);
-                for (int q = 0; q < kProdCap / kCT; ++q) {
-                    const int i = tid * (kProdCap / kCT) + q;
-                    if (i < np && (i == 0 || k[i] != k[i - 1])) {
-                        double s = v[i];
-                        for (int t = i + 1; t < np && k[t] == k[i]; ++t) s += v[t];
-                        S.ok[o] = k[i];
-                        S.ov[o] = s;
-                        ++o;
-                    }
-                }
-                nout = htot;
-            } else {
-                int32_t cnt = 0;
-                for (int q = 0; q < kHashSlots / kCT; ++q) cnt += S.pk0[tid * (kHashSlots / kCT) + q] != kEmpty;
-                int32_t tot;
-                int32_t o = block_excl<int32_t>(cnt, S.tmp32, &tot);
-                for (int q = 0; q < kHashSlots / kCT; ++q) {
-                    const int i = tid * (kHashSlots / kCT) + q;
-                    if (S.pk0[i] != kEmpty) {
-                        S.ok[o] = S.pk0[i];
-                        S.ov[o] = S.pv0[i];
-                        ++o;
-                    }
-                }
-                __syncthreads();
-                nout = tot;
-                const int rs = cta_sort(S.ok, S.ov, S.pk1, S.pv1, nout, a.colbits, S.whist, S.run, S.tmp64);
-                if (rs) {
-                    for (int i = tid; i < nout; i += kCT) {
-                        S.ok[i] = S.pk1[i];
-                        S.ov[i] = S.pv1[i];
-                    }
+            // stable sort by column, then sum each run in generation order
+            const int rs = cta_sort(S.pk0, S.pv0, S.pk1, S.pv1, np, a.colbits, S.whist, S.run, S.tmp64);
+            const uint64_t *k = rs ? S.pk1 : S.pk0;
+            const double *v = rs ? S.pv1 : S.pv0;
+            int32_t hc = 0;
+            for (int q = 0; q < kProdCap / kCT; ++q) {
+                const int i = tid * (kProdCap / kCT) + q;
+                if (i < np && (i == 0 || k[i] != k[i - 1])) ++hc;
+            }
+            int32_t htot;
+            int32_t o = block_excl<int32_t>(hc, S.tmp32, &htot);
+            for (int q = 0; q < kProdCap / kCT; ++q) {
+                const int i = tid * (kProdCap / kCT) + q;
+                if (i < np && (i == 0 || k[i] != k[i - 1])) {
+                    double s = v[i];
+                    for (int t = i + 1; t < np && k[t] == k[i]; ++t) s += v[t];
+                    S.ok[o] = k[i];
+                    S.ov[o] = s;
+                    ++o;
                 }
             }
+            const int64_t nout = htot;
             __syncthreads();
             for (int64_t i = tid; i < nout; i += kCT) {
                 a.sk0[pbase + i] = S.ok[i];
@@ -1378,6 +1332,17 @@ extern "C" {
 
 int32_t lco_contract_plan(const lco_shape *a, const lco_shape *b, int32_t ncontract, const int32_t *modes_a,
                           const int32_t *modes_b, int32_t force_alg, lco_plan **plan_out) {
+    lco_tune t;
+    t.alg = force_alg;
+    t.max_digit_bits = 0;
+    return lco_contract_plan_ex(a, b, ncontract, modes_a, modes_b, &t, plan_out);
+}
+
+int32_t lco_contract_plan_ex(const lco_shape *a, const lco_shape *b, int32_t ncontract, const int32_t *modes_a,
+                             const int32_t *modes_b, const lco_tune *tune, lco_plan **plan_out) {
+    const int32_t force_alg = tune ? tune->alg : LCO_ALG_AUTO;
+    const int max_bits = tune && tune->max_digit_bits > 0 ? tune->max_digit_bits : kMaxDigitBits;
+    if (tune && (tune->max_digit_bits < 0 || tune->max_digit_bits > kMaxDigitBits)) return LCO_ERR_INVALID;
     if (!plan_out) return LCO_ERR_INVALID;
     *plan_out = nullptr;
     int64_t ta, tb;
@@ -1451,8 +1416,8 @@ int32_t lco_contract_plan(const lco_shape *a, const lco_shape *b, int32_t ncontr
     p->src_r = transposed ? *a : *b;
     const int32_t *l_target = transposed ? b_col : a_row;
     const int32_t *r_target = transposed ? a_col : b_row;
-    if ((rc = rp_plan(&p->src_l, l_target, &p->rp_l)) != LCO_OK) { delete p; return rc; }
-    if ((rc = rp_plan(&p->src_r, r_target, &p->rp_r)) != LCO_OK) { delete p; return rc; }
+    if ((rc = rp_plan(&p->src_l, l_target, &p->rp_l, max_bits)) != LCO_OK) { delete p; return rc; }
+    if ((rc = rp_plan(&p->src_r, r_target, &p->rp_r, max_bits)) != LCO_OK) { delete p; return rc; }
     p->need_l = !same_sig(p->src_l.order, p->src_l.sig, l_target);
     p->need_r = !same_sig(p->src_r.order, p->src_r.sig, r_target);
     p->mL = transposed ? n : m;
@@ -1739,7 +1704,6 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         ha.div_n = make_div((uint64_t)p->nR);
         ha.nR = p->nR;
         ha.colbits = p->colbits;
-        ha.acc = p->acc;
         ha.mdt = mdt;
         ha.row_start = row_start;
         ha.row_work = row_work;

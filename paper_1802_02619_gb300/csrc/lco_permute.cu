@@ -66,7 +66,7 @@ RelinParams make_relin(int32_t order, const int64_t *dims, const int32_t *sig_ol
     return r;
 }
 
-int32_t rp_plan(const lco_shape *t, const int32_t *new_sig, RpPlan *out) {
+int32_t rp_plan(const lco_shape *t, const int32_t *new_sig, RpPlan *out, int max_digit_bits) {
     int64_t total = 0;
     int32_t rc = check_shape(t, &total);
     if (rc != LCO_OK) return rc;
@@ -120,7 +120,7 @@ int32_t rp_plan(const lco_shape *t, const int32_t *new_sig, RpPlan *out) {
     int bits = 0;
     while (bits < 63 && (1ull << bits) < range) ++bits;
     int D, P;
-    radix_digits(bits, &D, &P);
+    radix_digits(bits, &D, &P, max_digit_bits);
     p.info.key_bits = bits;
     p.info.digit_bits = D;
     p.info.passes = P;

@@ -51,10 +51,12 @@ struct RadixJob {
     int32_t *status;
 };
 
-// Digit plan for a key range of `key_bits` bits.
-inline void radix_digits(int key_bits, int *D, int *P) {
+// Digit plan for a key range of `key_bits` bits, digits at most max_bits wide.
+inline void radix_digits(int key_bits, int *D, int *P, int max_bits = kMaxDigitBits) {
+    if (max_bits < 1 || max_bits > kMaxDigitBits) max_bits = kMaxDigitBits;
     if (key_bits <= 0) { *D = 1; *P = 1; return; }
-    int p = (key_bits + kMaxDigitBits - 1) / kMaxDigitBits;
+    int p = (key_bits + max_bits - 1) / max_bits;
+    if (p > kMaxPasses) p = kMaxPasses;
     int d = (key_bits + p - 1) / p;
     *D = d;
     *P = p;

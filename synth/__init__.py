@@ -254,3 +254,119 @@ def config_rmat_na(bits=(14, 14, 12), nnz=1 << 18, seeds=(5, 6)):
     B = rotate_modes(rmat3(bits, nnz, seeds[1]), 2)
     return {"name": f"rmat_{'x'.join(str(1 << b) for b in bits)}_{nnz}_mode2_x_mode0",
             "A": A, "B": B, "modes_a": [2], "modes_b": [0]}
+
+
+# ---------------------------------------------------------------------------
+# Batched workload: uneven FD compositions and R-MAT products
+# ---------------------------------------------------------------------------
+
+STENCIL_2D = [(0, 0), (-1, 0), (1, 0), (0, -1), (0, 1)]
+STENCIL_3D = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+
+
+def rmat3_torch(bits, nnz, seed, device="cuda", probs=RMAT_PROBS):
+    """rmat3's distribution drawn with torch's seeded generator on `device`
+    (fast for many large tensors; a different random stream from rmat3)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    p = torch.tensor(probs, dtype=torch.float64)
+    p = p / p.sum()
+    cum = torch.cumsum(p, 0).to(device)
+    p0_zero, p1_zero = float(p[0] + p[1]), float(p[0] + p[2])
+    p2_given = (float(p[0] / (p[0] + p[1])), float(p[2] / (p[2] + p[3])))
+    bits = [int(b) for b in bits]
+    dims = [1 << b for b in bits]
+    L = max(bits)
+
+    def draw(count):
+        co = torch.zeros((count, 3), dtype=torch.int64, device=device)
+        for t in range(L):
+            act = [t < b for b in bits]
+            b0 = b1 = None
+            if act[0] and act[1]:
+                q = torch.searchsorted(cum, torch.rand(count, generator=g, device=device, dtype=torch.float64),
+                                       right=True).clamp_(max=3)
+                b0, b1 = q >> 1, q & 1
+            elif act[0]:
+                b0 = (torch.rand(count, generator=g, device=device, dtype=torch.float64) >= p0_zero).long()
+            elif act[1]:
+                b1 = (torch.rand(count, generator=g, device=device, dtype=torch.float64) >= p1_zero).long()
+            if act[2]:
+                u = torch.rand(count, generator=g, device=device, dtype=torch.float64)
+                if b0 is not None:
+                    thr = torch.where(b0 == 0, p2_given[0], p2_given[1])
+                else:
+                    thr = torch.full((count,), p0_zero, device=device, dtype=torch.float64)
+                co[:, 2] |= (u >= thr).long() << (bits[2] - 1 - t)
+            if b0 is not None:
+                co[:, 0] |= b0 << (bits[0] - 1 - t)
+            if b1 is not None:
+                co[:, 1] |= b1 << (bits[1] - 1 - t)
+        vals = torch.rand(count, generator=g, device=device, dtype=torch.float64) * 2.0 - 1.0
+        return co, vals
+
+    all_liv = torch.empty(0, dtype=torch.int64, device=device)
+    all_val = torch.empty(0, dtype=torch.float64, device=device)
+    need = nnz
+    while True:
+        co, vals = draw(int(need * 1.05) + 64)
+        liv = (co[:, 0] * dims[1] + co[:, 1]) * dims[2] + co[:, 2]
+        all_liv = torch.cat([all_liv, liv])
+        all_val = torch.cat([all_val, vals])
+        order = torch.sort(all_liv, stable=True).indices
+        s = all_liv[order]
+        first = torch.ones_like(s, dtype=torch.bool)
+        first[1:] = s[1:] != s[:-1]
+        keep = order[first]                     # first draw of every distinct LIV
+        if keep.numel() >= nnz:
+            keep = torch.sort(keep).values[:nnz]
+            liv, val = all_liv[keep], all_val[keep]
+            o = torch.argsort(liv)
+            return {"dims": dims, "sig": [2, 1, 0], "liv": liv[o], "val": val[o]}
+        need = nnz - keep.numel()
+
+
+def _log_uniform(rng, lo, hi):
+    return float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+
+
+def batch_problems(count=4096, seed=100, fd2d=(8, 128), fd3d=(8, 32), rmat_nnz=(1e3, 1e6),
+                   ratio=(1.0, 500.0), device="cuda"):
+    """The batched workload: count/4 2D and count/4 3D FD operators with one
+    U(-1,1) coefficient per stencil position, each composed with itself over
+    its input-grid modes (grid sides log-uniform), and count/2 R-MAT pairs in
+    one of the paper's three forms -- a_ijk b_ljk (Eq. 14), a_ijk b_lmk
+    (Eq. 16) or M x N x N with M = N^2 (Sec. 5.2.5) -- with nnz log-uniform
+    and hyper-sparsity ratio log-uniform.  Returns (A, B, modes_a, modes_b,
+    kind) tuples; R-MAT tensors live on `device` as torch tensors, FD ones
+    as numpy arrays."""
+    rng = np.random.default_rng(seed)
+    n2, n3 = count // 4, count // 4
+    out = []
+    for _ in range(n2):
+        n = int(round(_log_uniform(rng, *fd2d)))
+        A = stencil_operator((n, n), STENCIL_2D, rng.uniform(-1, 1, len(STENCIL_2D)))
+        out.append((A, A, [2, 3], [0, 1], "fd2d"))
+    for _ in range(n3):
+        n = int(round(_log_uniform(rng, *fd3d)))
+        A = stencil_operator((n, n, n), STENCIL_3D, rng.uniform(-1, 1, len(STENCIL_3D)))
+        out.append((A, A, [3, 4, 5], [0, 1, 2], "fd3d"))
+    for _ in range(count - n2 - n3):
+        form = int(rng.integers(0, 3))
+        nnz = int(_log_uniform(rng, *rmat_nnz))
+        rho = _log_uniform(rng, *ratio)
+        s1, s2 = int(rng.integers(0, 2**31)), int(rng.integers(0, 2**31))
+        if form < 2:
+            b = max(2, int(np.ceil(np.log2(np.sqrt(rho * nnz)))))
+            bits = (b, b, b)
+        else:
+            b = max(2, int(np.ceil(np.log2((rho * nnz) ** 0.25))))
+            bits = (2 * b, b, b)
+        A = rmat3_torch(bits, nnz, s1, device)
+        B = rmat3_torch(bits, nnz, s2, device)
+        if form == 1:
+            out.append((A, B, [2], [2], "rmat_eq16"))
+        else:
+            out.append((A, B, [1, 2], [1, 2], "rmat_eq14" if form == 0 else "rmat_sop"))
+    return out

@@ -232,3 +232,16 @@ def test_plan_reuse_gives_identical_results():
         outs.append((c_liv[:r["nnz_c"]].clone(), c_val[:r["nnz_c"]].clone()))
     assert torch.equal(outs[0][0], outs[1][0])
     assert torch.equal(outs[0][1].view(torch.int64), outs[1][1].view(torch.int64))
+
+
+def test_results_are_deterministic_on_every_branch():
+    """Every branch sums each output's products in generation order, so two
+    runs give the same bits, heavy rows included."""
+    A = synth.rmat3((9, 6, 6), 30000, seed=41)
+    B = synth.rmat3((9, 6, 6), 30000, seed=42)
+    for alg in ("CSR", "CSRNA", "DCSR", "SOP", "CSC", "CSCNA", "DCSC"):
+        C1, info = _run(A, B, [1, 2], [1, 2], alg)
+        C2, _ = _run(A, B, [1, 2], [1, 2], alg)
+        assert torch.equal(C1.liv, C2.liv), alg
+        assert torch.equal(C1.val.view(torch.int64), C2.val.view(torch.int64)), alg
+        assert_contract_matches(C1, A, B, [1, 2], [1, 2])
