@@ -61,10 +61,16 @@ def parse_args():
     ap.add_argument("--impl", choices=["lco", "reference"], default="lco")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["step", "permute"], default="step",
+    ap.add_argument("--case", choices=["step", "permute", "batch"], default="step",
                     help="step: the benchmark workload; permute: a stand-alone radix permutation "
                          "of a random 6th-order 64^6 tensor (profiling aid)")
     ap.add_argument("--nnz", type=int, default=16 << 20, help="non-zeros for --case permute")
+    ap.add_argument("--config", choices=sorted(CONFIGS), default="C2",
+                    help="--case step: C1 fd2d 16^2 L^2, C2 fd3d 64^3 L.Dx + permute (the metric's), "
+                         "C3 R-MAT 1e7 DCSR, C3b R-MAT 2^18 CSRNA")
+    ap.add_argument("--count", type=int, default=4096, help="problems for --case batch")
+    ap.add_argument("--streams", type=int, default=16, help="stream pool for --case batch")
+    ap.add_argument("--per-kind", action="store_true", help="--case batch: also time each kind alone")
     return ap.parse_args()
 
 
@@ -200,13 +206,32 @@ def profiled_traffic(kernel):
 # the step
 # ---------------------------------------------------------------------------
 
-class Fd3dStep:
-    def __init__(self, device):
+CONFIGS = {
+    # name: (synth constructor, workload label)
+    "C1": ("config_fd2d", "fd2d_laplacian5_16^2_squared"),
+    "C2": ("config_fd3d", WORKLOAD),
+    "C3": ("config_rmat_dcsr", "rmat_2^20x2^20x2^12_1e7_each_a_ijk_b_ljk"),
+    "C3b": ("config_rmat_na", "rmat_2^14x2^14x2^12_2^18_each_mode2_x_mode0"),
+}
+
+
+def c_dims_of(cfg):
+    """Dims of the product: A's free modes in order, then B's."""
+    A, B = cfg["A"], cfg["B"]
+    fa = [d for t, d in enumerate(A["dims"]) if t not in cfg["modes_a"]]
+    fb = [d for t, d in enumerate(B["dims"]) if t not in cfg["modes_b"]]
+    return fa + fb
+
+
+class ConfigStep:
+    """One pass of the hot path on a configuration: contract (with whatever
+    operand permutations and conversions its plan needs) and, when the
+    configuration asks for it, permute the product."""
+
+    def __init__(self, cfg, device):
         import torch
         import paper_1802_02619_gb300 as lco
-        import synth
         self.torch, self.lco = torch, lco
-        cfg = synth.config_fd3d()
         self.cfg = cfg
         self.A = lco.LcoTensor.from_host(cfg["A"], device)
         self.B = lco.LcoTensor.from_host(cfg["B"], device)
@@ -219,27 +244,44 @@ class Fd3dStep:
         assert r["status"] == 0, r
         self.f = r["f"]
         self.plan.ensure_workspace(self.f, device)
-        self.c_liv = torch.empty(self.f, dtype=torch.int64, device=device)
-        self.c_val = torch.empty(self.f, dtype=torch.float64, device=device)
+        self.c_liv = torch.empty(max(self.f, 1), dtype=torch.int64, device=device)
+        self.c_val = torch.empty(max(self.f, 1), dtype=torch.float64, device=device)
         self.plan.run(self.A, self.B, self.c_liv, self.c_val)
         r = self.plan.result()
         assert r["status"] == 0, r
         self.nnz_c = r["nnz_c"]
+        self.nzr_b = r["nzr_b"]
         self.alg = r["alg"]
-        self.perm = lco.Permuter(self.plan.c_dims, self.plan.c_sig, cfg["permute_sig"], self.nnz_c, device)
-        self.p_liv = torch.empty(self.nnz_c, dtype=torch.int64, device=device)
-        self.p_val = torch.empty(self.nnz_c, dtype=torch.float64, device=device)
+        self.perm = None
+        if "permute_sig" in cfg:
+            self.perm = lco.Permuter(self.plan.c_dims, self.plan.c_sig, cfg["permute_sig"], self.nnz_c, device)
+            self.p_liv = torch.empty(self.nnz_c, dtype=torch.int64, device=device)
+            self.p_val = torch.empty(self.nnz_c, dtype=torch.float64, device=device)
+        self.out_liv = self.p_liv if self.perm else self.c_liv[:self.nnz_c]
+        self.out_val = self.p_val if self.perm else self.c_val[:self.nnz_c]
         self.units = self.A.nnz + self.B.nnz + self.nnz_c
+        # tensors the radix engine permutes in one step
+        info = self.plan.info
+        self.permuted = ([self.A.nnz] if info["permute_a"] else []) + \
+            ([self.B.nnz] if info["permute_b"] else []) + ([self.nnz_c] if self.perm else [])
 
     def contract(self):
         self.plan.run(self.A, self.B, self.c_liv, self.c_val)
 
     def permute(self):
-        self.perm(self.c_liv[:self.nnz_c], self.c_val[:self.nnz_c], self.p_liv, self.p_val)
+        if self.perm:
+            self.perm(self.c_liv[:self.nnz_c], self.c_val[:self.nnz_c], self.p_liv, self.p_val)
 
     def __call__(self):
         self.contract()
         self.permute()
+
+
+def load_config(name):
+    import synth
+    ctor, label = CONFIGS[name]
+    cfg = getattr(synth, ctor)()
+    return cfg, label
 
 
 def run_lco(args):
@@ -248,14 +290,15 @@ def run_lco(args):
     rank, world, local = dist_setup()
     device = f"cuda:{local}"
     lib = lco.load()
-    step = Fd3dStep(device)
+    cfg, workload = load_config(args.config)
+    step = ConfigStep(cfg, device)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
 
-    # sanity: the permuted output is ascending and holds every product entry
+    # sanity: the output is strictly ascending
     step()
     torch.cuda.synchronize()
-    assert bool((step.p_liv[1:] > step.p_liv[:-1]).all()), "permuted LIVs not ascending"
+    assert bool((step.out_liv[1:] > step.out_liv[:-1]).all()), "output LIVs not ascending"
 
     # ---- warm-up and graph capture ----
     for _ in range(max(args.warmup, 3)):
@@ -294,6 +337,7 @@ def run_lco(args):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
+    step_sorted = sorted(step_ms)
     total_ms_max = reduce_max(total_ms, world)
     ms_per_step = total_ms_max / K
     value = world * step.units * K / (total_ms_max * 1e-3) / 1e9
@@ -340,24 +384,27 @@ def run_lco(args):
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nnz_a": step.A.nnz, "nnz_b": step.B.nnz, "nnz_c": step.nnz_c,
-                   "f": step.f, "alg": step.alg, "permute_keys": step.nnz_c,
+        "config": {"workload": workload, "name": args.config, "nnz_a": step.A.nnz, "nnz_b": step.B.nnz,
+                   "nnz_c": step.nnz_c, "f": step.f, "alg": step.alg, "permuted_keys": step.permuted,
                    "l2": "flushed before every step (256 MiB memset, outside the step events)",
                    "graph": "each step replayed from one CUDA graph", "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "gpu_launches": int(round(launches_per_step * K)),
         "clocks": clk,
+        "latency_ms": {"p50": round(step_sorted[len(step_sorted) // 2], 5),
+                       "p99": round(step_sorted[min(len(step_sorted) - 1, int(0.99 * len(step_sorted)))], 5)},
         "breakdown": {"contract_ms": round(statistics.median(phase_c), 5),
                       "permute_ms": round(statistics.median(phase_p), 5),
                       "contract_gnnz_s": round(step.units / (statistics.median(phase_c) * 1e-3) / 1e9, 3),
-                      "permute_gkeys_s": round(step.nnz_c / (statistics.median(phase_p) * 1e-3) / 1e9, 3),
+                      "permute_gkeys_s": (round(step.nnz_c / (statistics.median(phase_p) * 1e-3) / 1e9, 3)
+                                          if step.perm else None),
                       "kernels": {k: {kk: round(vv, 5) for kk, vv in v.items()} for k, v in kernels.items()},
                       "wall_s_timed_region": round(wall, 4)},
     }
     if not args.no_e2e:
         out["e2e"] = run_e2e(step, device, min(K, 200), world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(step.cfg, budget_s=12.0)
+        out["cpu_baseline"] = cpu_baseline(cfg, budget_s=12.0)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -366,20 +413,25 @@ def run_lco(args):
 
 
 def algorithmic_bytes(kernel, step):
-    """Bytes the method must move per launch of `kernel` (lower bound)."""
+    """Bytes the method must move per launch of `kernel` (lower bound).
+    Radix kernels are charged per element of the tensor they permute (the
+    mean over the step's permuted tensors, exact when there is one)."""
     nA, nB, nC = step.A.nnz, step.B.nnz, step.nnz_c
+    nperm = statistics.mean(step.permuted) if step.permuted else 0
     if kernel == "k_rows":
         return 16 * (nA + nB + nC)            # read L and R once, write C
     if kernel == "k_row_table":
         return 8 * nA                         # row work offsets (upper bound: one row per entry)
     if kernel == "k_radix_scatter":
-        return 32 * nC                        # read key+value, write key+value
+        return int(32 * nperm)                # read key+value, write key+value
     if kernel in ("k_radix_upsweep", "k_radix_hist"):
-        return 8 * nC                         # read keys
+        return int(8 * nperm)                 # read keys
     if kernel == "k_work_scan":
         return 16 * nA                        # read L's LIVs, write the work prefix
     if kernel == "k_csr_rowptr":
         return 8 * nB + 8 * (step.plan.info["k"] + 1)
+    if kernel == "k_dcsr_build":
+        return 8 * nB + 16 * step.nzr_b       # read R's LIVs, write row ids and pointers
     return 0
 
 
@@ -400,8 +452,8 @@ def run_e2e(step, device, K, world):
         for h, d in zip(A_h, dev_bufs):
             d.copy_(h, non_blocking=True)
         step()
-        out_liv.copy_(step.p_liv, non_blocking=True)
-        out_val.copy_(step.p_val, non_blocking=True)
+        out_liv.copy_(step.out_liv, non_blocking=True)
+        out_val.copy_(step.out_val, non_blocking=True)
         stream.synchronize()
 
     for _ in range(3):
@@ -427,14 +479,16 @@ def cpu_baseline(cfg, budget_s=12.0):
     while True:
         t0 = time.perf_counter()
         liv, val, _ = oracle.contract(A, B, cfg["modes_a"], cfg["modes_b"])
-        oracle.permute([64] * 6, [5, 4, 3, 2, 1, 0], cfg["permute_sig"], liv, val)
+        if "permute_sig" in cfg:
+            cd = c_dims_of(cfg)
+            oracle.permute(cd, list(range(len(cd) - 1, -1, -1)), cfg["permute_sig"], liv, val)
         times.append(time.perf_counter() - t0)
         units = len(A["liv"]) + len(B["liv"]) + len(liv)
         if time.perf_counter() - t_start > budget_s or len(times) >= 5:
             break
     t = statistics.median(times)
     return {"value": round(units / t / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{len(times)} full workload step(s) (contraction + permutation), median {t:.3f} s"}
+            "sample": f"{len(times)} full workload step(s), median {t:.3f} s"}
 
 
 # ---------------------------------------------------------------------------
@@ -446,20 +500,22 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    import synth
-    cfg = synth.config_fd3d()
+    cfg, workload = load_config(args.config)
     A, B = cfg["A"], cfg["B"]
     nA, nB = len(A["liv"]), len(B["liv"])
-    # bounded sample: the leading rows of A (row blocks of the output grid)
+    total_a = int(np.prod(np.asarray(A["dims"], dtype=np.float64)))
+
+    # bounded sample: the leading rows of A (A is row-major, so a LIV prefix)
     def sample(frac):
-        m = 64 ** 3
-        keep = A["liv"] < int(frac * m) * (64 ** 3)
+        keep = A["liv"] < int(frac * total_a)
         return {"dims": A["dims"], "sig": A["sig"], "liv": A["liv"][keep], "val": A["val"][keep]}
 
     def one(As):
         t0 = time.perf_counter()
         liv, val, _ = oracle.contract(As, B, cfg["modes_a"], cfg["modes_b"])
-        oracle.permute([64] * 6, [5, 4, 3, 2, 1, 0], cfg["permute_sig"], liv, val)
+        if "permute_sig" in cfg:
+            cd = c_dims_of(cfg)
+            oracle.permute(cd, list(range(len(cd) - 1, -1, -1)), cfg["permute_sig"], liv, val)
         return time.perf_counter() - t0, len(As["liv"]) + nB + len(liv)
 
     t_full, _ = one(A)
@@ -481,7 +537,7 @@ def run_reference(args):
            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "nnz_a": nA, "nnz_b": nB},
+           "config": {"workload": workload, "name": args.config, "nnz_a": nA, "nnz_b": nB},
            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -521,10 +577,190 @@ def run_permute_case(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# batched workload: thousands of small contractions
+# ---------------------------------------------------------------------------
+
+def _lco_tensor(T, device):
+    import torch
+    import paper_1802_02619_gb300 as lco
+    if isinstance(T["liv"], torch.Tensor):
+        return lco.LcoTensor(list(T["dims"]), list(T["sig"]), T["liv"].to(device), T["val"].to(device))
+    return lco.LcoTensor.from_host(T, device)
+
+
+def batch_workload(count, seed, device):
+    """The batch mix with its admission rule: a drawn item is kept only if
+    its product count f is at most 16 (nnz_A + nnz_B) (f from the library's
+    symbolic phase); rejected items are redrawn from the next seed."""
+    import paper_1802_02619_gb300 as lco
+    import synth
+
+    def admit(A, B, ma, mb):
+        At, Bt = _lco_tensor(A, device), _lco_tensor(B, device)
+        p = lco.ContractPlan(At.dims, At.sig, At.nnz, Bt.dims, Bt.sig, Bt.nnz, ma, mb)
+        p.ensure_workspace(0, device)
+        p.symbolic(At, Bt)
+        return p.result()["f"] <= 16 * (At.nnz + Bt.nnz)
+
+    probs = synth.batch_problems(count=count, seed=seed, admit=admit, device=device)
+    items = [(_lco_tensor(A, device), _lco_tensor(B, device), ma, mb) for A, B, ma, mb, _ in probs]
+    return probs, items
+
+
+def run_batch_case(args):
+    """C4: args.count problems (1/4 2D FD, 1/4 3D FD, 1/2 R-MAT) contracted
+    as one batch replayed from a CUDA graph, against the plain loop of one
+    contraction call per problem with a stream synchronisation after each
+    (plans and workspaces prepared in advance for both)."""
+    import torch
+    import paper_1802_02619_gb300 as lco
+    device = "cuda"
+    t_gen = time.perf_counter()
+    probs, items = batch_workload(args.count, 100, device)
+    t_gen = time.perf_counter() - t_gen
+    kinds = {}
+    for *_x, kind in probs:
+        kinds[kind] = kinds.get(kind, 0) + 1
+    batch = lco.Batch(items, nstreams=args.streams)
+    batch.run()
+    outs = batch.results()
+    nnz_in = sum(A.nnz + B.nnz for A, B, _a, _b in items)
+    nnz_c = sum(C.nnz for C in outs)
+    units = nnz_in + nnz_c
+    algs = {}
+    for inf in batch.info:
+        algs[inf["alg"]] = algs.get(inf["alg"], 0) + 1
+    stream = torch.cuda.current_stream()
+
+    # ---- batched: one graph replay per step ----
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    t_cap = time.perf_counter()
+    with torch.cuda.stream(side):
+        batch.run()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=side):
+            batch.run()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    t_cap = time.perf_counter() - t_cap
+    n0 = lco.launch_count()
+    batch.run()
+    torch.cuda.synchronize()
+    launches_per_step = lco.launch_count() - n0
+    for _ in range(max(args.warmup, 3)):
+        graph.replay()
+    torch.cuda.synchronize()
+    K = args.steps
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_batch = e0.elapsed_time(e1) / K
+    for C, C2 in zip(outs, batch.results()):
+        assert torch.equal(C.liv, C2.liv), "graph replay changed a result"
+
+    # ---- plain loop: one call per problem, stream sync after each ----
+    plans = []
+    for (A, B, ma, mb), f in zip(items, batch.f):
+        p = lco.ContractPlan(A.dims, A.sig, A.nnz, B.dims, B.sig, B.nnz, ma, mb)
+        p.ensure_workspace(f, device)
+        plans.append(p)
+    c_liv = [batch.c_liv_all[o:o + f] for o, f in zip(batch.c_off, batch.f)]
+    c_val = [batch.c_val_all[o:o + f] for o, f in zip(batch.c_off, batch.f)]
+
+    def plain():
+        for p, (A, B, _a, _b), cl, cv in zip(plans, items, c_liv, c_val):
+            p.run(A, B, cl, cv)
+            stream.synchronize()
+
+    plain()
+    Kp = max(1, min(K, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(Kp):
+        plain()
+    ms_plain = (time.perf_counter() - t0) * 1e3 / Kp
+
+    out = {
+        "metric": "batched contraction GNNZ/s", "value": round(units / (ms_batch * 1e-3) / 1e9, 4),
+        "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_batch, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batch of {args.count}: fd2d/fd3d self-compositions + R-MAT Eq.14/Eq.16/SOP",
+                   "kinds": kinds, "algs": algs, "nnz_in": nnz_in, "nnz_c": nnz_c, "f": sum(batch.f),
+                   "streams": args.streams, "l2": "inputs larger than L2 (no flush)",
+                   "graph": "whole batch replayed from one CUDA graph",
+                   "gen_s": round(t_gen, 2), "capture_s": round(t_cap, 2)},
+        "plain_loop": {"value": round(units / (ms_plain * 1e-3) / 1e9, 4), "unit": UNIT,
+                       "ms_per_step": round(ms_plain, 3), "steps": Kp,
+                       "what": "one contraction call per problem + stream sync, plans/workspaces prepared"},
+        "speedup_vs_plain_loop": round(ms_plain / ms_batch, 3),
+        "gpu_launches": int(launches_per_step * K),
+        "clocks": clk,
+    }
+    if args.per_kind:
+        # each kind of problem as a batch of its own (same graph replay)
+        per = {}
+        for kind in sorted(kinds):
+            sel = [it for it, pr in zip(items, probs) if pr[4] == kind]
+            bk = lco.Batch(sel, nstreams=args.streams)
+            bk.run()
+            u = sum(A.nnz + B.nnz for A, B, _a, _b in sel) + sum(C.nnz for C in bk.results())
+            g = torch.cuda.CUDAGraph()
+            side.wait_stream(stream)
+            with torch.cuda.stream(side):
+                with torch.cuda.graph(g, stream=side):
+                    bk.run()
+            stream.wait_stream(side)
+            for _ in range(3):
+                g.replay()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(K):
+                g.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / K
+            per[kind] = {"problems": len(sel), "units": u, "ms": round(ms, 3),
+                         "gnnz_s": round(u / (ms * 1e-3) / 1e9, 3)}
+            del g, bk
+        out["per_kind"] = per
+    if not args.no_cpu_baseline:
+        import oracle
+        t_start, done_units, done_t = time.perf_counter(), 0, 0.0
+        order = np.random.default_rng(1).permutation(len(probs))
+        nprob = 0
+        for i in order:
+            A, B, ma, mb, _k = probs[i]
+            Ah = {kk: (v.cpu().numpy() if hasattr(v, "cpu") else v) for kk, v in A.items()}
+            Bh = {kk: (v.cpu().numpy() if hasattr(v, "cpu") else v) for kk, v in B.items()}
+            t1 = time.perf_counter()
+            liv, _v, _ = oracle.contract(Ah, Bh, ma, mb)
+            done_t += time.perf_counter() - t1
+            done_units += len(Ah["liv"]) + len(Bh["liv"]) + len(liv)
+            nprob += 1
+            if time.perf_counter() - t_start > 12.0:
+                break
+        out["cpu_baseline"] = {"value": round(done_units / done_t / 1e9, 6), "unit": UNIT, "cores": 1,
+                               "kind": "oracle", "sample": f"{nprob} random problems of the batch"}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.case == "permute":
         run_permute_case(args)
+        return
+    if args.case == "batch":
+        run_batch_case(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -1313,7 +1313,7 @@ bool same_sig(int order, const int32_t *a, const int32_t *b) {
 struct P2Layout {
     int64_t capc, nchunks_max;
     size_t chunk_state, chunk_ctr, reduce_state, zero_bytes;
-    size_t arr[6];          // cap-sized scratch arrays (8 bytes per entry)
+    size_t arr[6];          // cap-sized scratch arrays (8 bytes per entry; 4 used off SOP)
     size_t sop_radix;
     int sop_D, sop_P;
     size_t total;
@@ -1819,9 +1819,12 @@ P2Layout p2_layout(const lco_plan *p, int64_t cap) {
     L.reduce_state = off;
     off += align_up((size_t)((L.capc + kScanTile - 1) / kScanTile + 2) * 8);
     L.zero_bytes = off;
+    // SOP: products, sorted products and the radix tmp buffer (6 arrays);
+    // row kernels: heavy-row scratch and its ping-pong buffer (4 arrays)
+    const int narr = p->acc == 2 ? 6 : 4;
     for (int i = 0; i < 6; ++i) {
         L.arr[i] = off;
-        off += align_up((size_t)L.capc * 8);
+        if (i < narr) off += align_up((size_t)L.capc * 8);
     }
     L.sop_radix = off;
     radix_digits(p->sop_bits, &L.sop_D, &L.sop_P);

@@ -331,42 +331,60 @@ def _log_uniform(rng, lo, hi):
     return float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
 
 
-def batch_problems(count=4096, seed=100, fd2d=(8, 128), fd3d=(8, 32), rmat_nnz=(1e3, 1e6),
-                   ratio=(1.0, 500.0), device="cuda"):
+BATCH_KINDS = ("fd2d", "fd3d", "rmat_eq14", "rmat_eq16", "rmat_sop")
+
+
+def batch_item(i, count, seed, attempt=0, fd2d=(16, 256), fd3d=(8, 40), rmat_nnz=(1e3, 1e6),
+               ratio=(1.0, 500.0), device="cuda"):
+    """Item i of a batch of `count` (see batch_problems), drawn from its own
+    seed sequence (seed, i, attempt) so that any item can be redrawn alone."""
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), int(i), int(attempt)]))
+    if i < count // 4:
+        n = int(round(_log_uniform(rng, *fd2d)))
+        A = stencil_operator((n, n), STENCIL_2D, rng.uniform(-1, 1, len(STENCIL_2D)))
+        return A, A, [2, 3], [0, 1], "fd2d"
+    if i < count // 2:
+        n = int(round(_log_uniform(rng, *fd3d)))
+        A = stencil_operator((n, n, n), STENCIL_3D, rng.uniform(-1, 1, len(STENCIL_3D)))
+        return A, A, [3, 4, 5], [0, 1, 2], "fd3d"
+    form = int(rng.integers(0, 3))
+    nnz = int(_log_uniform(rng, *rmat_nnz))
+    rho = _log_uniform(rng, *ratio)
+    s1, s2 = int(rng.integers(0, 2**31)), int(rng.integers(0, 2**31))
+    if form < 2:
+        # a_ijk with three equal dims; contracted dims (j,k) or (k) give the ratio
+        b = max(2, int(np.ceil(np.log2(np.sqrt(rho * nnz)))))
+        bits = (b, b, b)
+    else:
+        # M x N x N with M = N^2 (Sec. 5.2.5): flattened as in Eq. 14 both
+        # operands are N^2 x N^2 with row- and column-sparsity N^2 / nnz
+        b = max(2, int(np.ceil(np.log2(rho * nnz) / 2)))
+        bits = (2 * b, b, b)
+    A = rmat3_torch(bits, nnz, s1, device)
+    B = rmat3_torch(bits, nnz, s2, device)
+    if form == 1:
+        return A, B, [2], [2], "rmat_eq16"
+    return A, B, [1, 2], [1, 2], ("rmat_eq14" if form == 0 else "rmat_sop")
+
+
+def batch_problems(count=4096, seed=100, admit=None, max_attempts=64, **kw):
     """The batched workload: count/4 2D and count/4 3D FD operators with one
     U(-1,1) coefficient per stencil position, each composed with itself over
     its input-grid modes (grid sides log-uniform), and count/2 R-MAT pairs in
     one of the paper's three forms -- a_ijk b_ljk (Eq. 14), a_ijk b_lmk
     (Eq. 16) or M x N x N with M = N^2 (Sec. 5.2.5) -- with nnz log-uniform
-    and hyper-sparsity ratio log-uniform.  Returns (A, B, modes_a, modes_b,
+    and hyper-sparsity ratio log-uniform.  `admit(A, B, modes_a, modes_b)`,
+    when given, decides whether a drawn item is kept; a rejected item is
+    redrawn from the next attempt's seed.  Returns (A, B, modes_a, modes_b,
     kind) tuples; R-MAT tensors live on `device` as torch tensors, FD ones
-    as numpy arrays."""
-    rng = np.random.default_rng(seed)
-    n2, n3 = count // 4, count // 4
+    as numpy arrays.  Keyword arguments go to batch_item."""
     out = []
-    for _ in range(n2):
-        n = int(round(_log_uniform(rng, *fd2d)))
-        A = stencil_operator((n, n), STENCIL_2D, rng.uniform(-1, 1, len(STENCIL_2D)))
-        out.append((A, A, [2, 3], [0, 1], "fd2d"))
-    for _ in range(n3):
-        n = int(round(_log_uniform(rng, *fd3d)))
-        A = stencil_operator((n, n, n), STENCIL_3D, rng.uniform(-1, 1, len(STENCIL_3D)))
-        out.append((A, A, [3, 4, 5], [0, 1, 2], "fd3d"))
-    for _ in range(count - n2 - n3):
-        form = int(rng.integers(0, 3))
-        nnz = int(_log_uniform(rng, *rmat_nnz))
-        rho = _log_uniform(rng, *ratio)
-        s1, s2 = int(rng.integers(0, 2**31)), int(rng.integers(0, 2**31))
-        if form < 2:
-            b = max(2, int(np.ceil(np.log2(np.sqrt(rho * nnz)))))
-            bits = (b, b, b)
+    for i in range(count):
+        for attempt in range(max_attempts):
+            item = batch_item(i, count, seed, attempt, **kw)
+            if admit is None or admit(*item[:4]):
+                out.append(item)
+                break
         else:
-            b = max(2, int(np.ceil(np.log2((rho * nnz) ** 0.25))))
-            bits = (2 * b, b, b)
-        A = rmat3_torch(bits, nnz, s1, device)
-        B = rmat3_torch(bits, nnz, s2, device)
-        if form == 1:
-            out.append((A, B, [2], [2], "rmat_eq16"))
-        else:
-            out.append((A, B, [1, 2], [1, 2], "rmat_eq14" if form == 0 else "rmat_sop"))
+            raise RuntimeError(f"batch item {i}: no admissible draw in {max_attempts} attempts")
     return out
