@@ -45,6 +45,10 @@ KERNEL_SOURCES = {
     "k_rows": "paper_1802_02619_gb300/csrc/lco_contract.cu",
     "k_heavy": "paper_1802_02619_gb300/csrc/lco_contract.cu",
     "k_row_table": "paper_1802_02619_gb300/csrc/lco_contract.cu",
+    "k_row_heavy": "paper_1802_02619_gb300/csrc/lco_contract.cu",
+    "k_copy_rows": "paper_1802_02619_gb300/csrc/lco_contract.cu",
+    "k_dcsr_build": "paper_1802_02619_gb300/csrc/lco_contract.cu",
+    "k_radix_offsets": "paper_1802_02619_gb300/csrc/lco_radix.cu",
     "k_work_scan": "paper_1802_02619_gb300/csrc/lco_contract.cu",
     "k_csr_rowptr": "paper_1802_02619_gb300/csrc/lco_contract.cu",
     "k_radix_scatter": "paper_1802_02619_gb300/csrc/lco_radix.cu",
@@ -69,6 +73,8 @@ def parse_args():
                     help="--case step: C1 fd2d 16^2 L^2, C2 fd3d 64^3 L.Dx + permute (the metric's), "
                          "C3 R-MAT 1e7 DCSR, C3b R-MAT 2^18 CSRNA")
     ap.add_argument("--count", type=int, default=4096, help="problems for --case batch")
+    ap.add_argument("--max-digit-bits", type=int, default=0,
+                    help="cap on the radix digit width of the operand permutations (0: library default)")
     ap.add_argument("--streams", type=int, default=16, help="stream pool for --case batch")
     ap.add_argument("--per-kind", action="store_true", help="--case batch: also time each kind alone")
     return ap.parse_args()
@@ -228,7 +234,7 @@ class ConfigStep:
     operand permutations and conversions its plan needs) and, when the
     configuration asks for it, permute the product."""
 
-    def __init__(self, cfg, device):
+    def __init__(self, cfg, device, max_digit_bits=0):
         import torch
         import paper_1802_02619_gb300 as lco
         self.torch, self.lco = torch, lco
@@ -236,7 +242,7 @@ class ConfigStep:
         self.A = lco.LcoTensor.from_host(cfg["A"], device)
         self.B = lco.LcoTensor.from_host(cfg["B"], device)
         self.plan = lco.ContractPlan(self.A.dims, self.A.sig, self.A.nnz, self.B.dims, self.B.sig, self.B.nnz,
-                                     cfg["modes_a"], cfg["modes_b"])
+                                     cfg["modes_a"], cfg["modes_b"], max_digit_bits=max_digit_bits)
         # first run sizes the output by the product count f
         self.plan.ensure_workspace(0, device)
         self.plan.symbolic(self.A, self.B)
@@ -291,7 +297,7 @@ def run_lco(args):
     device = f"cuda:{local}"
     lib = lco.load()
     cfg, workload = load_config(args.config)
-    step = ConfigStep(cfg, device)
+    step = ConfigStep(cfg, device, args.max_digit_bits)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
 
@@ -420,7 +426,7 @@ def algorithmic_bytes(kernel, step):
     nperm = statistics.mean(step.permuted) if step.permuted else 0
     if kernel == "k_rows":
         return 16 * (nA + nB + nC)            # read L and R once, write C
-    if kernel == "k_row_table":
+    if kernel in ("k_row_table", "k_row_heavy"):
         return 8 * nA                         # row work offsets (upper bound: one row per entry)
     if kernel == "k_radix_scatter":
         return int(32 * nperm)                # read key+value, write key+value

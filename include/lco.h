@@ -274,7 +274,8 @@ int32_t lco_contract_result_get(const void *ws, lco_contract_result *out, void *
 
 typedef struct {
     int32_t alg;             /* LCO_ALG_AUTO (Table 4) or a forced lco_alg */
-    int32_t max_digit_bits;  /* radix digit width cap for operand permutations, 4..11 (0 = 11) */
+    int32_t max_digit_bits;  /* radix digit width cap for operand permutations, 1..11; 0 = the
+                                default of 9 bits (wider digits coalesce worse on random keys) */
 } lco_tune;
 
 /* lco_contract_plan with tuning hints (tune may be NULL = defaults). */

@@ -67,7 +67,20 @@ struct Mdt {                 // multiplication datatype of R
     const int64_t *aux;      // DCSR: [naux+1]
     int32_t aux_shift;
     int64_t naux;
+    const uint64_t *ec;      // DCSR, numeric phase: the symbolic phase's lookup of every L entry
 };
+
+// Entry cache word: R-row start in the low 40 bits, length above; kEcMiss
+// when either does not fit (the consumer then looks the row up itself).
+constexpr int kEcB0Bits = 40;
+constexpr uint64_t kEcB0Mask = (1ull << kEcB0Bits) - 1;
+constexpr uint64_t kEcMiss = ~0ull;
+
+__device__ __forceinline__ uint64_t ec_pack(int64_t b0, int64_t len) {
+    if (len == 0) return 0;
+    if ((uint64_t)b0 >= kEcB0Mask || (uint64_t)len >= (1ull << (64 - kEcB0Bits)) - 1) return kEcMiss;
+    return (uint64_t)b0 | ((uint64_t)len << kEcB0Bits);
+}
 
 // (start, length) of R's row c, length 0 when the row is empty.
 __device__ __forceinline__ void mdt_lookup(const Mdt &m, int64_t c, int64_t &b0, int64_t &len) {
@@ -89,6 +102,34 @@ __device__ __forceinline__ void mdt_lookup(const Mdt &m, int64_t c, int64_t &b0,
         b0 = 0;
         len = 0;
     }
+}
+
+// (start, length) of the R row that L entry e (column c) meets: from the
+// entry cache when there is one, else by lookup.
+__device__ __forceinline__ void mdt_lookup_entry(const Mdt &m, int64_t e, int64_t c, int64_t &b0, int64_t &len) {
+    if (m.ec) {
+        const uint64_t x = m.ec[e];
+        if (x != kEcMiss) {
+            b0 = (int64_t)(x & kEcB0Mask);
+            len = (int64_t)(x >> kEcB0Bits);
+            return;
+        }
+    }
+    mdt_lookup(m, c, b0, len);
+}
+
+// Same, with the column taken from L's LIV only when the cache misses.
+__device__ __forceinline__ void mdt_lookup_entry(const Mdt &m, int64_t e, const int64_t *l_liv, int64_t rbase,
+                                                 int64_t &b0, int64_t &len) {
+    if (m.ec) {
+        const uint64_t x = m.ec[e];
+        if (x != kEcMiss) {
+            b0 = (int64_t)(x & kEcB0Mask);
+            len = (int64_t)(x >> kEcB0Bits);
+            return;
+        }
+    }
+    mdt_lookup(m, l_liv[e] - rbase, b0, len);
 }
 
 // ------------------------------------------------------------------------
@@ -339,6 +380,7 @@ struct ScanArgs {
     int64_t k;
     Mdt mdt;
     int64_t *P;            // [nnz_l + 1] or null
+    uint64_t *ec;          // [nnz_l] entry cache (DCSR) or null
     int64_t *row_start;    // [nrows + 1]
     int64_t *row_id;       // [nrows]
     int64_t *row_work;     // [nrows + 1]
@@ -370,6 +412,7 @@ __global__ void __launch_bounds__(kCT) k_work_scan(const __grid_constant__ ScanA
             const int64_t c = (int64_t)(liv - row * (uint64_t)a.k);
             int64_t b0, len;
             mdt_lookup(a.mdt, c, b0, len);
+            if (a.ec) a.ec[e] = ec_pack(b0, len);
             w[i] = 1 + len;
             rows[i] = (int64_t)row;
             if ((int64_t)row != prev) heads |= 1u << i;
@@ -432,23 +475,124 @@ __global__ void __launch_bounds__(kCT) k_work_scan(const __grid_constant__ ScanA
 // Heavy rows: rows whose work exceeds kHeavyWork are listed for the
 // CTA-level heavy-row kernel.
 struct TableArgs {
+    const int64_t *row_start;
     const int64_t *row_work;
     int64_t *heavy_list;   // [nrows]
     unsigned long long *nheavy;
-    int64_t cap_rows;      // upper bound on nrows (array sizes)
+    int64_t *act_rows;     // [nrows] rows with at least one product, in order
+    unsigned long long *nact;
+    uint64_t *state;       // look-back words, one per tile of rows
+    uint32_t *tile_ctr;
     int64_t cap;           // output capacity (f must not exceed it)
     WsHeader *hdr;
 };
 
-__global__ void __launch_bounds__(256) k_row_table(const __grid_constant__ TableArgs a) {
+constexpr int kTabItems = 8;
+constexpr int kTabTile = kCT * kTabItems;
+
+// Row classification: the ordered list of rows with at least one product
+// (rows whose entries all miss R produce nothing and are dropped), and the
+// heavy rows.  A heavy row with one entry is a scaled copy of one R row and
+// stays with the light-row kernel, which copies it without sorting.
+// Without compaction (every row assumed active, as when R is not row-sparse
+// and nearly every entry meets an R row): only the heavy rows are listed.
+__global__ void __launch_bounds__(256) k_row_heavy(const __grid_constant__ TableArgs a) {
     if (a.hdr->f > a.cap) return;
     const int64_t nrows = a.hdr->nrows_l;
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows && r < a.cap_rows; r += gsz) {
-        if (a.row_work[r + 1] - a.row_work[r] > kHeavyWork) {
-            const unsigned long long h = atomicAdd(a.nheavy, 1ull);
-            a.heavy_list[h] = r;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gsz) {
+        const int64_t work = a.row_work[r + 1] - a.row_work[r];
+        if (work > kHeavyWork) {
+            const int64_t nent = a.row_start[r + 1] - a.row_start[r];
+            if (work > nent && nent > 1) {
+                const unsigned long long h = atomicAdd(a.nheavy, 1ull);
+                a.heavy_list[h] = r;
+            }
         }
+    }
+}
+
+__global__ void __launch_bounds__(kCT) k_row_table(const __grid_constant__ TableArgs a) {
+    __shared__ int64_t s_tmp[kCW + 1];
+    __shared__ int64_t s_tile, s_ex;
+    __shared__ int64_t s_work[kTabTile + 1], s_start[kTabTile + 1];
+    if (a.hdr->f > a.cap) return;
+    const int64_t nrows = a.hdr->nrows_l;
+    const int64_t ntiles = (nrows + kTabTile - 1) / kTabTile;
+    if (ntiles == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {   // no rows at all
+            *a.nact = 0;
+            a.hdr->nnz_c = 0;
+        }
+        return;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
+        __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= ntiles) break;
+        const int64_t t0 = tile * kTabTile;
+        const int64_t nt = (nrows - t0 < kTabTile ? nrows - t0 : kTabTile) + 1;   // row boundaries
+        {
+            // coalesced staging, every load in flight before the first store
+            constexpr int kStg = (kTabTile + 1 + kCT - 1) / kCT;
+            int64_t wv[kStg], sv[kStg];
+#pragma unroll
+            for (int q = 0; q < kStg; ++q) {
+                const int i = q * kCT + threadIdx.x;
+                if (i < nt) {
+                    wv[q] = a.row_work[t0 + i];
+                    sv[q] = a.row_start[t0 + i];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kStg; ++q) {
+                const int i = q * kCT + threadIdx.x;
+                if (i < nt) {
+                    s_work[i] = wv[q];
+                    s_start[i] = sv[q];
+                }
+            }
+        }
+        __syncthreads();
+        const int lb = threadIdx.x * kTabItems;
+        uint32_t act = 0;
+#pragma unroll
+        for (int i = 0; i < kTabItems; ++i) {
+            const int j = lb + i;
+            if (j + 1 < nt) {
+                const int64_t work = s_work[j + 1] - s_work[j];
+                const int64_t nent = s_start[j + 1] - s_start[j];
+                if (work > nent) {
+                    act |= 1u << i;
+                    if (work > kHeavyWork && nent > 1) {
+                        const unsigned long long h = atomicAdd(a.nheavy, 1ull);
+                        a.heavy_list[h] = t0 + j;
+                    }
+                }
+            }
+        }
+        int64_t tot;
+        const int64_t ex = block_excl<int64_t>((int64_t)__popc(act), s_tmp, &tot);
+        if (threadIdx.x < 32) {
+            if (threadIdx.x == 0) lb_store(a.state + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
+            int64_t pre = 0;
+            if (tile > 0) pre = (int64_t)lookback_warp(a.state, tile, &a.hdr->status);
+            if (threadIdx.x == 0) {
+                if (tile > 0) lb_store(a.state + tile, kFlagIncl | (uint64_t)(pre + tot));
+                s_ex = pre;
+                if (tile == ntiles - 1) {
+                    *a.nact = (unsigned long long)(pre + tot);
+                    if (pre + tot == 0) a.hdr->nnz_c = 0;
+                }
+            }
+        }
+        __syncthreads();
+        int64_t o = s_ex + ex;
+#pragma unroll
+        for (int i = 0; i < kTabItems; ++i)
+            if (act & (1u << i)) a.act_rows[o++] = t0 + lb + i;
+        __syncthreads();
     }
 }
 
@@ -531,7 +675,7 @@ __global__ void __launch_bounds__(kCT, 1) k_heavy(const __grid_constant__ HeavyA
                     const uint64_t row = divu(a.div_k, liv);
                     const int64_t c = (int64_t)(liv - row * (uint64_t)a.k);
                     int64_t b0, len;
-                    mdt_lookup(a.mdt, c, b0, len);
+                    mdt_lookup_entry(a.mdt, e, c, b0, len);
                     S.b0[j] = b0;
                     S.aval[j] = a.l_val[e];
                     len_i[q] = len;
@@ -608,7 +752,7 @@ __global__ void __launch_bounds__(kCT, 1) k_heavy(const __grid_constant__ HeavyA
                     const uint64_t liv = (uint64_t)a.l_liv[e];
                     const uint64_t row = divu(a.div_k, liv);
                     c = (int64_t)(liv - row * (uint64_t)a.k);
-                    mdt_lookup(a.mdt, c, b0, len);
+                    mdt_lookup_entry(a.mdt, e, c, b0, len);
                     av = a.l_val[e];
                 }
                 int64_t ltot;
@@ -677,7 +821,12 @@ struct RowsArgs {
     const int64_t *row_start;
     const int64_t *row_id;
     const int64_t *row_work;
-    const int64_t *row_hout;
+    int64_t *row_hout;            // heavy rows: reduced length in; long copies: output offset out
+    const int64_t *act_rows;      // rows with at least one product, in order
+    const unsigned long long *nact;
+    int64_t *copy_list;           // long single-run rows, filled from the end (shares the heavy list)
+    unsigned long long *ncopy;
+    int64_t nlist;                // length of the shared list
     int64_t *c_liv;
     double *c_val;
     int64_t cap;
@@ -691,6 +840,7 @@ struct RowsArgs {
 };
 
 constexpr int kStage = 32 * 16;           // staged outputs of a tile's register-sorted rows
+constexpr int kLaneEnt = 16;              // rows with more entries look their R rows up warp-wide
 
 // Per warp: the warp-sort buffer, later reused to stage the outputs of the
 // register-sorted rows so that they reach C as coalesced stores.
@@ -850,7 +1000,7 @@ __device__ __forceinline__ int collect_runs(const RowsArgs &a, int64_t es, int64
     }
     for (int64_t e = es; e < ee; ++e) {
         int64_t b0, len;
-        mdt_lookup(a.mdt, a.l_liv[e] - rbase, b0, len);
+        mdt_lookup_entry(a.mdt, e, a.l_liv, rbase, b0, len);
         if (len > 0) {
             if (nr < kMergeRuns) {
                 const double v = a.l_val[e];
@@ -881,15 +1031,16 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
         return;
     }
     constexpr KeyT kNone = (KeyT)~(KeyT)0;
-    const int64_t nrows = a.hdr->nrows_l;
-    const int64_t ntiles = (nrows + 31) / 32;
+    const int64_t nact = a.act_rows ? (int64_t)*a.nact : a.hdr->nrows_l;
+    const int64_t ntiles = (nact + 31) / 32;
     const uint64_t nR = (uint64_t)a.nR;
     for (;;) {
         int64_t t = 0;
         if (lane == 0) t = atomicAdd(a.tile_ctr, 1u);
         t = __shfl_sync(kFull, t, 0);
         if (t >= ntiles) break;
-        const int64_t r = t * 32 + lane;
+        const int64_t idx = t * 32 + lane;
+        const int64_t r = idx < nact ? (a.act_rows ? a.act_rows[idx] : idx) : -1;
         int kind = kRowNone;
         int64_t es = 0, ee = 0, rid = 0, pb = 0, work = 0;
         int64_t copy_b0 = 0;
@@ -897,7 +1048,7 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
         KeyT nk[kNetProd];
         double nv[kNetProd];
         int64_t cnt = 0;
-        if (r < nrows) {
+        if (r >= 0) {
             es = a.row_start[r];
             ee = a.row_start[r + 1];
             const int64_t w0 = a.row_work[r];
@@ -906,9 +1057,16 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
             pb = w0 - es;
             const int64_t nent = ee - es;
             const int64_t frow = work - nent;
-            if (work > kHeavyWork) {
+            if (frow == 0) {
+                // no entry of the row meets a non-empty R row
+                kind = kRowNone;
+            } else if (work > kHeavyWork && nent > 1) {
                 kind = kRowHeavy;
                 cnt = a.row_hout[r] & ((1ll << 62) - 1);
+            } else if (nent > kLaneEnt) {
+                // many entries, few products (work <= kHeavyWork): the warp
+                // looks the entries up in parallel and sorts in shared memory
+                kind = kRowSort;
             } else if (nent <= kNetEnt && frow <= kNetProd) {
                 // ---- register network path ----
                 kind = kRowNet;
@@ -928,7 +1086,7 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
 #pragma unroll
                 for (int s2 = 0; s2 < kNetEnt; ++s2) {
                     int64_t len = 0;
-                    if (s2 < nent) mdt_lookup(a.mdt, lv[s2] - rbase, b0[s2], len);
+                    if (s2 < nent) mdt_lookup_entry(a.mdt, es + s2, lv[s2] - rbase, b0[s2], len);
                     pre[s2] = run;
                     run += (int)len;
                 }
@@ -993,7 +1151,7 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
                 int64_t b0 = 0, len = 0;
                 double v = 0.0;
                 if (e < see) {
-                    mdt_lookup(a.mdt, a.l_liv[e] - srb, b0, len);
+                    mdt_lookup_entry(a.mdt, e, a.l_liv, srb, b0, len);
                     v = a.l_val[e];
                 }
                 int x = (int)len, tot;
@@ -1111,6 +1269,15 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
             const int64_t scnt = __shfl_sync(kFull, cnt, src);
             const int64_t scb = __shfl_sync(kFull, cbase, src);
             if (skind == kRowCopy) {
+                if (scnt > kHeavyWork) {
+                    // long copy: left to k_copy_rows, one CTA per row
+                    if (lane == src) {
+                        a.row_hout[r] = sob;
+                        const unsigned long long q = atomicAdd(a.ncopy, 1ull);
+                        a.copy_list[a.nlist - 1 - (int64_t)q] = r;
+                    }
+                    continue;
+                }
                 const int64_t b0 = __shfl_sync(kFull, copy_b0, src);
                 const double v = __shfl_sync(kFull, copy_a, src);
                 for (int64_t i = lane; i < scnt; i += 32) {
@@ -1122,7 +1289,7 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
                 const int64_t spb = __shfl_sync(kFull, pb, src);
                 bool second = false;
                 if (skind == kRowHeavy) {
-                    const int64_t rr = t * 32 + src;
+                    const int64_t rr = __shfl_sync(kFull, r, src);
                     second = (a.row_hout[rr] >> 62) & 1;
                 }
                 const uint64_t *hk = (second ? a.sk1 : a.sk0) + spb;
@@ -1130,6 +1297,49 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
                 for (int64_t i = lane; i < scnt; i += 32) {
                     a.c_liv[sob + i] = scb + (int64_t)hk[i];
                     a.c_val[sob + i] = hv[i];
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// Long single-run rows (one entry of L meets an R row of more than
+// kHeavyWork entries): the row of C is that R row scaled by the entry.
+// k_rows has placed them (row_hout[r] = output offset); one CTA copies each.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_copy_rows(const __grid_constant__ RowsArgs a) {
+    if (a.hdr->f > a.cap) return;
+    const int64_t ncopy = (int64_t)*a.ncopy;
+    for (int64_t q = blockIdx.x; q < ncopy; q += gridDim.x) {
+        const int64_t r = a.copy_list[a.nlist - 1 - q];
+        const int64_t es = a.row_start[r], ee = a.row_start[r + 1];
+        const int64_t rid = a.row_id[r];
+        int64_t b0 = 0, len = 0;
+        double v = 0.0;
+        for (int64_t e = es; e < ee && len == 0; ++e) {   // the row's one matching entry
+            mdt_lookup_entry(a.mdt, e, a.l_liv, rid * a.k, b0, len);
+            v = a.l_val[e];
+        }
+        const int64_t obase = a.row_hout[r];
+        const int64_t cbase = rid * a.nR;
+        for (int64_t i0 = 0; i0 < len; i0 += 4 * 256) {
+            int64_t rl[4];
+            double rv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = i0 + u * 256 + threadIdx.x;
+                if (i < len) {
+                    rl[u] = a.r_liv[b0 + i];
+                    rv[u] = a.r_val[b0 + i];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = i0 + u * 256 + threadIdx.x;
+                if (i < len) {
+                    a.c_liv[obase + i] = cbase + (int64_t)col_of(a.div_n, (uint64_t)a.nR, rl[u]);
+                    a.c_val[obase + i] = v * rv[u];
                 }
             }
         }
@@ -1167,7 +1377,7 @@ __global__ void __launch_bounds__(256) k_sop_expand(const __grid_constant__ SopA
         const uint64_t row = divu(a.div_k, liv);
         const int64_t c = (int64_t)(liv - row * (uint64_t)a.k);
         int64_t b0, len;
-        mdt_lookup(a.mdt, c, b0, len);
+        mdt_lookup_entry(a.mdt, e, c, b0, len);
         const int64_t po = a.P[e] - e;
         const double av = a.l_val[e];
         const int64_t rowbase = (int64_t)row * a.nR;
@@ -1280,7 +1490,7 @@ struct lco_plan {
     size_t off_p1state, p1state_bytes;
     size_t off_mdt_rowptr, off_mdt_rowid, off_mdt_aux;
     size_t off_P;                    // per-entry work prefix (SOP only)
-    size_t off_row_start, off_row_id, off_row_work, off_row_hout, off_heavy;
+    size_t off_row_start, off_row_id, off_row_work, off_row_hout, off_heavy, off_ec;
     size_t phase1_end;
 };
 
@@ -1312,7 +1522,8 @@ bool same_sig(int order, const int32_t *a, const int32_t *b) {
 // Phase-2 workspace layout (offsets from the end of the phase-1 region).
 struct P2Layout {
     int64_t capc, nchunks_max;
-    size_t chunk_state, chunk_ctr, reduce_state, zero_bytes;
+    size_t chunk_state, chunk_ctr, reduce_state, table_state, zero_bytes;
+    size_t act_rows;
     size_t arr[6];          // cap-sized scratch arrays (8 bytes per entry; 4 used off SOP)
     size_t sop_radix;
     int sop_D, sop_P;
@@ -1341,7 +1552,7 @@ int32_t lco_contract_plan(const lco_shape *a, const lco_shape *b, int32_t ncontr
 int32_t lco_contract_plan_ex(const lco_shape *a, const lco_shape *b, int32_t ncontract, const int32_t *modes_a,
                              const int32_t *modes_b, const lco_tune *tune, lco_plan **plan_out) {
     const int32_t force_alg = tune ? tune->alg : LCO_ALG_AUTO;
-    const int max_bits = tune && tune->max_digit_bits > 0 ? tune->max_digit_bits : kMaxDigitBits;
+    const int max_bits = tune && tune->max_digit_bits > 0 ? tune->max_digit_bits : kDefaultDigitBits;
     if (tune && (tune->max_digit_bits < 0 || tune->max_digit_bits > kMaxDigitBits)) return LCO_ERR_INVALID;
     if (!plan_out) return LCO_ERR_INVALID;
     *plan_out = nullptr;
@@ -1500,6 +1711,9 @@ int32_t lco_contract_plan_ex(const lco_shape *a, const lco_shape *b, int32_t nco
         p->off_mdt_aux = take((size_t)(p->naux + 1) * 8);
     }
     p->off_P = p->acc == 2 ? take((size_t)(nl + 1) * 8) : 0;
+    // DCSR: the scan keeps every entry's lookup so that phase 2 reads it
+    // instead of searching R's row ids again
+    p->off_ec = p->lookup == kLookupDcsr ? take((size_t)nl * 8) : 0;
     p->off_row_start = take((size_t)(nl + 1) * 8);
     p->off_row_id = take((size_t)nl * 8);
     p->off_row_work = take((size_t)(nl + 1) * 8);
@@ -1564,6 +1778,7 @@ Mdt make_mdt(const lco_plan *p, char *ws) {
         m.aux = reinterpret_cast<int64_t *>(ws + p->off_mdt_aux);
         m.aux_shift = p->aux_shift;
         m.naux = p->naux;
+        m.ec = reinterpret_cast<const uint64_t *>(ws + p->off_ec);
     }
     return m;
 }
@@ -1636,7 +1851,9 @@ int32_t symbolic_enqueue(const lco_plan *p, const int64_t *a_liv, const double *
     sa.div_k = make_div((uint64_t)p->k);
     sa.k = p->k;
     sa.mdt = mdt;
+    sa.mdt.ec = nullptr;   // written by this scan
     sa.P = p->acc == 2 ? reinterpret_cast<int64_t *>(ws + p->off_P) : nullptr;
+    sa.ec = p->lookup == kLookupDcsr ? reinterpret_cast<uint64_t *>(ws + p->off_ec) : nullptr;
     sa.row_start = reinterpret_cast<int64_t *>(ws + p->off_row_start);
     sa.row_id = reinterpret_cast<int64_t *>(ws + p->off_row_id);
     sa.row_work = reinterpret_cast<int64_t *>(ws + p->off_row_work);
@@ -1682,17 +1899,33 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         int64_t *row_hout = reinterpret_cast<int64_t *>(ws + p->off_row_hout);
         int64_t *heavy = reinterpret_cast<int64_t *>(ws + p->off_heavy);
         unsigned long long *nheavy = reinterpret_cast<unsigned long long *>(chunk_ctr + 4);
+        int64_t *act_rows = reinterpret_cast<int64_t *>(p2 + L.act_rows);
+        unsigned long long *nact = reinterpret_cast<unsigned long long *>(chunk_ctr + 10);
         TableArgs ta{};
+        ta.row_start = row_start;
         ta.row_work = row_work;
         ta.heavy_list = heavy;
         ta.nheavy = nheavy;
-        ta.cap_rows = p->nnz_l;
+        ta.act_rows = act_rows;
+        ta.nact = nact;
+        ta.state = reinterpret_cast<uint64_t *>(p2 + L.table_state);
+        ta.tile_ctr = chunk_ctr + 8;
         ta.cap = cap;
         ta.hdr = hdr;
-        {
+        // Rows with no product are dropped from the light-row kernel's tiles
+        // only when R is row-sparse (DCSR): then many L entries miss R.
+        // Otherwise nearly every row is active and the ordered compaction,
+        // a chain of look-backs, would cost more than it saves.
+        const bool compact = p->lookup == kLookupDcsr;
+        if (compact) {
+            // persistent CTAs over tiles of rows (the rows are at most L's entries)
+            int64_t grid = (p->nnz_l + kTabTile - 1) / kTabTile;
+            if (grid > (int64_t)sms * 2) grid = (int64_t)sms * 2;
+            LCO_LAUNCH("k_row_table", s, k_row_table<<<(unsigned)(grid > 0 ? grid : 1), kCT, 0, s>>>(ta));
+        } else {
             int64_t grid = (p->nnz_l + 1 + 255) / 256;
             if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
-            LCO_LAUNCH("k_row_table", s, k_row_table<<<(unsigned)grid, 256, 0, s>>>(ta));
+            LCO_LAUNCH("k_row_heavy", s, k_row_heavy<<<(unsigned)grid, 256, 0, s>>>(ta));
         }
         HeavyArgs ha{};
         ha.l_liv = o.l_liv;
@@ -1736,6 +1969,11 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         ra.row_id = row_id;
         ra.row_work = row_work;
         ra.row_hout = row_hout;
+        ra.act_rows = compact ? act_rows : nullptr;
+        ra.nact = nact;
+        ra.copy_list = heavy;
+        ra.ncopy = reinterpret_cast<unsigned long long *>(chunk_ctr + 6);
+        ra.nlist = p->nnz_l;
         ra.c_liv = c_liv;
         ra.c_val = c_val;
         ra.cap = cap;
@@ -1754,6 +1992,7 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         } else {
             LCO_LAUNCH("k_rows", s, k_rows<uint64_t><<<(unsigned)grid, kRowsThreads, sizeof(RowsSmem) * warps, s>>>(ra));
         }
+        LCO_LAUNCH("k_copy_rows", s, k_copy_rows<<<(unsigned)(sms * 2), 256, 0, s>>>(ra));
     } else {
         SopArgs sa{};
         sa.l_liv = o.l_liv;
@@ -1814,11 +2053,17 @@ P2Layout p2_layout(const lco_plan *p, int64_t cap) {
     L.nchunks_max = (p->nnz_l + 31) / 32 + 2;   // row tiles of the light-row kernel
     size_t off = 0;
     L.chunk_state = off;
-    L.chunk_ctr = (size_t)L.nchunks_max * 8;   // [0] row tiles, [1] reduce tiles, [2] heavy rows, [4..5] heavy count
+    // counters: [0] row tiles, [1] reduce tiles, [2] heavy rows, [4..5] heavy
+    // count, [6..7] long copies, [8] row-table tiles, [10..11] active rows
+    L.chunk_ctr = (size_t)L.nchunks_max * 8;
     off += align_up((size_t)L.nchunks_max * 8 + 64);
     L.reduce_state = off;
     off += align_up((size_t)((L.capc + kScanTile - 1) / kScanTile + 2) * 8);
+    L.table_state = off;
+    off += align_up((size_t)((p->nnz_l + kTabTile - 1) / kTabTile + 2) * 8);
     L.zero_bytes = off;
+    L.act_rows = off;
+    off += align_up((size_t)(p->nnz_l > 0 ? p->nnz_l : 1) * 8);
     // SOP: products, sorted products and the radix tmp buffer (6 arrays);
     // row kernels: heavy-row scratch and its ping-pong buffer (4 arrays)
     const int narr = p->acc == 2 ? 6 : 4;

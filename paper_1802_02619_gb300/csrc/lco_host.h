@@ -21,7 +21,7 @@ struct RpPlan {
     int32_t identity;    // new order equals old order
 };
 
-int32_t rp_plan(const lco_shape *t, const int32_t *new_sig, RpPlan *out, int max_digit_bits = kMaxDigitBits);
+int32_t rp_plan(const lco_shape *t, const int32_t *new_sig, RpPlan *out, int max_digit_bits = kDefaultDigitBits);
 // Bytes the radix engine needs for this plan on nnz elements (state + tmp buffers),
 // excluding the workspace header.
 size_t rp_region_bytes(const RpPlan &plan, int64_t nnz);

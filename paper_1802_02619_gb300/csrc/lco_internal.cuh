@@ -152,6 +152,7 @@ __device__ __forceinline__ uint64_t lookback(const uint64_t *state, int64_t tile
                     set_error(status, LCO_ERR_TIMEOUT);
                     return excl;
                 }
+                __nanosleep(64);
                 s[i] = lb_load(state + (t - i) * stride);
             }
             excl += s[i] & kValueMask;
@@ -203,11 +204,66 @@ __device__ __forceinline__ uint64_t lookback_warp(const uint64_t *state, int64_t
                     if (lane == 0) set_error(status, LCO_ERR_TIMEOUT);
                     return excl;
                 }
+                // back off briefly so that spinning warps do not crowd the L2
+                // lines their predecessors are about to publish to
+                __nanosleep(64);
                 if ((notready >> lane) & 1u) w[j] = lb_load(state + idx);
             }
         }
     }
     return excl;
+}
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA, 1-D form) completing on a shared-memory
+// mbarrier.  Addresses must be 16-byte aligned and sizes multiples of 16.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Orders this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase with the given parity; false once the spin budget is
+// spent (the caller records the error and leaves).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kSpinBudgetCycles) return false;
+    }
+    return true;
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -293,7 +293,10 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(const __grid
     const int NB = 1 << j.D;
     int64_t *s_key = reinterpret_cast<int64_t *>(smem_raw);
     double *s_val = reinterpret_cast<double *>(s_key + kRadixTile);
-    int64_t *s_run = reinterpret_cast<int64_t *>(s_val + kRadixTile);
+    int64_t *in_key = reinterpret_cast<int64_t *>(s_val + kRadixTile);   // bulk-copied input tile
+    double *in_val = reinterpret_cast<double *>(in_key + kRadixTile);
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(in_val + kRadixTile);
+    int64_t *s_run = reinterpret_cast<int64_t *>(s_bar + 2);
     int64_t *s_gbase = s_run + NB;
     uint32_t *s_whist = reinterpret_cast<uint32_t *>(s_gbase + NB);
     uint32_t *s_tstart = s_whist + kRadixWarps * NB;
@@ -315,10 +318,40 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(const __grid
     for (int d = tid; d < NB; d += kRadixThreads) s_run[d] = (int64_t)j.roffs[(int64_t)blockIdx.x * NB + d];
     const unsigned lt = lanemask_lt();
     uint32_t *wh = s_whist + warp * NB;
+    // Input tiles come in by bulk copy, the next one while the current one is
+    // ranked and scattered, when both input arrays are 16-byte aligned (tile
+    // starts are even element offsets).  An odd last element is read directly.
+    const bool bulk = ((reinterpret_cast<uintptr_t>(io.sl) | reinterpret_cast<uintptr_t>(io.sv)) & 15) == 0;
+    uint32_t parity = 0;
+    auto issue = [&](int64_t base) {
+        const int64_t m = (hi - base < (int64_t)kRadixTile ? hi - base : (int64_t)kRadixTile) & ~(int64_t)1;
+        if (m <= 0) return;
+        const uint32_t bytes = (uint32_t)(m * 8);
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(s_bar, 2 * bytes);
+        bulk_copy_g2s(in_key, io.sl + base, bytes, s_bar);
+        bulk_copy_g2s(in_val, io.sv + base, bytes, s_bar);
+    };
+    if (bulk) {
+        if (tid == 0) {
+            mbar_init(s_bar, 1);
+            if (lo < hi) issue(lo);
+        }
+        __syncthreads();
+    }
 
     for (int64_t tile_base = lo; tile_base < hi; tile_base += kRadixTile) {
         const int tile_n = (int)((hi - tile_base) < (int64_t)kRadixTile ? (hi - tile_base) : (int64_t)kRadixTile);
+        const int64_t bulk_end = bulk ? tile_base + (tile_n & ~1) : tile_base;
         for (int i = tid; i < kRadixWarps * NB; i += kRadixThreads) s_whist[i] = 0;
+        if (bulk && bulk_end > tile_base) {
+            const bool ok = mbar_wait_bounded(s_bar, parity);
+            parity ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) set_error(j.status, LCO_ERR_TIMEOUT);
+                return;
+            }
+        }
         int64_t keys[kRadixItems];
         double vals[kRadixItems];
         uint32_t digs[kRadixItems];
@@ -327,10 +360,16 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(const __grid
         for (int i = 0; i < kRadixItems; ++i) {
             const int64_t e = wbase + i * 32 + lane;
             if (e < hi) {
-                int64_t k = io.sl[e];
+                int64_t k;
+                if (e < bulk_end) {
+                    k = in_key[e - tile_base];
+                    vals[i] = in_val[e - tile_base];
+                } else {
+                    k = io.sl[e];
+                    vals[i] = io.sv[e];
+                }
                 if (io.first) k = relin(j.relin, k);
                 keys[i] = k;
-                vals[i] = io.sv[e];
                 digs[i] = (uint32_t)((divu(j.key_div, (uint64_t)k) >> shift) & mask);
             } else {
                 keys[i] = 0;
@@ -339,6 +378,8 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(const __grid
             }
         }
         __syncthreads();
+        // the input buffer is free: fetch the next tile behind this one's work
+        if (bulk && tid == 0 && tile_base + kRadixTile < hi) issue(tile_base + kRadixTile);
         // warp-level stable ranking (multi-split by ballots); the rank is packed
         // above the digit (digit < 2^11, rank < 2^13) to keep registers low
 #pragma unroll
@@ -407,7 +448,8 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(const __grid
 
 size_t scatter_smem_bytes(int D) {
     size_t NB = (size_t)1 << D;
-    return (size_t)kRadixTile * 16 + NB * 16 + (size_t)kRadixWarps * NB * 4 + NB * 4 + (size_t)kRadixTile * 2;
+    return (size_t)kRadixTile * 16 * 2 + 16 + NB * 16 + (size_t)kRadixWarps * NB * 4 + NB * 4 +
+           (size_t)kRadixTile * 2;
 }
 
 size_t upsweep_smem_bytes(int D, int P) {
@@ -437,7 +479,7 @@ constexpr size_t kHistTableBytes = (size_t)kMaxPasses * ((size_t)1 << kMaxDigitB
 int radix_ranges(int64_t n_cap) {
     const int64_t tiles = (n_cap + kRadixTile - 1) / kRadixTile;
     int64_t g = (tiles + 3) / 4;                 // at least four tiles per range
-    int64_t gmax = 3 * (int64_t)radix_sm_count();  // three scatter CTAs per SM
+    int64_t gmax = 2 * (int64_t)radix_sm_count();  // two scatter CTAs per SM (9-bit digits)
     if (gmax > 32 * kOffItems) gmax = 32 * kOffItems;
     if (g > gmax) g = gmax;
     if (g < 1) g = 1;

@@ -22,6 +22,12 @@ constexpr int kRadixItems = 8;
 constexpr int kRadixTile = kRadixThreads * kRadixItems;
 constexpr int kRadixWarps = kRadixThreads / 32;
 constexpr int kMaxDigitBits = 11;
+// Default cap on the digit width.  A scatter tile holds 2048 elements; with
+// 2^11 buckets a random key leaves about one element per bucket per tile and
+// the scattered writes no longer coalesce (measured: an 11-bit pass cost 3x
+// an 8-bit pass on 32-bit random keys), so wider digits only pay when they
+// remove a pass and the keys are clustered.  A tuning hint may raise it.
+constexpr int kDefaultDigitBits = 9;
 constexpr int kMaxPasses = 6;
 constexpr int kUpsweepCtasPerSm = 4;
 
@@ -52,8 +58,8 @@ struct RadixJob {
 };
 
 // Digit plan for a key range of `key_bits` bits, digits at most max_bits wide.
-inline void radix_digits(int key_bits, int *D, int *P, int max_bits = kMaxDigitBits) {
-    if (max_bits < 1 || max_bits > kMaxDigitBits) max_bits = kMaxDigitBits;
+inline void radix_digits(int key_bits, int *D, int *P, int max_bits = kDefaultDigitBits) {
+    if (max_bits < 1 || max_bits > kMaxDigitBits) max_bits = kDefaultDigitBits;
     if (key_bits <= 0) { *D = 1; *P = 1; return; }
     int p = (key_bits + max_bits - 1) / max_bits;
     if (p > kMaxPasses) p = kMaxPasses;

@@ -56,7 +56,7 @@ class Tuner:
         out = []
         for alg in algs:
             p = ContractPlan(A.dims, A.sig, A.nnz, B.dims, B.sig, B.nnz, modes_a, modes_b, alg=alg)
-            bits = [0, 8] if (p.info["permute_a"] or p.info["permute_b"]) else [0]
+            bits = [0, 6, 11] if (p.info["permute_a"] or p.info["permute_b"]) else [0]
             out += [(alg, b) for b in bits]
         return out
 

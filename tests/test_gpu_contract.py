@@ -245,3 +245,26 @@ def test_results_are_deterministic_on_every_branch():
         assert torch.equal(C1.liv, C2.liv), alg
         assert torch.equal(C1.val.view(torch.int64), C2.val.view(torch.int64)), alg
         assert_contract_matches(C1, A, B, [1, 2], [1, 2])
+
+
+def test_single_entry_heavy_rows_are_copies():
+    """Rows of A with one entry that meets an R row of thousands of entries
+    (the row-sparse x column-sparse shape of the R-MAT mode-2 product) are
+    scaled copies of that R row; mixed with multi-entry heavy rows and light
+    rows, for every row-oriented branch."""
+    rng = np.random.default_rng(31)
+    k, n = 64, 5000
+    b_rows = {c: np.sort(rng.choice(n, size=(3000 if c % 8 == 0 else 5), replace=False)) for c in range(k)}
+    b_co = np.array([(c, j) for c in range(k) for j in b_rows[c]])
+    B = {"dims": [k, n], "sig": [1, 0], "liv": (b_co[:, 0] * n + b_co[:, 1]).astype(np.int64),
+         "val": rng.uniform(-1, 1, len(b_co))}
+    a_co = [(r, (r * 8) % k) for r in range(40)]                   # one entry on a long R row
+    a_co += [(40 + r, c) for r in range(4) for c in (0, 8, 16)]     # multi-entry heavy rows
+    a_co += [(50 + r, c) for r in range(30) for c in (1, 2, 3)]     # light rows
+    a_co += [(90, 5)]                                               # one entry on a short row
+    a_co = np.array(sorted(a_co))
+    A = {"dims": [100, k], "sig": [1, 0], "liv": (a_co[:, 0] * k + a_co[:, 1]).astype(np.int64),
+         "val": rng.uniform(-1, 1, len(a_co))}
+    for alg in ("CSR", "CSRNA", "DCSR"):
+        C, info = _run(A, B, [1], [0], alg)
+        assert_contract_matches(C, A, B, [1], [0])
