@@ -65,7 +65,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["lco", "reference"], default="lco")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["step", "permute", "batch"], default="step",
+    ap.add_argument("--case", choices=["step", "permute", "batch", "serve"], default="step",
                     help="step: the benchmark workload; permute: a stand-alone radix permutation "
                          "of a random 6th-order 64^6 tensor (profiling aid)")
     ap.add_argument("--nnz", type=int, default=16 << 20, help="non-zeros for --case permute")
@@ -77,6 +77,8 @@ def parse_args():
                     help="cap on the radix digit width of the operand permutations (0: library default)")
     ap.add_argument("--streams", type=int, default=16, help="stream pool for --case batch")
     ap.add_argument("--per-kind", action="store_true", help="--case batch: also time each kind alone")
+    ap.add_argument("--requests", type=int, default=10000, help="--case serve: requests per run")
+    ap.add_argument("--slots", type=int, default=16, help="--case serve: requests in flight")
     return ap.parse_args()
 
 
@@ -760,6 +762,128 @@ def run_batch_case(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# served workload: Poisson arrivals against the server
+# ---------------------------------------------------------------------------
+
+def _percentiles(xs):
+    xs = sorted(xs)
+    if not xs:
+        return {"p50": None, "p99": None}
+    return {"p50": round(xs[len(xs) // 2], 1), "p99": round(xs[min(len(xs) - 1, int(0.99 * len(xs)))], 1),
+            "max": round(xs[-1], 1)}
+
+
+def run_serve_case(args):
+    """C5: 128 resident problems (32 2D FD 16^2..256^2, 32 3D FD, 64 R-MAT
+    pairs of 1e3..1e6 non-zeros in the batch forms); requests pick a problem
+    uniformly (seed 200).  Saturation throughput from a burst of all
+    requests; then Poisson arrivals at 0.5x and 0.8x that rate, latency =
+    completion - arrival.  The plain path serves the same arrivals with one
+    contraction call and one stream synchronisation per request, in order."""
+    import threading as th
+    import torch
+    import paper_1802_02619_gb300 as lco
+    device = "cuda"
+    probs, items = batch_workload(128, 300, device)
+    rng = np.random.default_rng(200)
+    N = args.requests
+    pick = rng.integers(0, len(items), size=N)
+    srv = lco.Server(pool_bytes=64 << 30, nslots=args.slots)
+    handles = [(srv.put(A), srv.put(B)) for A, B, _a, _b in items]
+    # units of each problem (nnz_A + nnz_B + nnz_C), from one served run
+    units = []
+    for (ha, hb), (A, B, ma, mb) in zip(handles, items):
+        r = srv.wait(srv.submit(ha, hb, ma, mb))
+        assert r["status"] == 0, r
+        units.append(A.nnz + B.nnz + r["C"].nnz)
+    for rid in range(1, len(items) + 1):
+        srv.release(rid)
+
+    def serve_run(arrivals):
+        """Submit request k at arrivals[k] (seconds from start; None: all at
+        once); a collector thread waits and releases in submission order."""
+        rids = [0] * N
+        ready = [th.Event() for _ in range(N)]
+        lat, done_t = [0.0] * N, [0.0] * N
+
+        def collect():
+            for k in range(N):
+                ready[k].wait()
+                r = srv.wait(rids[k])
+                assert r["status"] == 0, r
+                lat[k] = r["done_us"] - r["submit_us"]
+                done_t[k] = r["done_us"]
+                srv.release(rids[k])
+
+        t = th.Thread(target=collect)
+        t.start()
+        t0 = time.perf_counter()
+        for k in range(N):
+            if arrivals is not None:
+                while time.perf_counter() - t0 < arrivals[k]:
+                    pass
+            ha, hb = handles[pick[k]]
+            A, B, ma, mb = items[pick[k]]
+            rids[k] = srv.submit(ha, hb, ma, mb)
+            ready[k].set()
+        t.join()
+        wall = time.perf_counter() - t0
+        u = sum(units[i] for i in pick)
+        return {"requests_per_s": round(N / wall, 1), "gnnz_s": round(u / wall / 1e9, 4),
+                "latency_us": _percentiles(lat), "wall_s": round(wall, 3)}
+
+    serve_run(None)                                        # warm-up
+    sat = serve_run(None)
+    lam = sat["requests_per_s"]
+
+    # plain path: plans and workspaces made in advance, one call + sync per request
+    plans, outs = [], []
+    for A, B, ma, mb in items:
+        p = lco.ContractPlan(A.dims, A.sig, A.nnz, B.dims, B.sig, B.nnz, ma, mb)
+        p.ensure_workspace(0, device)
+        p.symbolic(A, B)
+        f = p.result()["f"]
+        p.ensure_workspace(f, device)
+        plans.append(p)
+        outs.append((torch.empty(max(f, 1), dtype=torch.int64, device=device),
+                     torch.empty(max(f, 1), dtype=torch.float64, device=device)))
+    stream = torch.cuda.current_stream()
+
+    def plain_run(arrivals):
+        lat = []
+        t0 = time.perf_counter()
+        for k in range(N):
+            i = pick[k]
+            if arrivals is not None:
+                while time.perf_counter() - t0 < arrivals[k]:
+                    pass
+            A, B, _a, _b = items[i]
+            plans[i].run(A, B, outs[i][0], outs[i][1])
+            stream.synchronize()
+            lat.append((time.perf_counter() - t0 - (arrivals[k] if arrivals is not None else 0.0)) * 1e6)
+        wall = time.perf_counter() - t0
+        u = sum(units[i] for i in pick)
+        return {"requests_per_s": round(N / wall, 1), "gnnz_s": round(u / wall / 1e9, 4),
+                "latency_us": _percentiles(lat), "wall_s": round(wall, 3)}
+
+    plain_run(None)
+    plain_sat = plain_run(None)
+    rates = {}
+    for frac in (0.5, 0.8):
+        arr = np.cumsum(rng.exponential(1.0 / (frac * lam), size=N))
+        rates[str(frac)] = {"rate_per_s": round(frac * lam, 1), "served": serve_run(arr), "plain": plain_run(arr)}
+    st = srv.stats()
+    srv.close()
+    out = {"metric": "served contraction GNNZ/s", "value": rates["0.8"]["served"]["gnnz_s"], "unit": UNIT,
+           "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "128 resident problems (fd2d, fd3d, R-MAT Eq.14/Eq.16/SOP), uniform picks",
+                      "requests": N, "slots": args.slots, "pool_gb": 64},
+           "saturation": {"served": sat, "plain": plain_sat},
+           "poisson": rates, "pool_peak_gb": round(st["pool_peak"] / 2**30, 2)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.case == "permute":
@@ -767,6 +891,9 @@ def main():
         return
     if args.case == "batch":
         run_batch_case(args)
+        return
+    if args.case == "serve":
+        run_serve_case(args)
         return
     if args.impl == "reference":
         run_reference(args)

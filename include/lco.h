@@ -339,6 +339,104 @@ int32_t lco_batch_contract(lco_batch *batch, const lco_operands *ops, const int6
 int32_t lco_batch_results(const lco_batch *batch, const int64_t *caps, const void *ws,
                           lco_contract_result *out, void *stream);
 
+/* ------------------------------------------------------------------ */
+/* Device memory pool (bookkeeping over a caller-given address range;   */
+/* no paper counterpart).  The served path keeps its operands, results  */
+/* and workspaces in one such pool so that admission is a host-side    */
+/* allocation that either fits or waits.                                */
+/* ------------------------------------------------------------------ */
+
+typedef struct lco_pool lco_pool;     /* opaque host object */
+
+/* A first-fit pool over [base, base + bytes).  The pool never touches the
+ * memory itself (any address range works, including one that is not
+ * device memory); blocks are 256-byte aligned; freed neighbours merge.
+ * Errors: LCO_ERR_INVALID (null base/out, bytes < 256), LCO_ERR_OOM. */
+int32_t lco_pool_create(void *base, size_t bytes, lco_pool **pool);
+int32_t lco_pool_destroy(lco_pool *pool);
+/* *ptr = start of a free block of at least `bytes` bytes, or NULL with
+ * LCO_ERR_OOM when no free block is large enough (nothing changes). */
+int32_t lco_pool_alloc(lco_pool *pool, size_t bytes, void **ptr);
+/* Returns a block from lco_pool_alloc; LCO_ERR_INVALID for any other
+ * pointer (including a second free of the same block). */
+int32_t lco_pool_free(lco_pool *pool, void *ptr);
+/* Bytes in use, the peak of that, and the largest free block. */
+int32_t lco_pool_stats(const lco_pool *pool, size_t *used, size_t *peak, size_t *largest_free);
+
+/* ------------------------------------------------------------------ */
+/* Served contractions (continuous batching; no paper counterpart).     */
+/*                                                                      */
+/* A server owns a device memory pool and a set of worker streams.      */
+/* Operands are put once (copied into the pool) and referred to by      */
+/* handle; requests name two handles and the contracted mode pairs and  */
+/* are admitted, in arrival order, as soon as a stream slot is free and */
+/* the pool holds their workspace.  A host worker thread runs each      */
+/* request as Sec. 5.2's steps on its slot's stream -- phase 1 (f),     */
+/* an asynchronous read of f, phase 2 into a pool buffer of f entries --  */
+/* observing completion with CUDA events, so many requests are in       */
+/* flight at once and none waits on another's host round trip.  The     */
+/* arithmetic of a request is exactly that of lco_contract.             */
+/* ------------------------------------------------------------------ */
+
+typedef struct lco_server lco_server; /* opaque host object */
+
+typedef struct {
+    void *pool;            /* device memory for the pool, or NULL: the server cudaMallocs pool_bytes */
+    size_t pool_bytes;     /* size of the pool */
+    int32_t nslots;        /* requests in flight at once (1..256), one stream each */
+    int32_t device;        /* CUDA device of the pool and streams (-1: current) */
+} lco_serve_config;
+
+/* Creates the server and starts its worker thread.  Errors: LCO_ERR_INVALID,
+ * LCO_ERR_OOM (pool allocation), LCO_ERR_CUDA. */
+int32_t lco_serve_create(const lco_serve_config *cfg, lco_server **srv);
+/* Stops the worker (requests still queued fail with LCO_ERR_ADMISSION),
+ * waits for work in flight, frees everything the server allocated. */
+int32_t lco_serve_destroy(lco_server *srv);
+
+/* Copies a sorted LCO tensor (liv/val on the host or the device) into the
+ * pool and returns its handle (> 0).  Blocks until the copy is done.
+ * Errors: LCO_ERR_INVALID, LCO_ERR_OVERFLOW, LCO_ERR_ADMISSION (pool full),
+ * LCO_ERR_CUDA. */
+int32_t lco_serve_put(lco_server *srv, const lco_shape *t, const int64_t *liv, const double *val,
+                      int64_t *handle);
+/* Releases an operand; requests already submitted keep it alive. */
+int32_t lco_serve_drop(lco_server *srv, int64_t handle);
+
+/* Queues C = A x_modes B (ncontract pairs, as lco_contract_plan) on operand
+ * handles and returns its id at once.  The plan is made here, so shape
+ * errors are returned synchronously (LCO_ERR_INVALID, LCO_ERR_OVERFLOW). */
+int32_t lco_serve_submit(lco_server *srv, int64_t ha, int64_t hb, int32_t ncontract,
+                         const int32_t *modes_a, const int32_t *modes_b, uint64_t *req);
+
+typedef struct {
+    int32_t done;          /* 0 queued or running, 1 finished */
+    int32_t status;        /* LCO_OK or the request's error (device status, LCO_ERR_ADMISSION, ...) */
+    int32_t alg;           /* algorithm that ran */
+    lco_shape c;           /* shape of C (order, dims, sig; nnz = entries of C) */
+    const int64_t *c_liv;  /* device, sorted; valid until lco_serve_release */
+    const double *c_val;
+    int64_t f;             /* scalar products */
+    double submit_us;      /* host steady-clock times (microseconds, server epoch) */
+    double done_us;
+} lco_serve_result;
+
+/* Non-blocking state of a request. Errors: LCO_ERR_INVALID (unknown id). */
+int32_t lco_serve_poll(lco_server *srv, uint64_t req, lco_serve_result *out);
+/* Blocks until the request finishes or timeout_us passes (out->done says
+ * which); timeout_us < 0 waits without limit. */
+int32_t lco_serve_wait(lco_server *srv, uint64_t req, int64_t timeout_us, lco_serve_result *out);
+/* Frees a finished request's output; the pointers become invalid. */
+int32_t lco_serve_release(lco_server *srv, uint64_t req);
+
+typedef struct {
+    uint64_t submitted, completed, failed;
+    int64_t queued, in_flight;
+    size_t pool_used, pool_peak, pool_bytes;
+} lco_serve_stats;
+
+int32_t lco_serve_get_stats(const lco_server *srv, lco_serve_stats *out);
+
 #ifdef __cplusplus
 }
 #endif

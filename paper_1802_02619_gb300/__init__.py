@@ -80,6 +80,23 @@ class Operands(ctypes.Structure):
                 ("b_val", ctypes.c_void_p), ("c_liv", ctypes.c_void_p), ("c_val", ctypes.c_void_p)]
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("pool", ctypes.c_void_p), ("pool_bytes", ctypes.c_size_t), ("nslots", ctypes.c_int32),
+                ("device", ctypes.c_int32)]
+
+
+class ServeResult(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int32), ("alg", ctypes.c_int32), ("c", Shape),
+                ("c_liv", ctypes.c_void_p), ("c_val", ctypes.c_void_p), ("f", ctypes.c_int64),
+                ("submit_us", ctypes.c_double), ("done_us", ctypes.c_double)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("queued", ctypes.c_int64), ("in_flight", ctypes.c_int64), ("pool_used", ctypes.c_size_t),
+                ("pool_peak", ctypes.c_size_t), ("pool_bytes", ctypes.c_size_t)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -133,6 +150,24 @@ _SIGNATURES = {
                            ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int32),
     "lco_batch_results": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ContractResult),
                           ctypes.c_void_p], ctypes.c_int32),
+    "lco_pool_create": ([ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int32),
+    "lco_pool_destroy": ([ctypes.c_void_p], ctypes.c_int32),
+    "lco_pool_alloc": ([ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int32),
+    "lco_pool_free": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "lco_pool_stats": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                        ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int32),
+    "lco_serve_create": ([ctypes.POINTER(ServeConfig), ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int32),
+    "lco_serve_destroy": ([ctypes.c_void_p], ctypes.c_int32),
+    "lco_serve_put": ([ctypes.c_void_p, ctypes.POINTER(Shape), ctypes.c_void_p, ctypes.c_void_p,
+                       ctypes.POINTER(ctypes.c_int64)], ctypes.c_int32),
+    "lco_serve_drop": ([ctypes.c_void_p, ctypes.c_int64], ctypes.c_int32),
+    "lco_serve_submit": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int32),
+    "lco_serve_poll": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ServeResult)], ctypes.c_int32),
+    "lco_serve_wait": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ServeResult)],
+                       ctypes.c_int32),
+    "lco_serve_release": ([ctypes.c_void_p, ctypes.c_uint64], ctypes.c_int32),
+    "lco_serve_get_stats": ([ctypes.c_void_p, ctypes.POINTER(ServeStats)], ctypes.c_int32),
 }
 
 
@@ -542,3 +577,143 @@ class Batch:
             out.append(LcoTensor(self.info[i]["c_dims"], self.info[i]["c_sig"], self.c_liv_all[o:o + nc],
                                  self.c_val_all[o:o + nc]))
         return out
+
+
+# ---------------------------------------------------------------------------
+# Device memory pool and served contractions
+# ---------------------------------------------------------------------------
+
+class Pool:
+    """First-fit bookkeeping over [base, base + nbytes) (see lco_pool_* in
+    include/lco.h); the pool never touches the memory."""
+
+    def __init__(self, base: int, nbytes: int):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        _check(self.lib.lco_pool_create(ctypes.c_void_p(base), ctypes.c_size_t(nbytes), ctypes.byref(h)),
+               "lco_pool_create")
+        self.handle = h
+
+    def alloc(self, nbytes: int) -> Optional[int]:
+        p = ctypes.c_void_p()
+        rc = self.lib.lco_pool_alloc(self.handle, ctypes.c_size_t(nbytes), ctypes.byref(p))
+        if rc == 4:          # LCO_ERR_OOM
+            return None
+        _check(rc, "lco_pool_alloc")
+        return int(p.value)
+
+    def free(self, ptr: int):
+        _check(self.lib.lco_pool_free(self.handle, ctypes.c_void_p(ptr)), "lco_pool_free")
+
+    def stats(self):
+        u, pk, lf = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+        _check(self.lib.lco_pool_stats(self.handle, ctypes.byref(u), ctypes.byref(pk), ctypes.byref(lf)),
+               "lco_pool_stats")
+        return {"used": u.value, "peak": pk.value, "largest_free": lf.value}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.lco_pool_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DeviceArray:
+    """A device pointer exposed through the CUDA array interface, so that
+    torch can view library-owned memory without copying."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def _view(ptr, n, dtype, device):
+    if n == 0 or not ptr:
+        return torch.empty(0, dtype=dtype, device=device)
+    typestr = "<i8" if dtype == torch.int64 else "<f8"
+    return torch.as_tensor(_DeviceArray(int(ptr), int(n), typestr), device=device)
+
+
+class Server:
+    """Served contractions (see lco_serve_* in include/lco.h): operands are
+    put once and named by handle; submit() returns at once and a worker
+    thread in the library runs each request on one of `nslots` streams."""
+
+    def __init__(self, pool_bytes: int, nslots: int = 16, device=None):
+        self.lib = load()
+        dev = torch.device(device or "cuda")
+        self.device = dev
+        cfg = ServeConfig()
+        cfg.pool = None
+        cfg.pool_bytes = int(pool_bytes)
+        cfg.nslots = int(nslots)
+        cfg.device = dev.index if dev.index is not None else torch.cuda.current_device()
+        h = ctypes.c_void_p()
+        _check(self.lib.lco_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "lco_serve_create")
+        self.handle = h
+
+    def put(self, t: LcoTensor) -> int:
+        sh = t.shape()
+        hdl = ctypes.c_int64()
+        torch.cuda.current_stream(t.liv.device).synchronize()
+        _check(self.lib.lco_serve_put(self.handle, ctypes.byref(sh), _ptr(t.liv), _ptr(t.val), ctypes.byref(hdl)),
+               "lco_serve_put")
+        return int(hdl.value)
+
+    def drop(self, handle: int):
+        _check(self.lib.lco_serve_drop(self.handle, ctypes.c_int64(handle)), "lco_serve_drop")
+
+    def submit(self, ha: int, hb: int, modes_a, modes_b) -> int:
+        if len(modes_a) != len(modes_b):
+            raise ValueError("modes_a and modes_b must pair up")
+        ma, mb = _sig_arr(modes_a), _sig_arr(modes_b)
+        rid = ctypes.c_uint64()
+        _check(self.lib.lco_serve_submit(self.handle, ctypes.c_int64(ha), ctypes.c_int64(hb), len(modes_a), ma, mb,
+                                         ctypes.byref(rid)), "lco_serve_submit")
+        return int(rid.value)
+
+    def _result(self, r: ServeResult) -> dict:
+        out = {"done": bool(r.done), "status": int(r.status), "alg": ALG_NAMES[r.alg] if r.done else None,
+               "f": int(r.f), "submit_us": r.submit_us, "done_us": r.done_us}
+        if r.done and r.status == 0:
+            c = r.c
+            n = int(c.nnz)
+            out["C"] = LcoTensor([c.dims[i] for i in range(c.order)], [c.sig[i] for i in range(c.order)],
+                                 _view(r.c_liv, n, torch.int64, self.device),
+                                 _view(r.c_val, n, torch.float64, self.device))
+        return out
+
+    def poll(self, req: int) -> dict:
+        r = ServeResult()
+        _check(self.lib.lco_serve_poll(self.handle, ctypes.c_uint64(req), ctypes.byref(r)), "lco_serve_poll")
+        return self._result(r)
+
+    def wait(self, req: int, timeout_us: int = -1) -> dict:
+        r = ServeResult()
+        _check(self.lib.lco_serve_wait(self.handle, ctypes.c_uint64(req), ctypes.c_int64(timeout_us),
+                                       ctypes.byref(r)), "lco_serve_wait")
+        return self._result(r)
+
+    def release(self, req: int):
+        _check(self.lib.lco_serve_release(self.handle, ctypes.c_uint64(req)), "lco_serve_release")
+
+    def stats(self) -> dict:
+        st = ServeStats()
+        _check(self.lib.lco_serve_get_stats(self.handle, ctypes.byref(st)), "lco_serve_get_stats")
+        return {k: getattr(st, k) for k, _ in ServeStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.lco_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -21,7 +21,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 SO_PATH = os.path.join(OUT_DIR, "liblco.so")
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-DLCO_BUILD_ARCH=1030",
+COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-pthread", "-DLCO_BUILD_ARCH=1030",
           "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
 
 
@@ -75,7 +75,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         tmp = SO_PATH + f".tmp{os.getpid()}"
         cuda_lib = "/usr/local/cuda/lib64"
         cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH_FLAGS + \
-            ["-cudart", "shared", "-Xlinker", f"-rpath,{cuda_lib}"]
+            ["-cudart", "shared", "-lpthread", "-Xlinker", f"-rpath,{cuda_lib}"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link of liblco.so failed:\n{r.stderr}")

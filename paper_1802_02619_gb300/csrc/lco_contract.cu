@@ -2078,6 +2078,29 @@ P2Layout p2_layout(const lco_plan *p, int64_t cap) {
     return L;
 }
 
+}  // namespace
+
+// The parts of a contraction workspace that must be zero before its first
+// use (everything else is written before it is read, or reset by the phases
+// themselves): the radix engines' digit-histogram tables.  Lets a caller run
+// on recycled memory without clearing the whole workspace.
+cudaError_t contract_ws_init(const lco_plan *p, void *ws, int64_t cap, cudaStream_t s) {
+    char *w = reinterpret_cast<char *>(ws);
+    if (p->need_l || p->need_r) {
+        cudaError_t e = cudaMemsetAsync(w + p->off_rp, 0, radix_hist_table_bytes(), s);
+        if (e != cudaSuccess) return e;
+    }
+    if (p->acc == 2 && cap >= 0) {
+        const P2Layout L = p2_layout(p, cap);
+        return cudaMemsetAsync(w + p->phase1_end + L.sop_radix, 0, radix_hist_table_bytes(), s);
+    }
+    return cudaSuccess;
+}
+
+size_t contract_phase1_bytes(const lco_plan *p) { return p->phase1_end; }
+
+namespace {
+
 int32_t check_ws(const lco_plan *p, void *ws, size_t ws_bytes, int64_t cap) {
     if (!ws) return LCO_ERR_INVALID;
     if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return LCO_ERR_INVALID;

@@ -39,4 +39,10 @@ RelinParams make_relin(int32_t order, const int64_t *dims, const int32_t *sig_ol
 cudaError_t relin_enqueue(const RelinParams &p, int64_t n, const int64_t *in, int64_t *out,
                           cudaStream_t stream);
 
+// Zeroes the parts of a contraction workspace (sized for capacity `cap`,
+// cap < 0: phase 1 only) that must start zeroed.
+cudaError_t contract_ws_init(const lco_plan *p, void *ws, int64_t cap, cudaStream_t s);
+// Bytes of the phase-1 region at the start of a contraction workspace.
+size_t contract_phase1_bytes(const lco_plan *p);
+
 }  // namespace lco
