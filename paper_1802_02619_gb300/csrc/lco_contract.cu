@@ -26,6 +26,7 @@
 // with decoupled look-back, so C is written once, in order.  SOP (Sec. 5.2.5) expands all f products, sorts them by output LIV
 // with the radix engine and sums runs.
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -844,17 +845,22 @@ constexpr int kLaneEnt = 16;              // rows with more entries look their R
 
 // Per warp: the warp-sort buffer, later reused to stage the outputs of the
 // register-sorted rows so that they reach C as coalesced stores.
-union RowsSmem {
-    struct {
-        uint64_t pcol[kWarpSortCap];
-        double pval[kWarpSortCap];
-    } sort;
-    struct {
-        int64_t liv[kStage];
-        double val[kStage];
-        int32_t soff[33];   // staged start of each lane's row
-        int32_t doff[32];   // tile-local output offset of each lane's row
-    } stage;
+struct RowsSmem {
+    union {
+        struct {
+            uint64_t pcol[kWarpSortCap];
+            double pval[kWarpSortCap];
+        } sort;
+        struct {
+            int64_t liv[kStage];
+            double val[kStage];
+            int32_t soff[33];   // staged start of each lane's row
+            int32_t doff[32];   // tile-local output offset of each lane's row
+        } stage;
+    };
+    // register-network rows: product values by slot ([slot][lane]: no bank
+    // conflicts); the keys (column, slot) are sorted in registers
+    double nval[16][32];
 };
 
 __device__ __forceinline__ uint64_t col_of(const DivU64 &div_n, uint64_t nR, int64_t liv) {
@@ -960,8 +966,10 @@ enum RowKind { kRowNone = -1, kRowLane = 0, kRowCopy = 1, kRowSort = 2, kRowHeav
 constexpr int kNetEnt = 8;
 constexpr int kNetProd = 16;
 
+// Bitonic network over kNetProd keys (column << 4 | slot): every key is
+// distinct, so the order is total and equal columns stay in slot order.
 template <typename KeyT>
-__device__ __forceinline__ void net_sort(KeyT (&k)[kNetProd], double (&v)[kNetProd]) {
+__device__ __forceinline__ void net_sort(KeyT (&k)[kNetProd]) {
 #pragma unroll
     for (int kk = 2; kk <= kNetProd; kk <<= 1) {
 #pragma unroll
@@ -970,14 +978,15 @@ __device__ __forceinline__ void net_sort(KeyT (&k)[kNetProd], double (&v)[kNetPr
             for (int i = 0; i < kNetProd; ++i) {
                 const int l = i ^ j;
                 if (l > i) {
-                    const bool up = (i & kk) == 0;
-                    const bool sw = up ? (k[i] > k[l]) : (k[i] < k[l]);
-                    const KeyT tk = sw ? k[l] : k[i];
-                    k[l] = sw ? k[i] : k[l];
-                    k[i] = tk;
-                    const double tv = sw ? v[l] : v[i];
-                    v[l] = sw ? v[i] : v[l];
-                    v[i] = tv;
+                    const KeyT lo = k[i] < k[l] ? k[i] : k[l];
+                    const KeyT hi = k[i] < k[l] ? k[l] : k[i];
+                    if ((i & kk) == 0) {
+                        k[i] = lo;
+                        k[l] = hi;
+                    } else {
+                        k[i] = hi;
+                        k[l] = lo;
+                    }
                 }
             }
         }
@@ -1046,7 +1055,6 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
         int64_t copy_b0 = 0;
         double copy_a = 0.0;
         KeyT nk[kNetProd];
-        double nv[kNetProd];
         int64_t cnt = 0;
         if (r >= 0) {
             es = a.row_start[r];
@@ -1067,7 +1075,7 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
                 // many entries, few products (work <= kHeavyWork): the warp
                 // looks the entries up in parallel and sorts in shared memory
                 kind = kRowSort;
-            } else if (nent <= kNetEnt && frow <= kNetProd) {
+            } else if (nent <= kNetEnt && frow <= kNetProd && (sizeof(KeyT) == 4 || nR < (1ull << 59))) {
                 // ---- register network path ----
                 kind = kRowNet;
                 const int64_t rbase = rid * a.k;
@@ -1094,7 +1102,6 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
 #pragma unroll
                 for (int q = 0; q < kNetProd; ++q) {
                     nk[q] = kNone;
-                    nv[q] = 0.0;
                     if (q < run) {
                         int sel = 0;
 #pragma unroll
@@ -1108,15 +1115,15 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
                                 psel = pre[s2];
                             }
                         const int64_t b = bsel + (q - psel);
-                        nk[q] = (KeyT)col_of(a.div_n, nR, a.r_liv[b]);
-                        nv[q] = a.l_val[es + sel] * a.r_val[b];
+                        nk[q] = ((KeyT)col_of(a.div_n, nR, a.r_liv[b]) << 4) | (KeyT)q;
+                        S.nval[q][lane] = a.l_val[es + sel] * a.r_val[b];
                     }
                 }
-                net_sort<KeyT>(nk, nv);
+                net_sort<KeyT>(nk);
                 int u = 0;
 #pragma unroll
                 for (int q = 0; q < kNetProd; ++q)
-                    u += (nk[q] != kNone) && (q == 0 || nk[q] != nk[q - 1]);
+                    u += (nk[q] != kNone) && (q == 0 || (nk[q] >> 4) != (nk[q - 1] >> 4));
                 cnt = u;
             } else {
                 int64_t st[kMergeRuns];
@@ -1208,16 +1215,18 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
 #pragma unroll
                 for (int q = 0; q < kNetProd; ++q) {
                     if (nk[q] != kNone) {
-                        if (q == 0 || nk[q] != ck) {
+                        const KeyT col = nk[q] >> 4;
+                        const double v = S.nval[(int)(nk[q] & 15)][lane];
+                        if (q == 0 || col != ck) {
                             if (o >= 0) {
                                 S.stage.liv[soff + o] = cb + (int64_t)ck;
                                 S.stage.val[soff + o] = acc;
                             }
                             ++o;
-                            ck = nk[q];
-                            acc = nv[q];
+                            ck = col;
+                            acc = v;
                         } else {
-                            acc += nv[q];
+                            acc += v;
                         }
                     }
                 }
@@ -1950,10 +1959,17 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         ha.sv1 = sv1;
         ha.ctr = chunk_ctr + 2;
         ha.hdr = hdr;
-        static bool attr = false;
-        if (!attr) {
+        // function attributes are per device: set them once on each
+        static std::atomic<uint64_t> attr_done{0};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const uint64_t bit = 1ull << (dev & 63);
+        if (!(attr_done.load() & bit)) {
             cudaFuncSetAttribute(k_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(HeavySmem));
-            attr = true;
+            const int rows_smem = (int)sizeof(RowsSmem) * (kRowsThreads / 32);
+            cudaFuncSetAttribute(k_rows<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem);
+            cudaFuncSetAttribute(k_rows<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem);
+            attr_done.fetch_or(bit);
         }
         LCO_LAUNCH("k_heavy", s, k_heavy<<<(unsigned)sms, kCT, sizeof(HeavySmem), s>>>(ha));
         RowsArgs ra{};

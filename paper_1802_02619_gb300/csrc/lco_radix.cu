@@ -1,4 +1,6 @@
 // lco_radix.cu -- histogram and scatter kernels of the stable LSD radix engine.
+#include <atomic>
+
 #include "lco_radix.cuh"
 
 namespace lco {
@@ -515,13 +517,17 @@ void radix_carve(RadixJob &job, char *region) {
 }
 
 cudaError_t radix_enqueue(const RadixJob &job, cudaStream_t stream) {
-    static bool attr_done = false;
-    if (!attr_done) {
+    // function attributes are per device: set them once on each
+    static std::atomic<uint64_t> attr_done{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(attr_done.load() & bit)) {
         cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)scatter_smem_bytes(kMaxDigitBits));
         cudaFuncSetAttribute(k_radix_upsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)upsweep_smem_bytes(kMaxDigitBits, kMaxPasses));
-        attr_done = true;
+        attr_done.fetch_or(bit);
     }
     if (job.n_cap <= 0) return cudaSuccess;
     const unsigned G = (unsigned)job.G;
