@@ -850,6 +850,7 @@ struct RowsSmem {
         struct {
             uint64_t pcol[kWarpSortCap];
             double pval[kWarpSortCap];
+            uint16_t pslot[kWarpSortCap];
         } sort;
         struct {
             int64_t liv[kStage];
@@ -890,11 +891,18 @@ __device__ __forceinline__ int lane_merge_g(const RowsArgs &a, const int64_t (&s
 #pragma unroll
         for (int i = 1; i < kMergeRuns; ++i) m = hk[i] < m ? hk[i] : m;
         if (m == kNone) break;
+        // products rounded before they are added, and added in run order,
+        // starting from the first: the same arithmetic as every other path
         double s = 0.0;
+        bool first = true;
 #pragma unroll
         for (int i = 0; i < kMergeRuns; ++i) {
             if (hk[i] == m) {
-                if (kWrite) s += av[i] * a.r_val[st[i] + pos[i]];
+                if (kWrite) {
+                    const double pr = __dmul_rn(av[i], a.r_val[st[i] + pos[i]]);
+                    s = first ? pr : __dadd_rn(s, pr);
+                    first = false;
+                }
                 ++pos[i];
                 hk[i] = pos[i] < ln[i] ? (KeyT)col_of(a.div_n, (uint64_t)a.nR, a.r_liv[st[i] + pos[i]]) : kNone;
             }
@@ -911,7 +919,7 @@ __device__ __forceinline__ int lane_merge_g(const RowsArgs &a, const int64_t (&s
 // Sort n (col, val) pairs in place with a bitonic network (elements at
 // n..pow2 are treated as +infinity), then sum runs of equal columns and
 // compact them to the front.  Whole warp; returns the distinct count.
-__device__ int warp_sort_reduce(uint64_t *col, double *val, int n) {
+__device__ int warp_sort_reduce(uint64_t *col, double *val, uint16_t *slot, int n) {
     const int lane = threadIdx.x & 31;
     int n2 = 1;
     while (n2 < n) n2 <<= 1;
@@ -921,13 +929,18 @@ __device__ int warp_sort_reduce(uint64_t *col, double *val, int n) {
                 const int i = 2 * j * (t / j) + (t % j);
                 const int l = (j == (kk >> 1)) ? (i ^ (kk - 1)) : (i + j);
                 const int lo = i < l ? i : l, hi = i < l ? l : i;
-                if (hi < n && col[lo] > col[hi]) {
+                // (column, slot) order: slots are generation indices, so
+                // equal columns keep generation order
+                if (hi < n && (col[lo] > col[hi] || (col[lo] == col[hi] && slot[lo] > slot[hi]))) {
                     const uint64_t tc = col[lo];
                     col[lo] = col[hi];
                     col[hi] = tc;
                     const double tv = val[lo];
                     val[lo] = val[hi];
                     val[hi] = tv;
+                    const uint16_t ts = slot[lo];
+                    slot[lo] = slot[hi];
+                    slot[hi] = ts;
                 }
             }
             __syncwarp();
@@ -1172,11 +1185,12 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
                 for (int64_t q = 0; q < len; ++q) {
                     S.sort.pcol[off + q] = col_of(a.div_n, nR, a.r_liv[b0 + q]);
                     S.sort.pval[off + q] = v * a.r_val[b0 + q];
+                    S.sort.pslot[off + q] = (uint16_t)(off + q);
                 }
                 carry += tot;
             }
             __syncwarp();
-            const int n = warp_sort_reduce(S.sort.pcol, S.sort.pval, carry);
+            const int n = warp_sort_reduce(S.sort.pcol, S.sort.pval, S.sort.pslot, carry);
             for (int i = lane; i < n; i += 32) {
                 a.sk0[spb + i] = S.sort.pcol[i];
                 a.sv0[spb + i] = S.sort.pval[i];

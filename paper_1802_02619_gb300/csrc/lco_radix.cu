@@ -382,19 +382,16 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(const __grid
         __syncthreads();
         // the input buffer is free: fetch the next tile behind this one's work
         if (bulk && tid == 0 && tile_base + kRadixTile < hi) issue(tile_base + kRadixTile);
-        // warp-level stable ranking (multi-split by ballots); the rank is packed
-        // above the digit (digit < 2^11, rank < 2^13) to keep registers low
+        // warp-level stable ranking: the lanes holding the same digit find each
+        // other with one match instruction (invalid lanes carry a digit no
+        // valid lane has); the rank is packed above the digit (digit < 2^11,
+        // rank < 2^13) to keep registers low
 #pragma unroll
         for (int i = 0; i < kRadixItems; ++i) {
             const int64_t e = wbase + i * 32 + lane;
             const bool valid = e < hi;
-            unsigned peers = __ballot_sync(kFull, valid);
             const uint32_t d = digs[i];
-            for (int b = 0; b < j.D; ++b) {
-                const unsigned bit = (d >> b) & 1u;
-                const unsigned bal = __ballot_sync(kFull, bit);
-                peers &= bit ? bal : ~bal;
-            }
+            const unsigned peers = __match_any_sync(kFull, valid ? d : 0xffffu);
             const int leader = valid ? (__ffs(peers) - 1) : lane;
             uint32_t basev = 0;
             if (valid && lane == leader) {

@@ -268,3 +268,23 @@ def test_single_entry_heavy_rows_are_copies():
     for alg in ("CSR", "CSRNA", "DCSR"):
         C, info = _run(A, B, [1], [0], alg)
         assert_contract_matches(C, A, B, [1], [0])
+
+
+def test_row_branches_are_bit_identical():
+    """Every row branch (and the one-CTA path) multiplies each pair once,
+    rounds the product, and adds the products of an output in generation
+    order; so CSR, CSRNA, DCSR, SOP and the automatic plan agree bit for bit."""
+    rng = np.random.default_rng(44)
+    A = synth.stencil_operator((12, 12), synth.STENCIL_2D, rng.uniform(-1, 1, 5))
+    R1 = synth.rmat3((7, 7, 5), 6000, seed=45)
+    R2 = synth.rmat3((7, 7, 5), 6000, seed=46)
+    for X, Y, ma, mb in ((A, A, [2, 3], [0, 1]), (R1, R2, [1, 2], [1, 2])):
+        ref = None
+        for alg in (None, "CSR", "CSRNA", "DCSR", "SOP"):
+            C, _ = _run(X, Y, ma, mb, alg)
+            if ref is None:
+                ref = C
+                assert_contract_matches(C, X, Y, ma, mb)
+                continue
+            assert torch.equal(C.liv, ref.liv), alg
+            assert torch.equal(C.val.view(torch.int64), ref.val.view(torch.int64)), alg
