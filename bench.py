@@ -78,7 +78,8 @@ def parse_args():
     ap.add_argument("--streams", type=int, default=16, help="stream pool for --case batch")
     ap.add_argument("--per-kind", action="store_true", help="--case batch: also time each kind alone")
     ap.add_argument("--requests", type=int, default=10000, help="--case serve: requests per run")
-    ap.add_argument("--slots", type=int, default=16, help="--case serve: requests in flight")
+    ap.add_argument("--slots", type=int, default=64, help="--case serve: requests in flight")
+    ap.add_argument("--workers", type=int, default=8, help="--case serve: host worker threads")
     return ap.parse_args()
 
 
@@ -789,7 +790,7 @@ def run_serve_case(args):
     rng = np.random.default_rng(200)
     N = args.requests
     pick = rng.integers(0, len(items), size=N)
-    srv = lco.Server(pool_bytes=64 << 30, nslots=args.slots)
+    srv = lco.Server(pool_bytes=64 << 30, nslots=args.slots, nworkers=args.workers)
     handles = [(srv.put(A), srv.put(B)) for A, B, _a, _b in items]
     # units of each problem (nnz_A + nnz_B + nnz_C), from one served run
     units = []
@@ -869,6 +870,21 @@ def run_serve_case(args):
 
     plain_run(None)
     plain_sat = plain_run(None)
+
+    def api_run(n_req):
+        """The public one-call API per request (plan, workspace, two
+        synchronisations), back to back: its saturation throughput."""
+        t0 = time.perf_counter()
+        for k in range(n_req):
+            A, B, ma, mb = items[pick[k]]
+            lco.contract(A, B, ma, mb)
+        wall = time.perf_counter() - t0
+        u = sum(units[pick[k]] for k in range(n_req))
+        return {"requests_per_s": round(n_req / wall, 1), "gnnz_s": round(u / wall / 1e9, 4),
+                "requests": n_req, "wall_s": round(wall, 3)}
+
+    api_run(min(N, 200))
+    api_sat = api_run(min(N, 2000))
     rates = {}
     for frac in (0.5, 0.8):
         arr = np.cumsum(rng.exponential(1.0 / (frac * lam), size=N))
@@ -878,8 +894,10 @@ def run_serve_case(args):
     out = {"metric": "served contraction GNNZ/s", "value": rates["0.8"]["served"]["gnnz_s"], "unit": UNIT,
            "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "128 resident problems (fd2d, fd3d, R-MAT Eq.14/Eq.16/SOP), uniform picks",
-                      "requests": N, "slots": args.slots, "pool_gb": 64},
-           "saturation": {"served": sat, "plain": plain_sat},
+                      "requests": N, "slots": args.slots, "workers": args.workers, "pool_gb": 64},
+           "saturation": {"served": sat, "plain": plain_sat, "plain_api": api_sat,
+                          "served_vs_plain": round(sat["requests_per_s"] / plain_sat["requests_per_s"], 2),
+                          "served_vs_plain_api": round(sat["requests_per_s"] / api_sat["requests_per_s"], 2)},
            "poisson": rates, "pool_peak_gb": round(st["pool_peak"] / 2**30, 2)}
     print(json.dumps(out), flush=True)
 

@@ -385,9 +385,10 @@ typedef struct {
     size_t pool_bytes;     /* size of the pool */
     int32_t nslots;        /* requests in flight at once (1..256), one stream each */
     int32_t device;        /* CUDA device of the pool and streams (-1: current) */
+    int32_t nworkers;      /* host worker threads sharing the slots (0: 4) */
 } lco_serve_config;
 
-/* Creates the server and starts its worker thread.  Errors: LCO_ERR_INVALID,
+/* Creates the server and starts its worker threads.  Errors: LCO_ERR_INVALID,
  * LCO_ERR_OOM (pool allocation), LCO_ERR_CUDA. */
 int32_t lco_serve_create(const lco_serve_config *cfg, lco_server **srv);
 /* Stops the worker (requests still queued fail with LCO_ERR_ADMISSION),

@@ -82,7 +82,7 @@ class Operands(ctypes.Structure):
 
 class ServeConfig(ctypes.Structure):
     _fields_ = [("pool", ctypes.c_void_p), ("pool_bytes", ctypes.c_size_t), ("nslots", ctypes.c_int32),
-                ("device", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("nworkers", ctypes.c_int32)]
 
 
 class ServeResult(ctypes.Structure):
@@ -644,7 +644,7 @@ class Server:
     put once and named by handle; submit() returns at once and a worker
     thread in the library runs each request on one of `nslots` streams."""
 
-    def __init__(self, pool_bytes: int, nslots: int = 16, device=None):
+    def __init__(self, pool_bytes: int, nslots: int = 16, device=None, nworkers: int = 4):
         self.lib = load()
         dev = torch.device(device or "cuda")
         self.device = dev
@@ -653,6 +653,7 @@ class Server:
         cfg.pool_bytes = int(pool_bytes)
         cfg.nslots = int(nslots)
         cfg.device = dev.index if dev.index is not None else torch.cuda.current_device()
+        cfg.nworkers = int(nworkers)
         h = ctypes.c_void_p()
         _check(self.lib.lco_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "lco_serve_create")
         self.handle = h

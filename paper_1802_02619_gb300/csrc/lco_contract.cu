@@ -495,24 +495,6 @@ constexpr int kTabTile = kCT * kTabItems;
 // (rows whose entries all miss R produce nothing and are dropped), and the
 // heavy rows.  A heavy row with one entry is a scaled copy of one R row and
 // stays with the light-row kernel, which copies it without sorting.
-// Without compaction (every row assumed active, as when R is not row-sparse
-// and nearly every entry meets an R row): only the heavy rows are listed.
-__global__ void __launch_bounds__(256) k_row_heavy(const __grid_constant__ TableArgs a) {
-    if (a.hdr->f > a.cap) return;
-    const int64_t nrows = a.hdr->nrows_l;
-    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gsz) {
-        const int64_t work = a.row_work[r + 1] - a.row_work[r];
-        if (work > kHeavyWork) {
-            const int64_t nent = a.row_start[r + 1] - a.row_start[r];
-            if (work > nent && nent > 1) {
-                const unsigned long long h = atomicAdd(a.nheavy, 1ull);
-                a.heavy_list[h] = r;
-            }
-        }
-    }
-}
-
 __global__ void __launch_bounds__(kCT) k_row_table(const __grid_constant__ TableArgs a) {
     __shared__ int64_t s_tmp[kCW + 1];
     __shared__ int64_t s_tile, s_ex;
@@ -626,6 +608,7 @@ struct HeavyArgs {
     uint64_t *sk1;
     double *sv1;
     uint32_t *ctr;
+    int32_t detect;        // 1: no heavy list, find the heavy rows here
     WsHeader *hdr;
 };
 
@@ -645,150 +628,184 @@ struct HeavySmem {
     int32_t tmp32[kCW + 2];
 };
 
+// One heavy row r, by the whole CTA.
+__device__ __forceinline__ void heavy_row(const HeavyArgs &a, HeavySmem &S, int64_t r) {
+    const int tid = threadIdx.x;
+    const int64_t h0 = a.row_start[r], eend = a.row_start[r + 1];
+    const int64_t pbase = a.row_work[r] - h0;
+    const int64_t nprod = (a.row_work[r + 1] - eend) - pbase;
+    const int64_t nent = eend - h0;
+    if (nent <= kEntCap && nprod <= kProdCap) {
+        // ---- shared-memory path ----
+        int64_t len_i[kEntCap / kCT];
+        int64_t lsum = 0;
+#pragma unroll
+        for (int q = 0; q < kEntCap / kCT; ++q) {
+            const int j = tid * (kEntCap / kCT) + q;
+            len_i[q] = 0;
+            if (j < nent) {
+                const int64_t e = h0 + j;
+                const uint64_t liv = (uint64_t)a.l_liv[e];
+                const uint64_t row = divu(a.div_k, liv);
+                const int64_t c = (int64_t)(liv - row * (uint64_t)a.k);
+                int64_t b0, len;
+                mdt_lookup_entry(a.mdt, e, c, b0, len);
+                S.b0[j] = b0;
+                S.aval[j] = a.l_val[e];
+                len_i[q] = len;
+            }
+            lsum += len_i[q];
+        }
+        int32_t ltot;
+        int32_t lex = block_excl<int32_t>((int32_t)lsum, S.tmp32, &ltot);
+#pragma unroll
+        for (int q = 0; q < kEntCap / kCT; ++q) {
+            const int j = tid * (kEntCap / kCT) + q;
+            if (j < nent) S.poff[j] = lex;
+            lex += (int32_t)len_i[q];
+        }
+        if (tid == 0) S.poff[nent] = ltot;
+        __syncthreads();
+        const int np = ltot;
+        for (int p = tid; p < np; p += kCT) {
+            int lo = 0, hi = (int)nent;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (S.poff[mid] <= p) lo = mid; else hi = mid;
+            }
+            const int64_t b = S.b0[lo] + (p - S.poff[lo]);
+            const uint64_t rl = (uint64_t)a.r_liv[b];
+            const uint64_t col = rl - divu(a.div_n, rl) * (uint64_t)a.nR;
+            const double v = S.aval[lo] * a.r_val[b];
+            S.pk0[p] = col;
+            S.pv0[p] = v;
+        }
+        __syncthreads();
+        // stable sort by column, then sum each run in generation order
+        const int rs = cta_sort(S.pk0, S.pv0, S.pk1, S.pv1, np, a.colbits, S.whist, S.run, S.tmp64);
+        const uint64_t *k = rs ? S.pk1 : S.pk0;
+        const double *v = rs ? S.pv1 : S.pv0;
+        int32_t hc = 0;
+        for (int q = 0; q < kProdCap / kCT; ++q) {
+            const int i = tid * (kProdCap / kCT) + q;
+            if (i < np && (i == 0 || k[i] != k[i - 1])) ++hc;
+        }
+        int32_t htot;
+        int32_t o = block_excl<int32_t>(hc, S.tmp32, &htot);
+        for (int q = 0; q < kProdCap / kCT; ++q) {
+            const int i = tid * (kProdCap / kCT) + q;
+            if (i < np && (i == 0 || k[i] != k[i - 1])) {
+                double s = v[i];
+                for (int t = i + 1; t < np && k[t] == k[i]; ++t) s += v[t];
+                S.ok[o] = k[i];
+                S.ov[o] = s;
+                ++o;
+            }
+        }
+        const int64_t nout = htot;
+        __syncthreads();
+        for (int64_t i = tid; i < nout; i += kCT) {
+            a.sk0[pbase + i] = S.ok[i];
+            a.sv0[pbase + i] = S.ov[i];
+        }
+        if (tid == 0) a.row_hout[r] = nout;
+        __syncthreads();
+    } else {
+        // ---- global path: expand, sort and reduce in scratch ----
+        uint64_t *gk0 = a.sk0 + pbase;
+        double *gv0 = a.sv0 + pbase;
+        uint64_t *gk1 = a.sk1 + pbase;
+        double *gv1 = a.sv1 + pbase;
+        int64_t prod_before = 0;
+        for (int64_t t0 = h0; t0 < eend; t0 += kCT) {
+            const int64_t e = t0 + tid;
+            int64_t b0 = 0, len = 0;
+            double av = 0.0;
+            int64_t c = 0;
+            if (e < eend) {
+                const uint64_t liv = (uint64_t)a.l_liv[e];
+                const uint64_t row = divu(a.div_k, liv);
+                c = (int64_t)(liv - row * (uint64_t)a.k);
+                mdt_lookup_entry(a.mdt, e, c, b0, len);
+                av = a.l_val[e];
+            }
+            int64_t ltot;
+            const int64_t lex = block_excl<int64_t>(len, S.tmp64, &ltot);
+            for (int64_t t = 0; t < len; ++t) {
+                const int64_t rl = a.r_liv[b0 + t];
+                gk0[prod_before + lex + t] = (uint64_t)(rl - c * a.nR);
+                gv0[prod_before + lex + t] = av * a.r_val[b0 + t];
+            }
+            prod_before += ltot;
+        }
+        __syncthreads();
+        const int rs = cta_sort(gk0, gv0, gk1, gv1, nprod, a.colbits, S.whist, S.run, S.tmp64);
+        const uint64_t *k = rs ? gk1 : gk0;
+        const double *v = rs ? gv1 : gv0;
+        uint64_t *ok = rs ? gk0 : gk1;
+        double *ov = rs ? gv0 : gv1;
+        int64_t outc = 0;
+        for (int64_t t0 = 0; t0 < nprod; t0 += kCT) {
+            const int64_t i = t0 + tid;
+            const int hd = (i < nprod) && (i == 0 || k[i] != k[i - 1]);
+            int32_t tot;
+            const int32_t o = block_excl<int32_t>(hd, S.tmp32, &tot);
+            if (hd) {
+                double s = v[i];
+                for (int64_t t = i + 1; t < nprod && k[t] == k[i]; ++t) s += v[t];
+                ok[outc + o] = k[i];
+                ov[outc + o] = s;
+            }
+            outc += tot;
+        }
+        __syncthreads();
+        if (tid == 0) a.row_hout[r] = outc | (rs ? 0ll : (1ll << 62));
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(kCT, 1) k_heavy(const __grid_constant__ HeavyArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HeavySmem &S = *reinterpret_cast<HeavySmem *>(smem_raw);
     __shared__ int64_t s_h;
+    __shared__ int64_t s_list[kCT];
+    __shared__ int s_n;
     const int tid = threadIdx.x;
     if (a.hdr->f > a.cap) return;
+    if (a.detect) {
+        // no heavy list: CTAs take chunks of kCT rows, find the heavy ones
+        // (work > kHeavyWork, more than one entry) and reduce them
+        const int64_t nrows = a.hdr->nrows_l;
+        for (;;) {
+            if (tid == 0) {
+                s_h = atomicAdd(a.ctr, 1u);
+                s_n = 0;
+            }
+            __syncthreads();
+            const int64_t r0 = s_h * kCT;
+            if (r0 >= nrows) break;
+            const int64_t r = r0 + tid;
+            if (r < nrows) {
+                const int64_t work = a.row_work[r + 1] - a.row_work[r];
+                if (work > kHeavyWork) {
+                    const int64_t nent = a.row_start[r + 1] - a.row_start[r];
+                    if (work > nent && nent > 1) s_list[atomicAdd(&s_n, 1)] = r;
+                }
+            }
+            __syncthreads();
+            const int n = s_n;
+            for (int i = 0; i < n; ++i) heavy_row(a, S, s_list[i]);
+            __syncthreads();
+        }
+        return;
+    }
     const int64_t nheavy = (int64_t)*a.nheavy;
     for (;;) {
         if (tid == 0) s_h = atomicAdd(a.ctr, 1u);
         __syncthreads();
         const int64_t h = s_h;
         if (h >= nheavy) break;
-        const int64_t r = a.heavy_list[h];
-        const int64_t h0 = a.row_start[r], eend = a.row_start[r + 1];
-        const int64_t pbase = a.row_work[r] - h0;
-        const int64_t nprod = (a.row_work[r + 1] - eend) - pbase;
-        const int64_t nent = eend - h0;
-        if (nent <= kEntCap && nprod <= kProdCap) {
-            // ---- shared-memory path ----
-            int64_t len_i[kEntCap / kCT];
-            int64_t lsum = 0;
-#pragma unroll
-            for (int q = 0; q < kEntCap / kCT; ++q) {
-                const int j = tid * (kEntCap / kCT) + q;
-                len_i[q] = 0;
-                if (j < nent) {
-                    const int64_t e = h0 + j;
-                    const uint64_t liv = (uint64_t)a.l_liv[e];
-                    const uint64_t row = divu(a.div_k, liv);
-                    const int64_t c = (int64_t)(liv - row * (uint64_t)a.k);
-                    int64_t b0, len;
-                    mdt_lookup_entry(a.mdt, e, c, b0, len);
-                    S.b0[j] = b0;
-                    S.aval[j] = a.l_val[e];
-                    len_i[q] = len;
-                }
-                lsum += len_i[q];
-            }
-            int32_t ltot;
-            int32_t lex = block_excl<int32_t>((int32_t)lsum, S.tmp32, &ltot);
-#pragma unroll
-            for (int q = 0; q < kEntCap / kCT; ++q) {
-                const int j = tid * (kEntCap / kCT) + q;
-                if (j < nent) S.poff[j] = lex;
-                lex += (int32_t)len_i[q];
-            }
-            if (tid == 0) S.poff[nent] = ltot;
-            __syncthreads();
-            const int np = ltot;
-            for (int p = tid; p < np; p += kCT) {
-                int lo = 0, hi = (int)nent;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (S.poff[mid] <= p) lo = mid; else hi = mid;
-                }
-                const int64_t b = S.b0[lo] + (p - S.poff[lo]);
-                const uint64_t rl = (uint64_t)a.r_liv[b];
-                const uint64_t col = rl - divu(a.div_n, rl) * (uint64_t)a.nR;
-                const double v = S.aval[lo] * a.r_val[b];
-                S.pk0[p] = col;
-                S.pv0[p] = v;
-            }
-            __syncthreads();
-            // stable sort by column, then sum each run in generation order
-            const int rs = cta_sort(S.pk0, S.pv0, S.pk1, S.pv1, np, a.colbits, S.whist, S.run, S.tmp64);
-            const uint64_t *k = rs ? S.pk1 : S.pk0;
-            const double *v = rs ? S.pv1 : S.pv0;
-            int32_t hc = 0;
-            for (int q = 0; q < kProdCap / kCT; ++q) {
-                const int i = tid * (kProdCap / kCT) + q;
-                if (i < np && (i == 0 || k[i] != k[i - 1])) ++hc;
-            }
-            int32_t htot;
-            int32_t o = block_excl<int32_t>(hc, S.tmp32, &htot);
-            for (int q = 0; q < kProdCap / kCT; ++q) {
-                const int i = tid * (kProdCap / kCT) + q;
-                if (i < np && (i == 0 || k[i] != k[i - 1])) {
-                    double s = v[i];
-                    for (int t = i + 1; t < np && k[t] == k[i]; ++t) s += v[t];
-                    S.ok[o] = k[i];
-                    S.ov[o] = s;
-                    ++o;
-                }
-            }
-            const int64_t nout = htot;
-            __syncthreads();
-            for (int64_t i = tid; i < nout; i += kCT) {
-                a.sk0[pbase + i] = S.ok[i];
-                a.sv0[pbase + i] = S.ov[i];
-            }
-            if (tid == 0) a.row_hout[r] = nout;
-            __syncthreads();
-        } else {
-            // ---- global path: expand, sort and reduce in scratch ----
-            uint64_t *gk0 = a.sk0 + pbase;
-            double *gv0 = a.sv0 + pbase;
-            uint64_t *gk1 = a.sk1 + pbase;
-            double *gv1 = a.sv1 + pbase;
-            int64_t prod_before = 0;
-            for (int64_t t0 = h0; t0 < eend; t0 += kCT) {
-                const int64_t e = t0 + tid;
-                int64_t b0 = 0, len = 0;
-                double av = 0.0;
-                int64_t c = 0;
-                if (e < eend) {
-                    const uint64_t liv = (uint64_t)a.l_liv[e];
-                    const uint64_t row = divu(a.div_k, liv);
-                    c = (int64_t)(liv - row * (uint64_t)a.k);
-                    mdt_lookup_entry(a.mdt, e, c, b0, len);
-                    av = a.l_val[e];
-                }
-                int64_t ltot;
-                const int64_t lex = block_excl<int64_t>(len, S.tmp64, &ltot);
-                for (int64_t t = 0; t < len; ++t) {
-                    const int64_t rl = a.r_liv[b0 + t];
-                    gk0[prod_before + lex + t] = (uint64_t)(rl - c * a.nR);
-                    gv0[prod_before + lex + t] = av * a.r_val[b0 + t];
-                }
-                prod_before += ltot;
-            }
-            __syncthreads();
-            const int rs = cta_sort(gk0, gv0, gk1, gv1, nprod, a.colbits, S.whist, S.run, S.tmp64);
-            const uint64_t *k = rs ? gk1 : gk0;
-            const double *v = rs ? gv1 : gv0;
-            uint64_t *ok = rs ? gk0 : gk1;
-            double *ov = rs ? gv0 : gv1;
-            int64_t outc = 0;
-            for (int64_t t0 = 0; t0 < nprod; t0 += kCT) {
-                const int64_t i = t0 + tid;
-                const int hd = (i < nprod) && (i == 0 || k[i] != k[i - 1]);
-                int32_t tot;
-                const int32_t o = block_excl<int32_t>(hd, S.tmp32, &tot);
-                if (hd) {
-                    double s = v[i];
-                    for (int64_t t = i + 1; t < nprod && k[t] == k[i]; ++t) s += v[t];
-                    ok[outc + o] = k[i];
-                    ov[outc + o] = s;
-                }
-                outc += tot;
-            }
-            __syncthreads();
-            if (tid == 0) a.row_hout[r] = outc | (rs ? 0ll : (1ll << 62));
-            __syncthreads();
-        }
+        heavy_row(a, S, a.heavy_list[h]);
     }
 }
 
@@ -1712,6 +1729,13 @@ int32_t lco_contract_plan_ex(const lco_shape *a, const lco_shape *b, int32_t nco
     size_t off = kWsHeaderBytes;
     auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes ? bytes : 1); return o; };
     const int64_t nl = p->nnz_l > 0 ? p->nnz_l : 1, nr = p->nnz_r > 0 ? p->nnz_r : 1;
+    // the phase-1 look-back words follow the header, so one memset resets both
+    {
+        const size_t scan_tiles = (size_t)((nl + kScanTile - 1) / kScanTile) + 1;
+        const size_t dcsr_tiles = (size_t)((nr + kScanTile - 1) / kScanTile) + 1;
+        p->off_p1state = take((2 * scan_tiles + dcsr_tiles) * 8);
+        p->p1state_bytes = align_up((2 * scan_tiles + dcsr_tiles) * 8);
+    }
     p->off_l_liv = p->need_l ? take((size_t)nl * 8) : 0;
     p->off_l_val = p->need_l ? take((size_t)nl * 8) : 0;
     p->off_r_liv = p->need_r ? take((size_t)nr * 8) : 0;
@@ -1722,10 +1746,6 @@ int32_t lco_contract_plan_ex(const lco_shape *a, const lco_shape *b, int32_t nco
         if (p->need_r) { size_t x = rp_region_bytes(p->rp_r, p->nnz_r); if (x > rb) rb = x; }
         p->off_rp = take(rb);
     }
-    const size_t scan_tiles = (size_t)((nl + kScanTile - 1) / kScanTile) + 1;
-    const size_t dcsr_tiles = (size_t)((nr + kScanTile - 1) / kScanTile) + 1;
-    p->off_p1state = take((2 * scan_tiles + dcsr_tiles) * 8);
-    p->p1state_bytes = align_up((2 * scan_tiles + dcsr_tiles) * 8);
     if (p->lookup == kLookupCsr) {
         p->off_mdt_rowptr = take((size_t)(k + 1) * 8);
     } else {
@@ -1818,9 +1838,9 @@ bool check_ptrs(const lco_plan *p, const int64_t *a_liv, const double *a_val, co
 int32_t symbolic_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a_val, const int64_t *b_liv,
                          const double *b_val, char *ws, cudaStream_t s) {
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
-    // reset header (status, results, counters) and the phase-1 look-back state
-    if (cudaMemsetAsync(ws, 0, kWsHeaderBytes, s) != cudaSuccess) return LCO_ERR_CUDA;
-    if (cudaMemsetAsync(ws + p->off_p1state, 0, p->p1state_bytes, s) != cudaSuccess) return LCO_ERR_CUDA;
+    // reset header (status, results, counters) and the phase-1 look-back
+    // state, which follows it
+    if (cudaMemsetAsync(ws, 0, p->off_p1state + p->p1state_bytes, s) != cudaSuccess) return LCO_ERR_CUDA;
     if (p->nnz_l == 0 || p->nnz_r == 0) {
         LCO_LAUNCH("k_set_empty", s, k_set_empty<<<1, 1, 0, s>>>(hdr, p->info.alg));
         return cudaGetLastError() == cudaSuccess ? LCO_OK : LCO_ERR_CUDA;
@@ -1945,10 +1965,6 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
             int64_t grid = (p->nnz_l + kTabTile - 1) / kTabTile;
             if (grid > (int64_t)sms * 2) grid = (int64_t)sms * 2;
             LCO_LAUNCH("k_row_table", s, k_row_table<<<(unsigned)(grid > 0 ? grid : 1), kCT, 0, s>>>(ta));
-        } else {
-            int64_t grid = (p->nnz_l + 1 + 255) / 256;
-            if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
-            LCO_LAUNCH("k_row_heavy", s, k_row_heavy<<<(unsigned)grid, 256, 0, s>>>(ta));
         }
         HeavyArgs ha{};
         ha.l_liv = o.l_liv;
@@ -1972,6 +1988,7 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         ha.sk1 = sk1;
         ha.sv1 = sv1;
         ha.ctr = chunk_ctr + 2;
+        ha.detect = compact ? 0 : 1;   // CSR plans: k_heavy finds its rows itself
         ha.hdr = hdr;
         // function attributes are per device: set them once on each
         static std::atomic<uint64_t> attr_done{0};

@@ -158,7 +158,7 @@ struct Request {
     std::shared_ptr<Operand> a, b;
     lco_plan *plan = nullptr;
     lco_plan_info info{};
-    int state = kQueued;
+    std::atomic<int> state{kQueued};
     int slot = -1;
     void *ws = nullptr;        // workspace (phase 1, and phase 2 when f fits)
     int64_t ws_cap = 0;        // output capacity the workspace is sized for
@@ -202,7 +202,8 @@ struct lco_server {
     uint64_t submitted = 0, completed = 0, failed = 0;
     int64_t in_flight = 0;
     bool stop = false;
-    std::thread worker;
+    std::vector<std::thread> workers;
+    int nworkers = 1;
     Clock::time_point epoch;
 
     double now_us() const {
@@ -213,12 +214,18 @@ struct lco_server {
         p = nullptr;
     }
     void finish(Request *r, int32_t status);
+    void finish_locked(Request *r, int32_t status);
     bool admit(Request *r, Slot &sl, int si);
     void advance(Slot &sl);
-    void run();
+    void run(int w);
 };
 
 void lco_server::finish(Request *r, int32_t status) {
+    std::lock_guard<std::mutex> g(mu);
+    finish_locked(r, status);
+}
+
+void lco_server::finish_locked(Request *r, int32_t status) {
     // caller holds mu; the request's device work has completed (or never ran)
     if (status != LCO_OK) r->status = status;
     pfree(r->ws);
@@ -268,7 +275,10 @@ bool lco_server::admit(Request *r, Slot &sl, int si) {
     }
     r->slot = si;
     sl.req = r;
-    in_flight++;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        in_flight++;
+    }
     r->state = kPhase1;
     cudaStream_t s = sl.stream;
     int32_t rc = LCO_OK;
@@ -357,15 +367,20 @@ void lco_server::advance(Slot &sl) {
     finish(r, LCO_OK);
 }
 
-void lco_server::run() {
+// Worker w owns the slots i with i % nworkers == w.  The server mutex is
+// held only to take requests from the queue and to publish results; CUDA
+// calls run without it, so the workers' host work overlaps.
+void lco_server::run(int w) {
     cudaSetDevice(device);
-    std::unique_lock<std::mutex> lk(mu);
+    std::vector<int> mine;
+    for (int i = w; i < (int)slots.size(); i += nworkers) mine.push_back(i);
     while (true) {
         bool progressed = false;
-        // 1. requests in flight
-        for (auto &sl : slots) {
-            if (!sl.req) continue;
+        // 1. this worker's requests in flight
+        for (int si : mine) {
+            Slot &sl = slots[si];
             Request *r = sl.req;
+            if (!r) continue;
             if (r->waiting_mem) {
                 // phase 1 is done; waiting for pool memory for phase 2
                 if (std::chrono::duration<double, std::micro>(Clock::now() - r->t_wait_mem).count() >
@@ -375,7 +390,7 @@ void lco_server::run() {
                     continue;
                 }
                 advance(sl);
-                progressed = progressed || !r->waiting_mem || r->state == kDone;
+                progressed = progressed || !r->waiting_mem;
                 continue;
             }
             const cudaError_t q = cudaEventQuery(sl.ev);
@@ -387,47 +402,53 @@ void lco_server::run() {
             }
             advance(sl);
         }
-        // 2. admissions, in arrival order
-        while (!queue.empty()) {
-            int si = -1;
-            for (int i = 0; i < (int)slots.size(); ++i)
-                if (!slots[i].req) {
-                    si = i;
-                    break;
-                }
-            if (si < 0) break;
-            Request *r = queue.front();
-            if (stop) {
+        // 2. admissions into free slots, in arrival order
+        for (int si : mine) {
+            Slot &sl = slots[si];
+            if (sl.req) continue;
+            Request *r = nullptr;
+            {
+                std::lock_guard<std::mutex> g(mu);
+                if (queue.empty()) break;
+                r = queue.front();
                 queue.pop_front();
-                finish(r, LCO_ERR_ADMISSION);
-                continue;
-            }
-            if (!admit(r, slots[si], si)) {
-                if (!r->waiting_mem) {
-                    r->waiting_mem = true;
-                    r->t_wait_mem = Clock::now();
-                } else if (std::chrono::duration<double, std::micro>(Clock::now() - r->t_wait_mem).count() >
-                           kAdmissionWaitUs) {
-                    queue.pop_front();
-                    r->waiting_mem = false;
-                    finish(r, LCO_ERR_ADMISSION);
+                if (stop) {
+                    finish_locked(r, LCO_ERR_ADMISSION);
                     progressed = true;
                     continue;
                 }
-                break;
             }
-            r->waiting_mem = false;
-            queue.pop_front();
-            progressed = true;
+            if (admit(r, sl, si)) {
+                r->waiting_mem = false;
+                progressed = true;
+                continue;
+            }
+            // no memory yet: back to the head of the queue (or fail once the
+            // wait has lasted too long)
+            std::lock_guard<std::mutex> g(mu);
+            if (!r->waiting_mem) {
+                r->waiting_mem = true;
+                r->t_wait_mem = Clock::now();
+            } else if (std::chrono::duration<double, std::micro>(Clock::now() - r->t_wait_mem).count() >
+                       kAdmissionWaitUs) {
+                r->waiting_mem = false;
+                finish_locked(r, LCO_ERR_ADMISSION);
+                progressed = true;
+                continue;
+            }
+            queue.push_front(r);
+            break;
         }
-        if (stop && queue.empty() && in_flight == 0) break;
+        bool busy = false;
+        for (int si : mine) busy = busy || slots[si].req != nullptr;
         if (!progressed) {
-            if (in_flight == 0 && queue.empty()) {
+            std::unique_lock<std::mutex> lk(mu);
+            if (stop && queue.empty() && !busy) break;
+            if (!busy && queue.empty()) {
                 cv_work.wait(lk);                        // idle: sleep until a submit or stop
             } else {
                 lk.unlock();                             // work on the device: poll again shortly
                 std::this_thread::sleep_for(std::chrono::microseconds(5));
-                lk.lock();
             }
         }
     }
@@ -500,8 +521,10 @@ int32_t lco_serve_create(const lco_serve_config *cfg, lco_server **out) {
         sl.hdr = reinterpret_cast<lco::WsHeader *>(h);
     }
     s->epoch = Clock::now();
+    s->nworkers = cfg->nworkers > 0 ? cfg->nworkers : 4;
+    if (s->nworkers > cfg->nslots) s->nworkers = cfg->nslots;
     lco_server *raw = s.release();
-    raw->worker = std::thread([raw] { raw->run(); });
+    for (int w = 0; w < raw->nworkers; ++w) raw->workers.emplace_back([raw, w] { raw->run(w); });
     *out = raw;
     return LCO_OK;
 }
@@ -513,7 +536,8 @@ int32_t lco_serve_destroy(lco_server *srv) {
         srv->stop = true;
         srv->cv_work.notify_all();
     }
-    if (srv->worker.joinable()) srv->worker.join();
+    for (auto &t : srv->workers)
+        if (t.joinable()) t.join();
     cudaSetDevice(srv->device);
     for (auto &sl : srv->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
