@@ -39,7 +39,9 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC, "-lm"]
+    # -ffp-contract=off: every product and sum is rounded as written (no
+    # fused multiply-add on targets that have one), the same on x86 and Arm
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)
     return _SO
@@ -211,3 +213,27 @@ def dispatch(m, k, n, nnz_a, nnz_b, perm_row=0, perm_col=0):
                                        ctypes.c_int64(nnz_a), ctypes.c_int64(nnz_b),
                                        ctypes.c_int32(perm_row), ctypes.c_int32(perm_col))
     return ALG_NAMES[code]
+
+
+def sort(liv, val):
+    """Entries in ascending LIV order (stable for equal LIVs): Sec. 3.2."""
+    lib = _load()
+    l, v = _i64(liv), _f64(val)
+    n = l.shape[0]
+    lo, vo = np.empty(n, np.int64), np.empty(n, np.float64)
+    _check(lib.lco_oracle_sort(ctypes.c_int64(n), _p(l), _p(v), _p(lo), _p(vo)), "sort")
+    return lo, vo
+
+
+def add(alpha, A, beta, B):
+    """alpha*A + beta*B for sorted LCO dicts in the same dims and order
+    (union of entries, structural zeros kept): Sec. 3.2, Eq. 4's sum."""
+    lib = _load()
+    la, va, lb, vb = _i64(A["liv"]), _f64(A["val"]), _i64(B["liv"]), _f64(B["val"])
+    n = la.shape[0] + lb.shape[0]
+    lc, vc = np.empty(max(n, 1), np.int64), np.empty(max(n, 1), np.float64)
+    nc = ctypes.c_int64()
+    _check(lib.lco_oracle_add(ctypes.c_double(alpha), ctypes.c_int64(la.shape[0]), _p(la), _p(va),
+                              ctypes.c_double(beta), ctypes.c_int64(lb.shape[0]), _p(lb), _p(vb),
+                              _p(lc), _p(vc), ctypes.byref(nc)), "add")
+    return lc[:nc.value].copy(), vc[:nc.value].copy()

@@ -38,6 +38,13 @@
  *                                        test dim/nnz > 3 (Secs. 5.2.3-5.2.5)
  *                                        with the n > m orientation rule of
  *                                        Sec. 5.2.2.
+ *   lco_oracle_sort                      Sec. 3.2: sorting non-zeros into
+ *                                        lexicographic (LIV) order
+ *                                        (definition: stable sort by LIV).
+ *   lco_oracle_add                       Sec. 3.2 / Fig. 3c: the sum of two
+ *                                        tensors in one order, as in Eq. 4
+ *                                        (definition: union of entries,
+ *                                        values added).
  *
  * Parity pins for every function live under tests/ (test_oracle_*.py).
  */
@@ -533,6 +540,67 @@ int lco_oracle_flops(int32_t order_a, const int64_t *dims_a, const int32_t *sig_
 }
 
 void lco_oracle_free(void *p) { free(p); }
+
+/* ------------------------------------------------------------------ */
+/* Sorting and addition (Sec. 3.2; Fig. 3c and the sum of Eq. 4).      */
+/* ------------------------------------------------------------------ */
+
+/* Sorting by definition: the entries in ascending LIV order; equal LIVs
+ * keep their input order (a stable sort on (LIV, input position)).  The
+ * order is unchanged; only the entries move. */
+int lco_oracle_sort(int64_t nnz, const int64_t *liv, const double *val, int64_t *liv_out, double *val_out)
+{
+    if (nnz < 0) return ORC_ERR_INVALID;
+    if (nnz == 0) return ORC_OK;
+    int64_t (*ki)[2] = malloc((size_t)nnz * sizeof *ki);
+    if (!ki) return ORC_ERR_OOM;
+    for (int64_t e = 0; e < nnz; ++e) {
+        ki[e][0] = liv[e];
+        ki[e][1] = e;
+    }
+    qsort(ki, (size_t)nnz, sizeof *ki, cmp_keyidx);
+    for (int64_t e = 0; e < nnz; ++e) {
+        liv_out[e] = ki[e][0];
+        val_out[e] = val[ki[e][1]];
+    }
+    free(ki);
+    return ORC_OK;
+}
+
+/* C = alpha A + beta B by definition, for two sorted LCO tensors in the
+ * same order: every LIV of A or B is an entry of C (structural entries are
+ * kept even when the sum is zero); an LIV present in both gets
+ * alpha a + beta b, one present in one only gets its scaled value.  Output
+ * ascending; returns the entry count in *nnz_c (c arrays must hold
+ * nnz_a + nnz_b). */
+int lco_oracle_add(double alpha, int64_t nnz_a, const int64_t *a_liv, const double *a_val,
+                   double beta, int64_t nnz_b, const int64_t *b_liv, const double *b_val,
+                   int64_t *c_liv, double *c_val, int64_t *nnz_c)
+{
+    if (nnz_a < 0 || nnz_b < 0 || !nnz_c) return ORC_ERR_INVALID;
+    int64_t i = 0, j = 0, o = 0;
+    while (i < nnz_a || j < nnz_b) {
+        if (j >= nnz_b || (i < nnz_a && a_liv[i] < b_liv[j])) {
+            c_liv[o] = a_liv[i];
+            c_val[o] = alpha * a_val[i];
+            ++i;
+        } else if (i >= nnz_a || b_liv[j] < a_liv[i]) {
+            c_liv[o] = b_liv[j];
+            c_val[o] = beta * b_val[j];
+            ++j;
+        } else {
+            const double pa = alpha * a_val[i];
+            const double pb = beta * b_val[j];
+            c_liv[o] = a_liv[i];
+            c_val[o] = pa + pb;
+            ++i;
+            ++j;
+        }
+        ++o;
+    }
+    *nnz_c = o;
+    return ORC_OK;
+}
 
 /* ------------------------------------------------------------------ */
 /* Sec. 5.2, Table 4: the poly-algorithm's choice.                     */

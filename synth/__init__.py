@@ -388,3 +388,33 @@ def batch_problems(count=4096, seed=100, admit=None, max_attempts=64, **kw):
         else:
             raise RuntimeError(f"batch item {i}: no admissible draw in {max_attempts} attempts")
     return out
+
+
+# ---------------------------------------------------------------------------
+# The combinatorial Laplacian of Eq. 4 (Sec. 2, Sec. 6)
+# ---------------------------------------------------------------------------
+
+def fd_matrix(N):
+    """The N x N FD matrix of Eq. 1 as a second-order LCO tensor d[i, i']."""
+    r, c, v = fd_matrix_entries(N, "eq1")
+    return _pack([N, N], np.stack([r, c], 1), v)
+
+
+def kronecker_delta(N):
+    """delta[j, l] = 1 for j == l (N entries)."""
+    i = np.arange(N, dtype=np.int64)
+    return _pack([N, N], np.stack([i, i], 1), np.ones(N))
+
+
+def quadratic_field(N):
+    """x[k, l] = k^2 + l^2 on an N x N grid (every point an entry)."""
+    k, l = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    co = np.stack([k.ravel(), l.ravel()], 1)
+    return _pack([N, N], co, (k.ravel() ** 2 + l.ravel() ** 2).astype(np.float64))
+
+
+def relabel(T, sig):
+    """The same entries read with another significance order: the tensor
+    whose mode m is T's mode m, with `sig` as its lexicographic order (no
+    data moves; used to name a product's modes like another's)."""
+    return {"dims": list(T["dims"]), "sig": list(sig), "liv": T["liv"], "val": T["val"]}
