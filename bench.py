@@ -71,7 +71,7 @@ def parse_args():
     ap.add_argument("--nnz", type=int, default=16 << 20, help="non-zeros for --case permute")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="C2",
                     help="--case step: C1 fd2d 16^2 L^2, C2 fd3d 64^3 L.Dx + permute (the metric's), "
-                         "C3 R-MAT 1e7 DCSR, C3b R-MAT 2^18 CSRNA")
+                         "C3 R-MAT 1e7 DCSR, C3b R-MAT 2^18 CSRNA, E17 the Sec. 6 product at N = 2047")
     ap.add_argument("--count", type=int, default=4096, help="problems for --case batch")
     ap.add_argument("--max-digit-bits", type=int, default=0,
                     help="cap on the radix digit width of the operand permutations (0: library default)")
@@ -221,6 +221,7 @@ CONFIGS = {
     "C2": ("config_fd3d", WORKLOAD),
     "C3": ("config_rmat_dcsr", "rmat_2^20x2^20x2^12_1e7_each_a_ijk_b_ljk"),
     "C3b": ("config_rmat_na", "rmat_2^14x2^14x2^12_2^18_each_mode2_x_mode0"),
+    "E17": ("config_eq17", "eq17_b_ii'jl_d_i'k_N2047 (Sec. 6; paper: 2.0 s on an E8400)"),
 }
 
 

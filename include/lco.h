@@ -340,6 +340,40 @@ int32_t lco_batch_results(const lco_batch *batch, const int64_t *caps, const voi
                           lco_contract_result *out, void *stream);
 
 /* ------------------------------------------------------------------ */
+/* Sorting and addition (Sec. 3.2; the sum of Eq. 4, Fig. 3c)           */
+/* ------------------------------------------------------------------ */
+
+/* Sorts nnz entries of a tensor of shape t (order, dims, sig) into
+ * ascending LIV order: Sec. 3.2's sorting task (e.g. after construction or
+ * unordered insertion), the general case of which a permutation is the
+ * pre-sorted special case.  Every radix digit of the LIV is sorted (passes
+ * whose digit is constant over the data are skipped); equal LIVs keep their
+ * input order.  in_* and out_* are device arrays of t->nnz entries (not
+ * aliased); ws is a device workspace of lco_sort_workspace bytes (256-byte
+ * aligned, any content: the call resets what it uses).
+ * Errors: LCO_ERR_INVALID, LCO_ERR_OVERFLOW, LCO_ERR_OOM (ws too small),
+ * LCO_ERR_CUDA; device status (lco_workspace_status) LCO_ERR_TIMEOUT. */
+int32_t lco_sort_workspace(const lco_shape *t, size_t *ws_bytes);
+int32_t lco_sort(const lco_shape *t, const int64_t *in_liv, const double *in_val, int64_t *out_liv,
+                 double *out_val, void *ws, size_t ws_bytes, void *stream);
+
+/* C = alpha A + beta B for two sorted LCO tensors of the same shape and
+ * order t (t->nnz is ignored): the addition of Eq. 4's two terms once one
+ * is re-sorted into the other's order (Sec. 3.2, Fig. 3c).  Every LIV of A
+ * or B is an entry of C -- a cancelled sum is kept as an explicit zero --
+ * with alpha*a + beta*b where both have it (each product rounded, then
+ * added) and the scaled value otherwise.  c_liv/c_val need room for
+ * nnz_a + nnz_b entries; the entry count is read with lco_add_result.  ws
+ * holds lco_add_workspace bytes (any content).  No host synchronisation.
+ * Errors: LCO_ERR_INVALID, LCO_ERR_OOM, LCO_ERR_CUDA. */
+int32_t lco_add_workspace(int64_t nnz_a, int64_t nnz_b, size_t *ws_bytes);
+int32_t lco_add(const lco_shape *t, double alpha, const int64_t *a_liv, const double *a_val, int64_t nnz_a,
+                double beta, const int64_t *b_liv, const double *b_val, int64_t nnz_b, int64_t *c_liv,
+                double *c_val, void *ws, size_t ws_bytes, void *stream);
+/* Synchronises `stream`; *nnz_c = entries of C, *status = device status. */
+int32_t lco_add_result(const void *ws, int64_t *nnz_c, int32_t *status, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* Device memory pool (bookkeeping over a caller-given address range;   */
 /* no paper counterpart).  The served path keeps its operands, results  */
 /* and workspaces in one such pool so that admission is a host-side    */

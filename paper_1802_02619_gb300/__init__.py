@@ -150,6 +150,15 @@ _SIGNATURES = {
                            ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int32),
     "lco_batch_results": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ContractResult),
                           ctypes.c_void_p], ctypes.c_int32),
+    "lco_sort_workspace": ([ctypes.POINTER(Shape), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int32),
+    "lco_sort": ([ctypes.POINTER(Shape)] + [ctypes.c_void_p] * 5 + [ctypes.c_size_t, ctypes.c_void_p],
+                 ctypes.c_int32),
+    "lco_add_workspace": ([ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int32),
+    "lco_add": ([ctypes.POINTER(Shape), ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                 ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int32),
+    "lco_add_result": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                        ctypes.c_void_p], ctypes.c_int32),
     "lco_pool_create": ([ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int32),
     "lco_pool_destroy": ([ctypes.c_void_p], ctypes.c_int32),
     "lco_pool_alloc": ([ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int32),
@@ -577,6 +586,54 @@ class Batch:
             out.append(LcoTensor(self.info[i]["c_dims"], self.info[i]["c_sig"], self.c_liv_all[o:o + nc],
                                  self.c_val_all[o:o + nc]))
         return out
+
+
+# ---------------------------------------------------------------------------
+# Sorting and addition
+# ---------------------------------------------------------------------------
+
+def sort(t: LcoTensor, stream=None) -> LcoTensor:
+    """t's entries in ascending LIV order (Sec. 3.2); t.liv need not be
+    sorted.  Equal LIVs keep their input order."""
+    lib = load()
+    _require_cuda(t.liv, t.val)
+    sh = t.shape()
+    nb = ctypes.c_size_t()
+    _check(lib.lco_sort_workspace(ctypes.byref(sh), ctypes.byref(nb)), "lco_sort_workspace")
+    ws = workspace(nb.value, t.liv.device)
+    liv, val = torch.empty_like(t.liv), torch.empty_like(t.val)
+    _check(lib.lco_sort(ctypes.byref(sh), _ptr(t.liv), _ptr(t.val), _ptr(liv), _ptr(val), _ptr(ws),
+                        ctypes.c_size_t(ws.numel()), _stream(stream)), "lco_sort")
+    st = ctypes.c_int32()
+    _check(lib.lco_workspace_status(_ptr(ws), ctypes.byref(st), _stream(stream)), "lco_workspace_status")
+    if st.value != 0:
+        raise LcoError(st.value, "lco_sort (device)")
+    return LcoTensor(list(t.dims), list(t.sig), liv, val)
+
+
+def add(A: LcoTensor, B: LcoTensor, alpha: float = 1.0, beta: float = 1.0, stream=None) -> LcoTensor:
+    """alpha*A + beta*B for two sorted tensors of the same dims and order
+    (Sec. 3.2; Eq. 4's sum).  Cancelled sums stay as explicit zeros."""
+    if list(A.dims) != list(B.dims) or list(A.sig) != list(B.sig):
+        raise ValueError("A and B must have the same dims and order (permute one first)")
+    lib = load()
+    _require_cuda(A.liv, A.val, B.liv, B.val)
+    sh = A.shape()
+    nb = ctypes.c_size_t()
+    _check(lib.lco_add_workspace(A.nnz, B.nnz, ctypes.byref(nb)), "lco_add_workspace")
+    dev = A.liv.device
+    ws = workspace(nb.value, dev)
+    n = A.nnz + B.nnz
+    c_liv = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
+    c_val = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+    _check(lib.lco_add(ctypes.byref(sh), ctypes.c_double(alpha), _ptr(A.liv), _ptr(A.val), A.nnz,
+                       ctypes.c_double(beta), _ptr(B.liv), _ptr(B.val), B.nnz, _ptr(c_liv), _ptr(c_val), _ptr(ws),
+                       ctypes.c_size_t(ws.numel()), _stream(stream)), "lco_add")
+    nc, st = ctypes.c_int64(), ctypes.c_int32()
+    _check(lib.lco_add_result(_ptr(ws), ctypes.byref(nc), ctypes.byref(st), _stream(stream)), "lco_add_result")
+    if st.value != 0:
+        raise LcoError(st.value, "lco_add (device)")
+    return LcoTensor(list(A.dims), list(A.sig), c_liv[:nc.value], c_val[:nc.value])
 
 
 # ---------------------------------------------------------------------------

@@ -418,3 +418,15 @@ def relabel(T, sig):
     whose mode m is T's mode m, with `sig` as its lexicographic order (no
     data moves; used to name a product's modes like another's)."""
     return {"dims": list(T["dims"]), "sig": list(sig), "liv": T["liv"], "val": T["val"]}
+
+
+def config_eq17(N=2047):
+    """Eq. 17, b_ii'jl d_i'k with b_ii'jl = d_ii' delta_jl (Sec. 6): b is an
+    N^3 x N row-sparse matrix once flattened, d the N x N FD matrix of
+    Eq. 1; b is built row-major (i, i', j, l), so the product first
+    rearranges it (the rearrangement the paper's timing includes)."""
+    r, c, v = fd_matrix_entries(N, "eq1")
+    j = np.arange(N, dtype=np.int64)
+    co = np.stack([np.repeat(r, N), np.repeat(c, N), np.tile(j, r.shape[0]), np.tile(j, r.shape[0])], 1)
+    b = _pack([N] * 4, co, np.repeat(v, N))
+    return {"name": f"eq17_b_d_N{N}", "A": b, "B": fd_matrix(N), "modes_a": [1], "modes_b": [0]}
