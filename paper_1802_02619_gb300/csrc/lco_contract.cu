@@ -495,6 +495,25 @@ constexpr int kTabTile = kCT * kTabItems;
 // (rows whose entries all miss R produce nothing and are dropped), and the
 // heavy rows.  A heavy row with one entry is a scaled copy of one R row and
 // stays with the light-row kernel, which copies it without sorting.
+// Without compaction (every row kept, as when R is not row-sparse and
+// nearly every entry meets an R row): only the heavy-row list is built, so
+// that k_heavy spreads the heavy rows over all its CTAs.
+__global__ void __launch_bounds__(256) k_row_heavy(const __grid_constant__ TableArgs a) {
+    if (a.hdr->f > a.cap) return;
+    const int64_t nrows = a.hdr->nrows_l;
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gsz) {
+        const int64_t work = a.row_work[r + 1] - a.row_work[r];
+        if (work > kHeavyWork) {
+            const int64_t nent = a.row_start[r + 1] - a.row_start[r];
+            if (work > nent && nent > 1) {
+                const unsigned long long h = atomicAdd(a.nheavy, 1ull);
+                a.heavy_list[h] = r;
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kCT) k_row_table(const __grid_constant__ TableArgs a) {
     __shared__ int64_t s_tmp[kCW + 1];
     __shared__ int64_t s_tile, s_ex;
@@ -608,7 +627,6 @@ struct HeavyArgs {
     uint64_t *sk1;
     double *sv1;
     uint32_t *ctr;
-    int32_t detect;        // 1: no heavy list, find the heavy rows here
     WsHeader *hdr;
 };
 
@@ -768,37 +786,8 @@ __global__ void __launch_bounds__(kCT, 1) k_heavy(const __grid_constant__ HeavyA
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HeavySmem &S = *reinterpret_cast<HeavySmem *>(smem_raw);
     __shared__ int64_t s_h;
-    __shared__ int64_t s_list[kCT];
-    __shared__ int s_n;
     const int tid = threadIdx.x;
     if (a.hdr->f > a.cap) return;
-    if (a.detect) {
-        // no heavy list: CTAs take chunks of kCT rows, find the heavy ones
-        // (work > kHeavyWork, more than one entry) and reduce them
-        const int64_t nrows = a.hdr->nrows_l;
-        for (;;) {
-            if (tid == 0) {
-                s_h = atomicAdd(a.ctr, 1u);
-                s_n = 0;
-            }
-            __syncthreads();
-            const int64_t r0 = s_h * kCT;
-            if (r0 >= nrows) break;
-            const int64_t r = r0 + tid;
-            if (r < nrows) {
-                const int64_t work = a.row_work[r + 1] - a.row_work[r];
-                if (work > kHeavyWork) {
-                    const int64_t nent = a.row_start[r + 1] - a.row_start[r];
-                    if (work > nent && nent > 1) s_list[atomicAdd(&s_n, 1)] = r;
-                }
-            }
-            __syncthreads();
-            const int n = s_n;
-            for (int i = 0; i < n; ++i) heavy_row(a, S, s_list[i]);
-            __syncthreads();
-        }
-        return;
-    }
     const int64_t nheavy = (int64_t)*a.nheavy;
     for (;;) {
         if (tid == 0) s_h = atomicAdd(a.ctr, 1u);
@@ -1965,6 +1954,10 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
             int64_t grid = (p->nnz_l + kTabTile - 1) / kTabTile;
             if (grid > (int64_t)sms * 2) grid = (int64_t)sms * 2;
             LCO_LAUNCH("k_row_table", s, k_row_table<<<(unsigned)(grid > 0 ? grid : 1), kCT, 0, s>>>(ta));
+        } else {
+            int64_t grid = (p->nnz_l + 1 + 255) / 256;
+            if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
+            LCO_LAUNCH("k_row_heavy", s, k_row_heavy<<<(unsigned)grid, 256, 0, s>>>(ta));
         }
         HeavyArgs ha{};
         ha.l_liv = o.l_liv;
@@ -1988,7 +1981,6 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         ha.sk1 = sk1;
         ha.sv1 = sv1;
         ha.ctr = chunk_ctr + 2;
-        ha.detect = compact ? 0 : 1;   // CSR plans: k_heavy finds its rows itself
         ha.hdr = hdr;
         // function attributes are per device: set them once on each
         static std::atomic<uint64_t> attr_done{0};
