@@ -155,22 +155,25 @@ def rp_keyspec(dims, sig_old, sig_new):
     return mt.value, ml.value, nr.value
 
 
-def contract(A, B, modes_a, modes_b):
+def contract(A, B, modes_a, modes_b, entry_a=(), entry_b=()):
     """Contraction by definition.  A and B are dicts with dims, sig, liv, val.
 
-    Returns (liv_c, val_c, abs_c) with C row-major over (A free modes, B free
-    modes); abs_c is the per-entry sum of |a||b| used by the tolerance.
+    Returns (liv_c, val_c, abs_c) with C row-major over (entrywise pairs, A
+    free modes, B free modes); abs_c is the per-entry sum of |a||b| used by
+    the tolerance.  entry_a/entry_b pair up shared modes that are kept, not
+    summed (Sec. 5's entrywise products).
     """
     lib = _load()
     da, sa, la, va = _i64(A["dims"]), _i32(A["sig"]), _i64(A["liv"]), _f64(A["val"])
     db, sb, lb, vb = _i64(B["dims"]), _i32(B["sig"]), _i64(B["liv"]), _f64(B["val"])
     ma, mb = _i32(modes_a), _i32(modes_b)
+    ea, eb = _i32(entry_a), _i32(entry_b)
     nnz_c = ctypes.c_int64()
     pl, pv, pa = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
-    rc = lib.lco_oracle_contract(
+    rc = lib.lco_oracle_contract_ew(
         ctypes.c_int32(len(da)), _p(da), _p(sa), ctypes.c_int64(la.shape[0]), _p(la), _p(va),
         ctypes.c_int32(len(db)), _p(db), _p(sb), ctypes.c_int64(lb.shape[0]), _p(lb), _p(vb),
-        ctypes.c_int32(len(ma)), _p(ma), _p(mb),
+        ctypes.c_int32(len(ma)), _p(ma), _p(mb), ctypes.c_int32(len(ea)), _p(ea), _p(eb),
         ctypes.byref(nnz_c), ctypes.byref(pl), ctypes.byref(pv), ctypes.byref(pa))
     _check(rc, "contract")
     n = nnz_c.value

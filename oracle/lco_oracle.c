@@ -34,6 +34,10 @@
  *                                        inner/outer products of Sec. 5.2):
  *                                        C = sum over matched contracted
  *                                        coordinates of a * b (definition).
+ *   lco_oracle_contract_ew               Sec. 5: the same with entrywise
+ *                                        (shared, unsummed) mode pairs --
+ *                                        one matrix product per value of the
+ *                                        shared indices (definition).
  *   lco_oracle_dispatch                  Sec. 5.2, Table 4 and the ratio
  *                                        test dim/nnz > 3 (Secs. 5.2.3-5.2.5)
  *                                        with the n > m orientation rule of
@@ -371,15 +375,24 @@ static int cmp_i64(const void *pa, const void *pb)
     return a < b ? -1 : (a > b ? 1 : 0);
 }
 
-int lco_oracle_contract(int32_t order_a, const int64_t *dims_a, const int32_t *sig_a,
-                        int64_t nnz_a, const int64_t *liv_a, const double *val_a,
-                        int32_t order_b, const int64_t *dims_b, const int32_t *sig_b,
-                        int64_t nnz_b, const int64_t *liv_b, const double *val_b,
-                        int32_t ncontract, const int32_t *modes_a, const int32_t *modes_b,
-                        int64_t *nnz_c, int64_t **liv_c, double **val_c, double **abs_c)
+/* The contraction with entrywise mode pairs (emodes_a[t], emodes_b[t]):
+ * shared indices that are neither summed nor dropped (Sec. 5: entrywise
+ * products map the tensor product to repeated matrix products, one per
+ * value of the shared indices).  By definition:
+ *   C[h, free_a, free_b] = sum_k A[h, free_a, k] B[h, k, free_b]
+ * with C's modes ordered entrywise pairs (pairing order), then A's free
+ * modes, then B's free modes, row-major.  nentry = 0 is the plain
+ * contraction. */
+int lco_oracle_contract_ew(int32_t order_a, const int64_t *dims_a, const int32_t *sig_a,
+                           int64_t nnz_a, const int64_t *liv_a, const double *val_a,
+                           int32_t order_b, const int64_t *dims_b, const int32_t *sig_b,
+                           int64_t nnz_b, const int64_t *liv_b, const double *val_b,
+                           int32_t ncontract, const int32_t *modes_a, const int32_t *modes_b,
+                           int32_t nentry, const int32_t *emodes_a, const int32_t *emodes_b,
+                           int64_t *nnz_c, int64_t **liv_c, double **val_c, double **abs_c)
 {
     int is_con_a[ORC_MAX_ORDER] = {0}, is_con_b[ORC_MAX_ORDER] = {0};
-    int64_t tot_a, tot_b, m = 1, n = 1;
+    int64_t tot_a, tot_b, m = 1, n = 1, hsz = 1;
     int64_t coord[ORC_MAX_ORDER];
     int rc;
     bent_t *bs = NULL;
@@ -399,7 +412,18 @@ int lco_oracle_contract(int32_t order_a, const int64_t *dims_a, const int32_t *s
         if (dims_a[ma] != dims_b[mb]) return ORC_ERR_INVALID;
         is_con_a[ma] = 1; is_con_b[mb] = 1;
     }
-    if (order_a - ncontract + order_b - ncontract > ORC_MAX_ORDER) return ORC_ERR_INVALID;
+    if (nentry < 0 || ncontract + nentry > order_a || ncontract + nentry > order_b) return ORC_ERR_INVALID;
+    for (int c = 0; c < nentry; ++c) {
+        int ma = emodes_a[c], mb = emodes_b[c];
+        if (ma < 0 || ma >= order_a || mb < 0 || mb >= order_b) return ORC_ERR_INVALID;
+        if (is_con_a[ma] || is_con_b[mb]) return ORC_ERR_INVALID;
+        if (dims_a[ma] != dims_b[mb]) return ORC_ERR_INVALID;
+        is_con_a[ma] = 2; is_con_b[mb] = 2;   /* 2: entrywise */
+        if (hsz > INT64_MAX / dims_a[ma]) return ORC_ERR_OVERFLOW;
+        hsz *= dims_a[ma];
+    }
+    if (nentry + (order_a - ncontract - nentry) + (order_b - ncontract - nentry) > ORC_MAX_ORDER)
+        return ORC_ERR_INVALID;
     for (int t = 0; t < order_a; ++t) if (!is_con_a[t]) {
         if (m > INT64_MAX / dims_a[t]) return ORC_ERR_OVERFLOW;
         m *= dims_a[t];
@@ -408,11 +432,12 @@ int lco_oracle_contract(int32_t order_a, const int64_t *dims_a, const int32_t *s
         if (n > INT64_MAX / dims_b[t]) return ORC_ERR_OVERFLOW;
         n *= dims_b[t];
     }
-    if (m > INT64_MAX / n) return ORC_ERR_OVERFLOW;
+    if (m > INT64_MAX / n || hsz > INT64_MAX / (m * n)) return ORC_ERR_OVERFLOW;
     if (nnz_a == 0 || nnz_b == 0) return ORC_OK;
 
-    /* B entries keyed by their contracted coordinates (pairing order, the
-     * first pair most significant), then by B's own LIV. */
+    /* B entries keyed by their entrywise, then contracted coordinates
+     * (pairing order, the first pair most significant), then by B's own
+     * LIV. */
     bs = (bent_t *)malloc(sizeof(bent_t) * (size_t)nnz_b);
     order_idx_a = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)nnz_a);
     if (!bs || !order_idx_a) { rc = ORC_ERR_OOM; goto done; }
@@ -420,6 +445,7 @@ int lco_oracle_contract(int32_t order_a, const int64_t *dims_a, const int32_t *s
         int64_t key = 0;
         if (liv_b[e] < 0 || liv_b[e] >= tot_b) { rc = ORC_ERR_INVALID; goto done; }
         delinearise_one(order_b, dims_b, sig_b, liv_b[e], coord);
+        for (int c = 0; c < nentry; ++c) key = key * dims_b[emodes_b[c]] + coord[emodes_b[c]];
         for (int c = 0; c < ncontract; ++c) key = key * dims_b[modes_b[c]] + coord[modes_b[c]];
         bs[e].key = key; bs[e].liv = liv_b[e]; bs[e].idx = e;
     }
@@ -435,11 +461,14 @@ int lco_oracle_contract(int32_t order_a, const int64_t *dims_a, const int32_t *s
 
     for (int64_t q = 0; q < nnz_a; ++q) {
         int64_t e = order_idx_a[2 * q + 1];
-        int64_t key = 0, row = 0;
+        int64_t key = 0, row = 0, h = 0;
         int64_t lo, hi;
         delinearise_one(order_a, dims_a, sig_a, liv_a[e], coord);
+        for (int c = 0; c < nentry; ++c) h = h * dims_a[emodes_a[c]] + coord[emodes_a[c]];
+        key = h;
         for (int c = 0; c < ncontract; ++c) key = key * dims_a[modes_a[c]] + coord[modes_a[c]];
         for (int t = 0; t < order_a; ++t) if (!is_con_a[t]) row = row * dims_a[t] + coord[t];
+        row += h * m;
         /* first B entry with this key (binary search) */
         lo = 0; hi = nnz_b;
         while (lo < hi) {
@@ -499,6 +528,18 @@ done:
     free(order_idx_a);
     free(prods);
     return rc;
+}
+
+int lco_oracle_contract(int32_t order_a, const int64_t *dims_a, const int32_t *sig_a,
+                        int64_t nnz_a, const int64_t *liv_a, const double *val_a,
+                        int32_t order_b, const int64_t *dims_b, const int32_t *sig_b,
+                        int64_t nnz_b, const int64_t *liv_b, const double *val_b,
+                        int32_t ncontract, const int32_t *modes_a, const int32_t *modes_b,
+                        int64_t *nnz_c, int64_t **liv_c, double **val_c, double **abs_c)
+{
+    return lco_oracle_contract_ew(order_a, dims_a, sig_a, nnz_a, liv_a, val_a, order_b, dims_b, sig_b, nnz_b,
+                                  liv_b, val_b, ncontract, modes_a, modes_b, 0, NULL, NULL, nnz_c, liv_c, val_c,
+                                  abs_c);
 }
 
 /* Number of products f = sum over A entries of the matching B entries
