@@ -283,6 +283,24 @@ int32_t lco_contract_plan_ex(const lco_shape *a, const lco_shape *b, int32_t nco
                              const int32_t *modes_a, const int32_t *modes_b,
                              const lco_tune *tune, lco_plan **plan);
 
+/* Contraction with entrywise mode pairs (Sec. 5: a product whose operands
+ * share indices that are neither summed nor dropped maps to one matrix
+ * product per value of the shared indices):
+ *     C[h, free_a, free_b] = sum_k A[h, free_a, k] B[h, k, free_b]
+ * (emodes_a[t], emodes_b[t]) are the shared pairs (equal dims, distinct from
+ * the contracted modes).  C's modes are the shared pairs (pairing order,
+ * dims from A), then A's free modes, then B's free modes; the shared modes
+ * are the most significant in C's order (lco_plan_info.c_shape gives the
+ * sig).  All of it is one product: the shared indices lead the rows of both
+ * matrix views, and an entry of row (h, i) meets R's row (h, k).  Table 4 is
+ * applied to the flattened views, whose dim/nnz ratios are the per-batch
+ * ones.  nentry = 0 is lco_contract_plan_ex.  The rest of the contraction
+ * API (workspace, phases, results) is unchanged. */
+int32_t lco_contract_plan_entrywise(const lco_shape *a, const lco_shape *b, int32_t ncontract,
+                                    const int32_t *modes_a, const int32_t *modes_b, int32_t nentry,
+                                    const int32_t *emodes_a, const int32_t *emodes_b, const lco_tune *tune,
+                                    lco_plan **plan);
+
 /* ------------------------------------------------------------------ */
 /* Batched contractions (many independent, uneven problems per call)    */
 /* ------------------------------------------------------------------ */

@@ -137,6 +137,9 @@ _SIGNATURES = {
     "lco_contract_plan_ex": ([ctypes.POINTER(Shape), ctypes.POINTER(Shape), ctypes.c_int32, ctypes.c_void_p,
                               ctypes.c_void_p, ctypes.POINTER(Tune), ctypes.POINTER(ctypes.c_void_p)],
                              ctypes.c_int32),
+    "lco_contract_plan_entrywise": ([ctypes.POINTER(Shape), ctypes.POINTER(Shape), ctypes.c_int32, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.POINTER(Tune), ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int32),
     "lco_batch_plan": ([ctypes.c_int32, ctypes.POINTER(Problem), ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)],
                        ctypes.c_int32),
     "lco_batch_destroy": ([ctypes.c_void_p], ctypes.c_int32),
@@ -384,19 +387,22 @@ class ContractPlan:
     digit width of operand permutations (tuning hints)."""
 
     def __init__(self, a_dims, a_sig, a_nnz, b_dims, b_sig, b_nnz, modes_a, modes_b, alg=None,
-                 max_digit_bits=0):
+                 max_digit_bits=0, entry_a=(), entry_b=()):
         self.lib = load()
         self.sa = make_shape(a_dims, a_sig, a_nnz)
         self.sb = make_shape(b_dims, b_sig, b_nnz)
-        if len(modes_a) != len(modes_b):
-            raise ValueError("modes_a and modes_b must pair up")
-        nc = len(modes_a)
+        if len(modes_a) != len(modes_b) or len(entry_a) != len(entry_b):
+            raise ValueError("modes_a/modes_b and entry_a/entry_b must pair up")
+        nc, ne = len(modes_a), len(entry_a)
         self._ma = (ctypes.c_int32 * max(1, nc))(*[int(x) for x in modes_a])
         self._mb = (ctypes.c_int32 * max(1, nc))(*[int(x) for x in modes_b])
+        self._ea = (ctypes.c_int32 * max(1, ne))(*[int(x) for x in entry_a])
+        self._eb = (ctypes.c_int32 * max(1, ne))(*[int(x) for x in entry_b])
         tune = Tune(_alg_code(alg), int(max_digit_bits))
         h = ctypes.c_void_p()
-        _check(self.lib.lco_contract_plan_ex(ctypes.byref(self.sa), ctypes.byref(self.sb), nc, self._ma, self._mb,
-                                             ctypes.byref(tune), ctypes.byref(h)), "lco_contract_plan_ex")
+        _check(self.lib.lco_contract_plan_entrywise(ctypes.byref(self.sa), ctypes.byref(self.sb), nc, self._ma,
+                                                    self._mb, ne, self._ea, self._eb, ctypes.byref(tune),
+                                                    ctypes.byref(h)), "lco_contract_plan_entrywise")
         self.handle = h
         info = PlanInfo()
         _check(self.lib.lco_plan_get_info(h, ctypes.byref(info)), "lco_plan_get_info")
@@ -461,10 +467,14 @@ class ContractPlan:
                "lco_contract")
 
 
-def contract(A: LcoTensor, B: LcoTensor, modes_a, modes_b, alg=None, stream=None, return_info=False):
-    """C = A x_modes B as an LCO tensor (Sec. 5.2).  Synchronises twice:
-    after phase 1 to size C by the product count f, and at the end to read nnz_C."""
-    plan = ContractPlan(A.dims, A.sig, A.nnz, B.dims, B.sig, B.nnz, modes_a, modes_b, alg)
+def contract(A: LcoTensor, B: LcoTensor, modes_a, modes_b, alg=None, stream=None, return_info=False,
+             entry_a=(), entry_b=()):
+    """C = A x_modes B as an LCO tensor (Sec. 5.2).  entry_a/entry_b pair up
+    shared modes kept in C (entrywise products, Sec. 5); C's modes are those
+    pairs, A's free modes, B's free modes.  Synchronises twice: after phase 1
+    to size C by the product count f, and at the end to read nnz_C."""
+    plan = ContractPlan(A.dims, A.sig, A.nnz, B.dims, B.sig, B.nnz, modes_a, modes_b, alg,
+                        entry_a=entry_a, entry_b=entry_b)
     dev = A.liv.device
     plan.ensure_workspace(0, dev)
     plan.symbolic(A, B, stream)

@@ -133,6 +133,14 @@ __device__ __forceinline__ void mdt_lookup_entry(const Mdt &m, int64_t e, const 
     mdt_lookup(m, l_liv[e] - rbase, b0, len);
 }
 
+// R's row met by an L entry in column c of L's row `row`.  With entrywise
+// mode pairs (Sec. 5) L's rows are (h, i) and R's rows (h, k): the entry
+// meets R row h * K + c, h = row div I (I = L rows per value of h); without
+// them I is all of L's rows and this is c.
+__device__ __forceinline__ int64_t r_row(const DivU64 &div_h, int64_t k, uint64_t row, int64_t c) {
+    return c + (int64_t)divu(div_h, row) * k;
+}
+
 // ------------------------------------------------------------------------
 // Block-wide scans (kCT threads)
 // ------------------------------------------------------------------------
@@ -379,6 +387,7 @@ struct ScanArgs {
     int64_t nnz_l;
     DivU64 div_k;
     int64_t k;
+    DivU64 div_h;          // L rows per value of the entrywise indices
     Mdt mdt;
     int64_t *P;            // [nnz_l + 1] or null
     uint64_t *ec;          // [nnz_l] entry cache (DCSR) or null
@@ -410,7 +419,7 @@ __global__ void __launch_bounds__(kCT) k_work_scan(const __grid_constant__ ScanA
         if (e < a.nnz_l) {
             const uint64_t liv = (uint64_t)a.l_liv[e];
             const uint64_t row = divu(a.div_k, liv);
-            const int64_t c = (int64_t)(liv - row * (uint64_t)a.k);
+            const int64_t c = r_row(a.div_h, a.k, row, (int64_t)(liv - row * (uint64_t)a.k));
             int64_t b0, len;
             mdt_lookup(a.mdt, c, b0, len);
             if (a.ec) a.ec[e] = ec_pack(b0, len);
@@ -612,6 +621,7 @@ struct HeavyArgs {
     const double *r_val;
     DivU64 div_k;
     int64_t k;
+    DivU64 div_h;
     DivU64 div_n;
     int64_t nR;
     int32_t colbits;
@@ -665,7 +675,7 @@ __device__ __forceinline__ void heavy_row(const HeavyArgs &a, HeavySmem &S, int6
                 const int64_t e = h0 + j;
                 const uint64_t liv = (uint64_t)a.l_liv[e];
                 const uint64_t row = divu(a.div_k, liv);
-                const int64_t c = (int64_t)(liv - row * (uint64_t)a.k);
+                const int64_t c = r_row(a.div_h, a.k, row, (int64_t)(liv - row * (uint64_t)a.k));
                 int64_t b0, len;
                 mdt_lookup_entry(a.mdt, e, c, b0, len);
                 S.b0[j] = b0;
@@ -743,7 +753,7 @@ __device__ __forceinline__ void heavy_row(const HeavyArgs &a, HeavySmem &S, int6
             if (e < eend) {
                 const uint64_t liv = (uint64_t)a.l_liv[e];
                 const uint64_t row = divu(a.div_k, liv);
-                c = (int64_t)(liv - row * (uint64_t)a.k);
+                c = r_row(a.div_h, a.k, row, (int64_t)(liv - row * (uint64_t)a.k));
                 mdt_lookup_entry(a.mdt, e, c, b0, len);
                 av = a.l_val[e];
             }
@@ -822,6 +832,7 @@ struct RowsArgs {
     const int64_t *r_liv;
     const double *r_val;
     int64_t k;
+    DivU64 div_h;
     DivU64 div_n;
     int64_t nR;
     Mdt mdt;
@@ -1019,7 +1030,7 @@ __device__ __forceinline__ int collect_runs(const RowsArgs &a, int64_t es, int64
                                             int64_t (&st)[kMergeRuns], int32_t (&ln)[kMergeRuns],
                                             double (&av)[kMergeRuns]) {
     int nr = 0;
-    const int64_t rbase = rid * a.k;
+    const int64_t rbase = (rid - (int64_t)divu(a.div_h, (uint64_t)rid)) * a.k;
 #pragma unroll
     for (int i = 0; i < kMergeRuns; ++i) {
         st[i] = 0;
@@ -1097,7 +1108,7 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
             } else if (nent <= kNetEnt && frow <= kNetProd && (sizeof(KeyT) == 4 || nR < (1ull << 59))) {
                 // ---- register network path ----
                 kind = kRowNet;
-                const int64_t rbase = rid * a.k;
+                const int64_t rbase = (rid - (int64_t)divu(a.div_h, (uint64_t)rid)) * a.k;
                 int64_t b0[kNetEnt];
                 int pre[kNetEnt + 1];
 #pragma unroll
@@ -1169,7 +1180,8 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
             sm &= sm - 1;
             const int64_t ses = __shfl_sync(kFull, es, src);
             const int64_t see = __shfl_sync(kFull, ee, src);
-            const int64_t srb = __shfl_sync(kFull, rid, src) * a.k;
+            const int64_t srid = __shfl_sync(kFull, rid, src);
+            const int64_t srb = (srid - (int64_t)divu(a.div_h, (uint64_t)srid)) * a.k;
             const int64_t spb = __shfl_sync(kFull, pb, src);
             int carry = 0;
             for (int64_t e0 = ses; e0 < see; e0 += 32) {
@@ -1347,7 +1359,7 @@ __global__ void __launch_bounds__(256) k_copy_rows(const __grid_constant__ RowsA
         int64_t b0 = 0, len = 0;
         double v = 0.0;
         for (int64_t e = es; e < ee && len == 0; ++e) {   // the row's one matching entry
-            mdt_lookup_entry(a.mdt, e, a.l_liv, rid * a.k, b0, len);
+            mdt_lookup_entry(a.mdt, e, a.l_liv, (rid - (int64_t)divu(a.div_h, (uint64_t)rid)) * a.k, b0, len);
             v = a.l_val[e];
         }
         const int64_t obase = a.row_hout[r];
@@ -1386,6 +1398,7 @@ struct SopArgs {
     int64_t nnz_l;
     DivU64 div_k;
     int64_t k;
+    DivU64 div_h;
     int64_t nR;
     Mdt mdt;
     const int64_t *P;
@@ -1404,7 +1417,7 @@ __global__ void __launch_bounds__(256) k_sop_expand(const __grid_constant__ SopA
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.nnz_l; e += gsz) {
         const uint64_t liv = (uint64_t)a.l_liv[e];
         const uint64_t row = divu(a.div_k, liv);
-        const int64_t c = (int64_t)(liv - row * (uint64_t)a.k);
+        const int64_t c = r_row(a.div_h, a.k, row, (int64_t)(liv - row * (uint64_t)a.k));
         int64_t b0, len;
         mdt_lookup_entry(a.mdt, e, c, b0, len);
         const int64_t po = a.P[e] - e;
@@ -1508,6 +1521,8 @@ struct lco_plan {
     int32_t lookup;              // lco::Lookup
     int32_t acc;                 // 1 accumulator, 0 no accumulator, 2 SOP
     int64_t mL, k, nR;
+    int64_t rows_h;              // L rows per value of the entrywise indices (mL without them)
+    int64_t kr;                  // R's rows: k per value of the entrywise indices
     int64_t nnz_l, nnz_r;
     int32_t colbits;
     int32_t aux_shift;
@@ -1580,6 +1595,13 @@ int32_t lco_contract_plan(const lco_shape *a, const lco_shape *b, int32_t ncontr
 
 int32_t lco_contract_plan_ex(const lco_shape *a, const lco_shape *b, int32_t ncontract, const int32_t *modes_a,
                              const int32_t *modes_b, const lco_tune *tune, lco_plan **plan_out) {
+    return lco_contract_plan_entrywise(a, b, ncontract, modes_a, modes_b, 0, nullptr, nullptr, tune, plan_out);
+}
+
+int32_t lco_contract_plan_entrywise(const lco_shape *a, const lco_shape *b, int32_t ncontract,
+                                    const int32_t *modes_a, const int32_t *modes_b, int32_t nentry,
+                                    const int32_t *emodes_a, const int32_t *emodes_b, const lco_tune *tune,
+                                    lco_plan **plan_out) {
     const int32_t force_alg = tune ? tune->alg : LCO_ALG_AUTO;
     const int max_bits = tune && tune->max_digit_bits > 0 ? tune->max_digit_bits : kDefaultDigitBits;
     if (tune && (tune->max_digit_bits < 0 || tune->max_digit_bits > kMaxDigitBits)) return LCO_ERR_INVALID;
@@ -1600,40 +1622,60 @@ int32_t lco_contract_plan_ex(const lco_shape *a, const lco_shape *b, int32_t nco
         if (a->dims[ma] != b->dims[mb]) return LCO_ERR_INVALID;
         con_a[ma] = con_b[mb] = 1;
     }
+    // entrywise pairs (Sec. 5): shared, kept in C, not summed
+    if (nentry < 0 || ncontract + nentry > a->order || ncontract + nentry > b->order) return LCO_ERR_INVALID;
+    if (nentry > 0 && (!emodes_a || !emodes_b)) return LCO_ERR_INVALID;
+    int64_t H = 1;
+    for (int i = 0; i < nentry; ++i) {
+        const int ma = emodes_a[i], mb = emodes_b[i];
+        if (ma < 0 || ma >= a->order || mb < 0 || mb >= b->order) return LCO_ERR_INVALID;
+        if (con_a[ma] || con_b[mb]) return LCO_ERR_INVALID;
+        if (a->dims[ma] != b->dims[mb]) return LCO_ERR_INVALID;
+        con_a[ma] = con_b[mb] = 2;
+        H *= a->dims[ma];
+    }
     int free_a[kMaxOrder], free_b[kMaxOrder], nfa = 0, nfb = 0;
     for (int t = 0; t < a->order; ++t) if (!con_a[t]) free_a[nfa++] = t;
     for (int t = 0; t < b->order; ++t) if (!con_b[t]) free_b[nfb++] = t;
-    if (nfa + nfb > kMaxOrder) return LCO_ERR_INVALID;
+    if (nentry + nfa + nfb > kMaxOrder) return LCO_ERR_INVALID;
     int64_t m = 1, k = 1, n = 1;
     for (int i = 0; i < nfa; ++i) m *= a->dims[free_a[i]];
     for (int i = 0; i < ncontract; ++i) k *= a->dims[modes_a[i]];
     for (int i = 0; i < nfb; ++i) n *= b->dims[free_b[i]];
-    if (m > INT64_MAX / n) return LCO_ERR_OVERFLOW;
+    if (m > INT64_MAX / n || H > INT64_MAX / (m * n)) return LCO_ERR_OVERFLOW;
 
     // matrix orders (most significant first), converted to sig (least significant first)
     int32_t a_row[kMaxOrder], a_col[kMaxOrder], b_row[kMaxOrder], b_col[kMaxOrder];
     {
+        // the entrywise modes lead every matrix order: one matrix product
+        // per value of them (Sec. 5)
         int32_t msf[kMaxOrder];
         int q = 0;
+        for (int i = 0; i < nentry; ++i) msf[q++] = emodes_a[i];
         for (int i = 0; i < nfa; ++i) msf[q++] = free_a[i];
         for (int i = 0; i < ncontract; ++i) msf[q++] = modes_a[i];
         for (int i = 0; i < q; ++i) a_row[i] = msf[q - 1 - i];
         q = 0;
+        for (int i = 0; i < nentry; ++i) msf[q++] = emodes_a[i];
         for (int i = 0; i < ncontract; ++i) msf[q++] = modes_a[i];
         for (int i = 0; i < nfa; ++i) msf[q++] = free_a[i];
         for (int i = 0; i < q; ++i) a_col[i] = msf[q - 1 - i];
         q = 0;
+        for (int i = 0; i < nentry; ++i) msf[q++] = emodes_b[i];
         for (int i = 0; i < ncontract; ++i) msf[q++] = modes_b[i];
         for (int i = 0; i < nfb; ++i) msf[q++] = free_b[i];
         for (int i = 0; i < q; ++i) b_row[i] = msf[q - 1 - i];
         q = 0;
+        for (int i = 0; i < nentry; ++i) msf[q++] = emodes_b[i];
         for (int i = 0; i < nfb; ++i) msf[q++] = free_b[i];
         for (int i = 0; i < ncontract; ++i) msf[q++] = modes_b[i];
         for (int i = 0; i < q; ++i) b_col[i] = msf[q - 1 - i];
     }
     const int perm_row = !same_sig(a->order, a->sig, a_row) + !same_sig(b->order, b->sig, b_row);
     const int perm_col = !same_sig(a->order, a->sig, a_col) + !same_sig(b->order, b->sig, b_col);
-    const int ca = sparsity_class(m, k, a->nnz), cb = sparsity_class(k, n, b->nnz);
+    // the flattened operands ((h, i) x (h, k) and (h, k) x (h, j)) have the
+    // per-batch ratios dim / (nnz / H)
+    const int ca = sparsity_class(H * m, H * k, a->nnz), cb = sparsity_class(H * k, H * n, b->nnz);
     int alg = force_alg;
     if (alg < 0) {
         const int cell = kTable4[ca][cb];
@@ -1660,9 +1702,11 @@ int32_t lco_contract_plan_ex(const lco_shape *a, const lco_shape *b, int32_t nco
     if ((rc = rp_plan(&p->src_r, r_target, &p->rp_r, max_bits)) != LCO_OK) { delete p; return rc; }
     p->need_l = !same_sig(p->src_l.order, p->src_l.sig, l_target);
     p->need_r = !same_sig(p->src_r.order, p->src_r.sig, r_target);
-    p->mL = transposed ? n : m;
+    p->rows_h = transposed ? n : m;
+    p->mL = H * p->rows_h;
     p->nR = transposed ? m : n;
     p->k = k;
+    p->kr = H * k;
     p->nnz_l = p->src_l.nnz;
     p->nnz_r = p->src_r.nnz;
     p->colbits = bits_host((uint64_t)p->nR);
@@ -1677,10 +1721,10 @@ int32_t lco_contract_plan_ex(const lco_shape *a, const lco_shape *b, int32_t nco
     {
         uint64_t na = 1;
         while (na < (uint64_t)(p->nnz_r > 0 ? p->nnz_r : 1)) na <<= 1;
-        const int kb = bits_host((uint64_t)k);
+        const int kb = bits_host((uint64_t)p->kr);
         const int nb = bits_host(na);
         p->aux_shift = kb > nb ? kb - nb : 0;
-        p->naux = (int64_t)(((uint64_t)(k - 1) >> p->aux_shift) + 1);
+        p->naux = (int64_t)(((uint64_t)(p->kr - 1) >> p->aux_shift) + 1);
     }
     // info
     p->info.alg = alg;
@@ -1693,9 +1737,11 @@ int32_t lco_contract_plan_ex(const lco_shape *a, const lco_shape *b, int32_t nco
     p->info.k = k;
     p->info.n = n;
     {
+        // C's modes: the entrywise pairs, A's free modes, B's free modes
         lco_shape &cs = p->info.c_shape;
-        cs.order = nfa + nfb;
+        cs.order = nentry + nfa + nfb;
         int q = 0;
+        for (int i = 0; i < nentry; ++i) cs.dims[q++] = a->dims[emodes_a[i]];
         for (int i = 0; i < nfa; ++i) cs.dims[q++] = a->dims[free_a[i]];
         for (int i = 0; i < nfb; ++i) cs.dims[q++] = b->dims[free_b[i]];
         if (cs.order == 0) {
@@ -1705,11 +1751,13 @@ int32_t lco_contract_plan_ex(const lco_shape *a, const lco_shape *b, int32_t nco
         } else if (!transposed) {
             for (int i = 0; i < cs.order; ++i) cs.sig[i] = cs.order - 1 - i;
         } else {
-            // most significant first: B's free modes (nfa..), then A's free modes (0..nfa-1)
+            // most significant first: the entrywise modes, B's free modes,
+            // then A's free modes
             int32_t msf[kMaxOrder];
             int t = 0;
-            for (int i = 0; i < nfb; ++i) msf[t++] = nfa + i;
-            for (int i = 0; i < nfa; ++i) msf[t++] = i;
+            for (int i = 0; i < nentry; ++i) msf[t++] = i;
+            for (int i = 0; i < nfb; ++i) msf[t++] = nentry + nfa + i;
+            for (int i = 0; i < nfa; ++i) msf[t++] = nentry + i;
             for (int i = 0; i < cs.order; ++i) cs.sig[i] = msf[cs.order - 1 - i];
         }
         cs.nnz = 0;
@@ -1736,7 +1784,7 @@ int32_t lco_contract_plan_ex(const lco_shape *a, const lco_shape *b, int32_t nco
         p->off_rp = take(rb);
     }
     if (p->lookup == kLookupCsr) {
-        p->off_mdt_rowptr = take((size_t)(k + 1) * 8);
+        p->off_mdt_rowptr = take((size_t)(p->kr + 1) * 8);
     } else {
         p->off_mdt_rowptr = take((size_t)(nr + 1) * 8);
         p->off_mdt_rowid = take((size_t)nr * 8);
@@ -1802,7 +1850,7 @@ Operands operands(const lco_plan *p, const int64_t *a_liv, const double *a_val, 
 Mdt make_mdt(const lco_plan *p, char *ws) {
     Mdt m{};
     m.kind = p->lookup;
-    m.k = p->k;
+    m.k = p->kr;
     m.nnz = p->nnz_r;
     m.row_ptr = reinterpret_cast<int64_t *>(ws + p->off_mdt_rowptr);
     if (p->lookup == kLookupDcsr) {
@@ -1856,9 +1904,9 @@ int32_t symbolic_enqueue(const lco_plan *p, const int64_t *a_liv, const double *
     uint64_t *scan_state = reinterpret_cast<uint64_t *>(ws + p->off_p1state);
     uint64_t *dcsr_state = scan_state + 2 * (((p->nnz_l + kScanTile - 1) / kScanTile) + 1);
     if (p->lookup == kLookupCsr) {
-        int64_t grid = (std::max<int64_t>(p->nnz_r, p->k + 1) + 255) / 256;
+        int64_t grid = (std::max<int64_t>(p->nnz_r, p->kr + 1) + 255) / 256;
         if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
-        LCO_LAUNCH("k_csr_rowptr", s, k_csr_rowptr<<<(unsigned)grid, 256, 0, s>>>(o.r_liv, p->nnz_r, div_n, p->k,
+        LCO_LAUNCH("k_csr_rowptr", s, k_csr_rowptr<<<(unsigned)grid, 256, 0, s>>>(o.r_liv, p->nnz_r, div_n, p->kr,
                                                     const_cast<int64_t *>(mdt.row_ptr)));
     } else {
         DcsrArgs d{};
@@ -1882,6 +1930,7 @@ int32_t symbolic_enqueue(const lco_plan *p, const int64_t *a_liv, const double *
     sa.nnz_l = p->nnz_l;
     sa.div_k = make_div((uint64_t)p->k);
     sa.k = p->k;
+    sa.div_h = make_div((uint64_t)p->rows_h);
     sa.mdt = mdt;
     sa.mdt.ec = nullptr;   // written by this scan
     sa.P = p->acc == 2 ? reinterpret_cast<int64_t *>(ws + p->off_P) : nullptr;
@@ -1966,6 +2015,7 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         ha.r_val = o.r_val;
         ha.div_k = make_div((uint64_t)p->k);
         ha.k = p->k;
+        ha.div_h = make_div((uint64_t)p->rows_h);
         ha.div_n = make_div((uint64_t)p->nR);
         ha.nR = p->nR;
         ha.colbits = p->colbits;
@@ -2001,6 +2051,7 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         ra.r_liv = o.r_liv;
         ra.r_val = o.r_val;
         ra.k = p->k;
+        ra.div_h = make_div((uint64_t)p->rows_h);
         ra.div_n = make_div((uint64_t)p->nR);
         ra.nR = p->nR;
         ra.mdt = mdt;
@@ -2041,6 +2092,7 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         sa.nnz_l = p->nnz_l;
         sa.div_k = make_div((uint64_t)p->k);
         sa.k = p->k;
+        sa.div_h = make_div((uint64_t)p->rows_h);
         sa.nR = p->nR;
         sa.mdt = mdt;
         sa.P = P;

@@ -17,9 +17,9 @@ def host(t):
     return t.liv.cpu().numpy(), t.val.cpu().numpy()
 
 
-def oracle_contract_in(A, B, ma, mb, c_dims, c_sig):
+def oracle_contract_in(A, B, ma, mb, c_dims, c_sig, ea=(), eb=()):
     """Oracle result expressed in the order c_sig (the oracle produces row-major)."""
-    liv, val, ab = oracle.contract(A, B, ma, mb)
+    liv, val, ab = oracle.contract(A, B, ma, mb, ea, eb)
     rm = list(range(len(c_dims) - 1, -1, -1))
     if list(c_sig) != rm and liv.shape[0] > 0:
         l2, v2 = oracle.permute(c_dims, rm, c_sig, liv, val)
@@ -29,9 +29,9 @@ def oracle_contract_in(A, B, ma, mb, c_dims, c_sig):
     return liv, val, ab
 
 
-def assert_contract_matches(C, A, B, ma, mb, tol=TOL):
+def assert_contract_matches(C, A, B, ma, mb, tol=TOL, ea=(), eb=()):
     liv, val = host(C)
-    rl, rv, ra = oracle_contract_in(A, B, ma, mb, C.dims, C.sig)
+    rl, rv, ra = oracle_contract_in(A, B, ma, mb, C.dims, C.sig, ea, eb)
     assert liv.shape == rl.shape, f"nnz {liv.shape[0]} vs oracle {rl.shape[0]}"
     assert np.array_equal(liv, rl), "index pattern differs from the oracle"
     err = np.abs(val - rv)

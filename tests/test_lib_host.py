@@ -140,3 +140,13 @@ def test_timing_hooks_without_launches():
     assert lco.timing_read() == []
     lco.timing_enable(False)
     assert lco.launch_count() >= 0
+
+
+def test_entrywise_plan_validation():
+    import paper_1802_02619_gb300 as lco
+    with pytest.raises(lco.LcoError):      # a mode both contracted and entrywise
+        lco.ContractPlan([3, 4], [1, 0], 5, [3, 4], [1, 0], 5, [1], [1], entry_a=[1], entry_b=[1])
+    with pytest.raises(lco.LcoError):      # entrywise dims differ
+        lco.ContractPlan([3, 4], [1, 0], 5, [4, 3], [1, 0], 5, [], [], entry_a=[0], entry_b=[0])
+    p = lco.ContractPlan([3, 4, 5], [2, 1, 0], 30, [3, 5, 6], [2, 1, 0], 40, [2], [1], entry_a=[0], entry_b=[0])
+    assert p.c_dims == [3, 4, 6] and p.c_sig == [2, 1, 0]
