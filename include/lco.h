@@ -358,6 +358,24 @@ int32_t lco_batch_results(const lco_batch *batch, const int64_t *caps, const voi
                           lco_contract_result *out, void *stream);
 
 /* ------------------------------------------------------------------ */
+/* Failure detection self-test (no paper counterpart)                   */
+/* ------------------------------------------------------------------ */
+
+/* Every device-side wait in the library (decoupled look-back over tiles,
+ * bulk-copy mbarrier phases) gives up after a budget of SM clock cycles
+ * (about one second), records LCO_ERR_TIMEOUT in the status word and lets
+ * its kernel finish, so a lost producer never hangs the GPU.  This call
+ * makes both kinds of wait run out on purpose: with the budget lowered to
+ * budget_cycles (for this test kernel only), one warp looks back over tiles
+ * that never publish and one thread waits on an mbarrier phase that never
+ * completes.  scratch: device memory of at least 512 bytes (any content).
+ * Synchronises `stream`; *lookback_status and *mbarrier_status receive the
+ * two waits' status (LCO_ERR_TIMEOUT when they ran out as designed).
+ * Errors: LCO_ERR_INVALID, LCO_ERR_CUDA. */
+int32_t lco_selftest_wait(void *scratch, int64_t budget_cycles, int32_t *lookback_status,
+                          int32_t *mbarrier_status, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* Sorting and addition (Sec. 3.2; the sum of Eq. 4, Fig. 3c)           */
 /* ------------------------------------------------------------------ */
 

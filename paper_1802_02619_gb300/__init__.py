@@ -153,6 +153,8 @@ _SIGNATURES = {
                            ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int32),
     "lco_batch_results": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ContractResult),
                           ctypes.c_void_p], ctypes.c_int32),
+    "lco_selftest_wait": ([ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
+                           ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p], ctypes.c_int32),
     "lco_sort_workspace": ([ctypes.POINTER(Shape), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int32),
     "lco_sort": ([ctypes.POINTER(Shape)] + [ctypes.c_void_p] * 5 + [ctypes.c_size_t, ctypes.c_void_p],
                  ctypes.c_int32),
@@ -596,6 +598,21 @@ class Batch:
             out.append(LcoTensor(self.info[i]["c_dims"], self.info[i]["c_sig"], self.c_liv_all[o:o + nc],
                                  self.c_val_all[o:o + nc]))
         return out
+
+
+# ---------------------------------------------------------------------------
+# Failure detection self-test
+# ---------------------------------------------------------------------------
+
+def selftest_wait(budget_cycles: int = 1_000_000, stream=None):
+    """Make the library's bounded device waits run out on purpose (see
+    lco_selftest_wait); returns (look-back status, mbarrier status)."""
+    lib = load()
+    scratch = workspace(512)
+    lb, mb = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib.lco_selftest_wait(_ptr(scratch), ctypes.c_int64(budget_cycles), ctypes.byref(lb), ctypes.byref(mb),
+                                 _stream(stream)), "lco_selftest_wait")
+    return lb.value, mb.value
 
 
 # ---------------------------------------------------------------------------

@@ -179,6 +179,7 @@ int32_t lco_sort_workspace(const lco_shape *t, size_t *ws_bytes) {
 
 int32_t lco_sort(const lco_shape *t, const int64_t *in_liv, const double *in_val, int64_t *out_liv, double *out_val,
                  void *ws, size_t ws_bytes, void *stream) {
+    NvtxRange nvtx("lco_sort");
     if (!t || !ws) return LCO_ERR_INVALID;
     RpPlan p;
     int32_t rc = sort_plan(t, &p);
@@ -208,6 +209,7 @@ int32_t lco_add_workspace(int64_t nnz_a, int64_t nnz_b, size_t *ws_bytes) {
 int32_t lco_add(const lco_shape *t, double alpha, const int64_t *a_liv, const double *a_val, int64_t nnz_a,
                 double beta, const int64_t *b_liv, const double *b_val, int64_t nnz_b, int64_t *c_liv, double *c_val,
                 void *ws, size_t ws_bytes, void *stream) {
+    NvtxRange nvtx("lco_add");
     if (!t || !ws || nnz_a < 0 || nnz_b < 0) return LCO_ERR_INVALID;
     int64_t total = 0;
     const int32_t rc = check_shape(t, &total);

@@ -164,6 +164,7 @@ int32_t lco_batch_numeric(lco_batch *b, const lco_operands *ops, const int64_t *
 
 int32_t lco_batch_contract(lco_batch *b, const lco_operands *ops, const int64_t *caps, void *ws, size_t ws_bytes,
                            void *stream) {
+    lco::NvtxRange nvtx("lco_batch_contract");
     if (!b || !ops || !ws || !caps) return LCO_ERR_INVALID;
     std::vector<size_t> offs;
     size_t total = 0;

@@ -2208,6 +2208,7 @@ extern "C" {
 int32_t lco_contract_symbolic(const lco_plan *plan, const int64_t *a_liv, const double *a_val,
                               const int64_t *b_liv, const double *b_val, void *ws, size_t ws_bytes,
                               void *stream) {
+    NvtxRange nvtx("lco_contract_symbolic");
     if (!plan) return LCO_ERR_INVALID;
     int32_t rc = check_ws(plan, ws, ws_bytes, -1);
     if (rc != LCO_OK) return rc;
@@ -2219,6 +2220,7 @@ int32_t lco_contract_symbolic(const lco_plan *plan, const int64_t *a_liv, const 
 int32_t lco_contract_numeric(const lco_plan *plan, const int64_t *a_liv, const double *a_val,
                              const int64_t *b_liv, const double *b_val, int64_t *c_liv, double *c_val,
                              int64_t cap, void *ws, size_t ws_bytes, void *stream) {
+    NvtxRange nvtx("lco_contract_numeric");
     if (!plan || cap < 0) return LCO_ERR_INVALID;
     int32_t rc = check_ws(plan, ws, ws_bytes, cap);
     if (rc != LCO_OK) return rc;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "lco.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace lco {
 
@@ -14,6 +15,9 @@ constexpr int kWsHeaderBytes = 256;
 // cycles (about one second at 2 GHz), records LCO_ERR_TIMEOUT and continues
 // with a zero contribution so that the kernel always terminates.
 constexpr long long kSpinBudgetCycles = 2000000000LL;
+// The budget in force (per translation unit); the wait self-test lowers it
+// to make a wait run out on purpose.
+static __device__ long long g_spin_budget = kSpinBudgetCycles;
 
 // ---------------------------------------------------------------------------
 // Unsigned 64-bit division by an invariant divisor.
@@ -148,7 +152,7 @@ __device__ __forceinline__ uint64_t lookback(const uint64_t *state, int64_t tile
         for (int i = 0; i < kLookbackBatch; ++i) {
             if (t - i < 0) return excl;
             while ((s[i] >> 62) == 0) {
-                if (clock64() - t0 > kSpinBudgetCycles) {
+                if (clock64() - t0 > g_spin_budget) {
                     set_error(status, LCO_ERR_TIMEOUT);
                     return excl;
                 }
@@ -200,7 +204,7 @@ __device__ __forceinline__ uint64_t lookback_warp(const uint64_t *state, int64_t
                     break;
                 }
                 // warp-uniform decision, so that all lanes leave together
-                if (__any_sync(0xffffffffu, clock64() - t0 > kSpinBudgetCycles)) {
+                if (__any_sync(0xffffffffu, clock64() - t0 > g_spin_budget)) {
                     if (lane == 0) set_error(status, LCO_ERR_TIMEOUT);
                     return excl;
                 }
@@ -261,7 +265,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kSpinBudgetCycles) return false;
+        if (clock64() - t0 > g_spin_budget) return false;
     }
     return true;
 }
@@ -273,6 +277,15 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// NVTX range over a public entry point (visible in ncu/nsys timelines; a
+// no-op when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Kernel timing / launch counting (implemented in lco_api.cu).
 void timing_begin(const char *name, cudaStream_t s);

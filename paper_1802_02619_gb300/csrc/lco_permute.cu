@@ -248,6 +248,7 @@ int32_t lco_radix_permute_workspace(const lco_shape *t, const int32_t *new_sig, 
 int32_t lco_radix_permute(const lco_shape *t, const int32_t *new_sig, const int64_t *liv_in,
                           const double *val_in, int64_t *liv_out, double *val_out, void *ws,
                           size_t ws_bytes, void *stream) {
+    NvtxRange nvtx("lco_radix_permute");
     RpPlan p;
     int32_t rc = rp_plan(t, new_sig, &p);
     if (rc != LCO_OK) return rc;
