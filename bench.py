@@ -77,6 +77,7 @@ def parse_args():
                     help="cap on the radix digit width of the operand permutations (0: library default)")
     ap.add_argument("--streams", type=int, default=16, help="stream pool for --case batch")
     ap.add_argument("--per-kind", action="store_true", help="--case batch: also time each kind alone")
+    ap.add_argument("--tune", action="store_true", help="--case batch: also run the autotuned batch")
     ap.add_argument("--requests", type=int, default=10000, help="--case serve: requests per run")
     ap.add_argument("--slots", type=int, default=64, help="--case serve: requests in flight")
     ap.add_argument("--workers", type=int, default=8, help="--case serve: host worker threads")
@@ -699,6 +700,8 @@ def run_batch_case(args):
     for _ in range(Kp):
         plain()
     ms_plain = (time.perf_counter() - t0) * 1e3 / Kp
+    del plans, c_liv, c_val                 # the plain loop's workspaces
+    torch.cuda.empty_cache()
 
     out = {
         "metric": "batched contraction GNNZ/s", "value": round(units / (ms_batch * 1e-3) / 1e9, 4),
@@ -716,6 +719,35 @@ def run_batch_case(args):
         "gpu_launches": int(launches_per_step * K),
         "clocks": clk,
     }
+    if args.tune:
+        # the autotuner's per-signature choices (one sample per group), then
+        # the same batch rebuilt with them and replayed the same way
+        from paper_1802_02619_gb300.tune import Tuner
+        t_tune = time.perf_counter()
+        tuner = Tuner(cache_path=None, reps=2)
+        choice = tuner.tune_batch(items, per_class=1)
+        t_tune = time.perf_counter() - t_tune
+        bt = lco.Batch([it + (alg, bits) for it, (alg, bits) in zip(items, choice)], nstreams=args.streams)
+        bt.run()
+        gt = torch.cuda.CUDAGraph()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(gt, stream=side):
+                bt.run()
+        stream.wait_stream(side)
+        for _ in range(3):
+            gt.replay()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(K):
+            gt.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_t = e0.elapsed_time(e1) / K
+        changed = sum(1 for inf, (alg, bits) in zip(batch.info, choice) if inf["alg"] != alg or bits != 0)
+        out["tuned"] = {"value": round(units / (ms_t * 1e-3) / 1e9, 4), "ms_per_step": round(ms_t, 4),
+                        "groups": len(tuner.cache), "problems_changed": changed, "tune_s": round(t_tune, 1)}
+        del gt, bt
     if args.per_kind:
         # each kind of problem as a batch of its own (same graph replay)
         per = {}
