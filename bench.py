@@ -109,11 +109,13 @@ def barrier(world):
 
 
 def reduce_max(x, world):
+    """Maximum of x over the ranks (NCCL on GPUs, gloo on the CPU)."""
     if world <= 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
