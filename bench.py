@@ -65,7 +65,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["lco", "reference"], default="lco")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["step", "permute", "batch", "serve"], default="step",
+    ap.add_argument("--case", choices=["step", "permute", "batch", "serve", "permsweep"], default="step",
                     help="step: the benchmark workload; permute: a stand-alone radix permutation "
                          "of a random 6th-order 64^6 tensor (profiling aid)")
     ap.add_argument("--nnz", type=int, default=16 << 20, help="non-zeros for --case permute")
@@ -79,6 +79,7 @@ def parse_args():
     ap.add_argument("--per-kind", action="store_true", help="--case batch: also time each kind alone")
     ap.add_argument("--tune", action="store_true", help="--case batch: also run the autotuned batch")
     ap.add_argument("--requests", type=int, default=10000, help="--case serve: requests per run")
+    ap.add_argument("--N", type=int, default=2895, help="--case permsweep: image side of the Eq. 4 operator")
     ap.add_argument("--slots", type=int, default=64, help="--case serve: requests in flight")
     ap.add_argument("--workers", type=int, default=8, help="--case serve: host worker threads")
     return ap.parse_args()
@@ -937,6 +938,59 @@ def run_serve_case(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# permutation sweep: every order of the Eq. 4 operator (Table 2's setting)
+# ---------------------------------------------------------------------------
+
+def run_permsweep_case(args):
+    """The combinatorial Laplacian of Eq. 4 (N x N image: N^4 index space,
+    ~5 N^2 entries) permuted from its row-major order into each of the 23
+    other orders of its four modes with the radix permutation (Sec. 4.1).
+    Per order: median time over the timed repetitions (L2 flushed before
+    each), keys/s, and the sort key's width and passes after the resting
+    digits are skipped."""
+    import itertools
+    import torch
+    import paper_1802_02619_gb300 as lco
+    import synth
+    from paper_1802_02619_gb300.laplacian import combinatorial_laplacian
+    N = args.N
+    a = combinatorial_laplacian(lco.LcoTensor.from_host(synth.fd_matrix(N), "cuda"),
+                                lco.LcoTensor.from_host(synth.kronecker_delta(N), "cuda"))
+    n = a.nnz
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out_l, out_v = torch.empty_like(a.liv), torch.empty_like(a.val)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for perm in itertools.permutations(range(4)):
+        sig = list(perm)
+        if sig == list(a.sig):
+            continue
+        info = lco.radix_permute_info(a.dims, a.sig, sig, n)
+        p = lco.Permuter(a.dims, a.sig, sig, n)
+        for _ in range(max(args.warmup, 2)):
+            p(a.liv, a.val, out_l, out_v)
+        ts = []
+        for _ in range(max(args.steps, 3)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p(a.liv, a.val, out_l, out_v)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        assert p.device_status() == 0
+        ms = statistics.median(ts)
+        rows.append({"sig": sig, "ms": round(ms, 4), "gkeys_s": round(n / (ms * 1e-3) / 1e9, 3),
+                     "key_bits": info["key_bits"], "passes": info["passes"], "n_rearr": info["n_rearr"]})
+    ms_all = sorted(r["ms"] for r in rows)
+    out = {"case": "permsweep", "metric": "permutation Gkeys/s", "N": N, "nnz": n, "orders": len(rows),
+           "summary_ms": {"max": ms_all[-1], "median": ms_all[len(ms_all) // 2], "min": ms_all[0]},
+           "paper_context": "RP on an E8400 at N ~ 2896 (Table 2): max 3.54 s, median 3.45 s, min 1.38 s",
+           "rows": rows}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.case == "permute":
@@ -947,6 +1001,9 @@ def main():
         return
     if args.case == "serve":
         run_serve_case(args)
+        return
+    if args.case == "permsweep":
+        run_permsweep_case(args)
         return
     if args.impl == "reference":
         run_reference(args)
