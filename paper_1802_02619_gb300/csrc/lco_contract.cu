@@ -1120,15 +1120,38 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
                 int64_t lv[kNetEnt];
 #pragma unroll
                 for (int s2 = 0; s2 < kNetEnt; ++s2) lv[s2] = s2 < nent ? a.l_liv[es + s2] : 0;
-                int run = 0;
+                int run = 0, mx = 0;
 #pragma unroll
                 for (int s2 = 0; s2 < kNetEnt; ++s2) {
                     int64_t len = 0;
                     if (s2 < nent) mdt_lookup_entry(a.mdt, es + s2, lv[s2] - rbase, b0[s2], len);
                     pre[s2] = run;
                     run += (int)len;
+                    mx = (int)len > mx ? (int)len : mx;
                 }
                 pre[kNetEnt] = run;
+                if (mx <= kNetProd / kNetEnt) {
+                    // every R row holds at most two entries: entry s2's t-th
+                    // product takes register slot s2 + 8 t (the sort ignores
+                    // positions; the key carries the generation index), and
+                    // its column is its LIV minus the R row's base
+#pragma unroll
+                    for (int s2 = 0; s2 < kNetEnt; ++s2) {
+                        const bool live = s2 < nent;
+                        const double av = live ? a.l_val[es + s2] : 0.0;
+                        const int64_t cb = (lv[s2] - rbase) * (int64_t)nR;
+#pragma unroll
+                        for (int t = 0; t < kNetProd / kNetEnt; ++t) {
+                            const int p = s2 + kNetEnt * t;
+                            nk[p] = kNone;
+                            if (live && t < pre[s2 + 1] - pre[s2]) {
+                                const int64_t b = b0[s2] + t;
+                                nk[p] = ((KeyT)(a.r_liv[b] - cb) << 4) | (KeyT)(pre[s2] + t);
+                                S.nval[pre[s2] + t][lane] = av * a.r_val[b];
+                            }
+                        }
+                    }
+                } else {
 #pragma unroll
                 for (int q = 0; q < kNetProd; ++q) {
                     nk[q] = kNone;
@@ -1148,6 +1171,7 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
                         nk[q] = ((KeyT)col_of(a.div_n, nR, a.r_liv[b]) << 4) | (KeyT)q;
                         S.nval[q][lane] = a.l_val[es + sel] * a.r_val[b];
                     }
+                }
                 }
                 net_sort<KeyT>(nk);
                 int u = 0;
