@@ -893,14 +893,28 @@ __device__ __forceinline__ uint64_t col_of(const DivU64 &div_n, uint64_t nR, int
 template <bool kWrite, typename KeyT>
 __device__ __forceinline__ int lane_merge_g(const RowsArgs &a, const int64_t (&st)[kMergeRuns],
                                             const int32_t (&ln)[kMergeRuns], const double (&av)[kMergeRuns],
-                                            int64_t base, int64_t *out_liv, double *out_val) {
+                                            int64_t base, int64_t *out_liv,
+                                            double *out_val) {
     constexpr KeyT kNone = (KeyT)~(KeyT)0;
-    int32_t pos[kMergeRuns];
+    // run i's next entry and the entries it has left; a column is the R
+    // entry's LIV less its row's first LIV cb[i] (one division per run),
+    // taken in KeyT arithmetic (exact: every column fits KeyT)
+    int64_t p[kMergeRuns];
+    int32_t left[kMergeRuns];
+    KeyT cb[kMergeRuns];
     KeyT hk[kMergeRuns];
 #pragma unroll
     for (int i = 0; i < kMergeRuns; ++i) {
-        pos[i] = 0;
-        hk[i] = ln[i] > 0 ? (KeyT)col_of(a.div_n, (uint64_t)a.nR, a.r_liv[st[i]]) : kNone;
+        p[i] = st[i];
+        left[i] = ln[i];
+        cb[i] = 0;
+        hk[i] = kNone;
+        if (left[i] > 0) {
+            const int64_t l0 = a.r_liv[p[i]];
+            const uint64_t c0 = col_of(a.div_n, (uint64_t)a.nR, l0);
+            cb[i] = (KeyT)((uint64_t)l0 - c0);
+            hk[i] = (KeyT)c0;
+        }
     }
     int o = 0;
     for (;;) {
@@ -916,12 +930,13 @@ __device__ __forceinline__ int lane_merge_g(const RowsArgs &a, const int64_t (&s
         for (int i = 0; i < kMergeRuns; ++i) {
             if (hk[i] == m) {
                 if (kWrite) {
-                    const double pr = __dmul_rn(av[i], a.r_val[st[i] + pos[i]]);
+                    const double pr = __dmul_rn(av[i], a.r_val[p[i]]);
                     s = first ? pr : __dadd_rn(s, pr);
                     first = false;
                 }
-                ++pos[i];
-                hk[i] = pos[i] < ln[i] ? (KeyT)col_of(a.div_n, (uint64_t)a.nR, a.r_liv[st[i] + pos[i]]) : kNone;
+                ++p[i];
+                --left[i];
+                hk[i] = left[i] > 0 ? (KeyT)a.r_liv[p[i]] - cb[i] : kNone;
             }
         }
         if (kWrite) {
