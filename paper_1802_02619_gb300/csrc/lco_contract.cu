@@ -1072,6 +1072,33 @@ __device__ __forceinline__ int collect_runs(const RowsArgs &a, int64_t es, int64
     return nr;
 }
 
+// Direct register-slot gather of a network row (see k_rows): E entries at
+// most, each meeting an R row of at most kNetProd / E entries; slot
+// s2 + E t holds entry s2's t-th product.
+template <int E, typename KeyT>
+__device__ __forceinline__ void net_gather_direct(const RowsArgs &a, int64_t es, int64_t nent, int64_t rbase,
+                                                  const int64_t (&lv)[kNetEnt], const int64_t (&b0)[kNetEnt],
+                                                  const int (&pre)[kNetEnt + 1], KeyT (&nk)[kNetProd],
+                                                  double (&nval)[16][32], int lane) {
+    constexpr KeyT kNone = (KeyT)~(KeyT)0;
+#pragma unroll
+    for (int s2 = 0; s2 < E; ++s2) {
+        const bool live = s2 < nent;
+        const double av = live ? a.l_val[es + s2] : 0.0;
+        const int64_t cb = (lv[s2] - rbase) * a.nR;
+#pragma unroll
+        for (int t = 0; t < kNetProd / E; ++t) {
+            const int p = s2 + E * t;
+            nk[p] = kNone;
+            if (live && t < pre[s2 + 1] - pre[s2]) {
+                const int64_t b = b0[s2] + t;
+                nk[p] = ((KeyT)(a.r_liv[b] - cb) << 4) | (KeyT)(pre[s2] + t);
+                nval[pre[s2] + t][lane] = av * a.r_val[b];
+            }
+        }
+    }
+}
+
 template <typename KeyT>
 __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant__ RowsArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1145,27 +1172,17 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
                     mx = (int)len > mx ? (int)len : mx;
                 }
                 pre[kNetEnt] = run;
-                if (mx <= kNetProd / kNetEnt) {
-                    // every R row holds at most two entries: entry s2's t-th
-                    // product takes register slot s2 + 8 t (the sort ignores
-                    // positions; the key carries the generation index), and
-                    // its column is its LIV minus the R row's base
-#pragma unroll
-                    for (int s2 = 0; s2 < kNetEnt; ++s2) {
-                        const bool live = s2 < nent;
-                        const double av = live ? a.l_val[es + s2] : 0.0;
-                        const int64_t cb = (lv[s2] - rbase) * (int64_t)nR;
-#pragma unroll
-                        for (int t = 0; t < kNetProd / kNetEnt; ++t) {
-                            const int p = s2 + kNetEnt * t;
-                            nk[p] = kNone;
-                            if (live && t < pre[s2 + 1] - pre[s2]) {
-                                const int64_t b = b0[s2] + t;
-                                nk[p] = ((KeyT)(a.r_liv[b] - cb) << 4) | (KeyT)(pre[s2] + t);
-                                S.nval[pre[s2] + t][lane] = av * a.r_val[b];
-                            }
-                        }
-                    }
+                // rows whose R rows are short gather straight into register
+                // slots: with at most E entries of at most kNetProd / E
+                // products each, entry s2's t-th product takes slot s2 + E t
+                // (the sort ignores positions; the key carries the generation
+                // index) and its column is its LIV minus the R row's base
+                if (mx <= kNetProd / 8) {
+                    net_gather_direct<8, KeyT>(a, es, nent, rbase, lv, b0, pre, nk, S.nval, lane);
+                } else if (nent <= 4 && mx <= kNetProd / 4) {
+                    net_gather_direct<4, KeyT>(a, es, nent, rbase, lv, b0, pre, nk, S.nval, lane);
+                } else if (nent <= 2 && mx <= kNetProd / 2) {
+                    net_gather_direct<2, KeyT>(a, es, nent, rbase, lv, b0, pre, nk, S.nval, lane);
                 } else {
 #pragma unroll
                 for (int q = 0; q < kNetProd; ++q) {
@@ -1321,15 +1338,23 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
             // coalesced copy of the staged outputs: entry i belongs to the
             // lane whose staged range holds it (binary search over 32 starts)
             const int ns = S.stage.soff[32];
-            for (int i = lane; i < ns; i += 32) {
-                int lo = 0, hi = 32;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (S.stage.soff[mid] <= i) lo = mid; else hi = mid;
+            if (__all_sync(kFull, kind == kRowNet || kind == kRowNone)) {
+                // every row of the tile was staged: staged order is C order
+                for (int i = lane; i < ns; i += 32) {
+                    a.c_liv[goff + i] = S.stage.liv[i];
+                    a.c_val[goff + i] = S.stage.val[i];
                 }
-                const int64_t g = goff + S.stage.doff[lo] + (i - S.stage.soff[lo]);
-                a.c_liv[g] = S.stage.liv[i];
-                a.c_val[g] = S.stage.val[i];
+            } else {
+                for (int i = lane; i < ns; i += 32) {
+                    int lo = 0, hi = 32;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (S.stage.soff[mid] <= i) lo = mid; else hi = mid;
+                    }
+                    const int64_t g = goff + S.stage.doff[lo] + (i - S.stage.soff[lo]);
+                    a.c_liv[g] = S.stage.liv[i];
+                    a.c_val[g] = S.stage.val[i];
+                }
             }
         }
         if (kind == kRowLane) {
