@@ -855,6 +855,10 @@ struct RowsArgs {
     uint64_t *tile_state;
     uint32_t *tile_ctr;
     WsHeader *hdr;
+    // placement by scratch (large problems): c_liv / c_val are the scratch
+    // arrays, tile t's outputs start at tile_base[t] and number tile_cnt[t]
+    int64_t *tile_cnt;
+    int64_t *tile_base;
 };
 
 constexpr int kStage = 32 * 16;           // staged outputs of a tile's register-sorted rows
@@ -1099,7 +1103,12 @@ __device__ __forceinline__ void net_gather_direct(const RowsArgs &a, int64_t es,
     }
 }
 
-template <typename KeyT>
+// kScratch: each 32-row tile writes its outputs to scratch from the product
+// offset of its first row (a row has at most as many outputs as products),
+// with no ordering between tiles; k_compact then places the tiles in C.
+// Otherwise a CTA takes kWarps consecutive 32-row tiles at a time (one per
+// warp) and finds their place in C with one decoupled look-back.
+template <typename KeyT, bool kScratch>
 __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant__ RowsArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1112,14 +1121,27 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
         return;
     }
     constexpr KeyT kNone = (KeyT)~(KeyT)0;
+    constexpr int kWarps = kRowsThreads / 32;
+    __shared__ int64_t s_ctile, s_goff;
+    __shared__ int64_t s_wtot[kWarps];
     const int64_t nact = a.act_rows ? (int64_t)*a.nact : a.hdr->nrows_l;
     const int64_t ntiles = (nact + 31) / 32;
+    const int64_t nctiles = (nact + 32 * kWarps - 1) / (32 * kWarps);
     const uint64_t nR = (uint64_t)a.nR;
     for (;;) {
-        int64_t t = 0;
-        if (lane == 0) t = atomicAdd(a.tile_ctr, 1u);
-        t = __shfl_sync(kFull, t, 0);
-        if (t >= ntiles) break;
+        int64_t t = 0, ct = 0;
+        if constexpr (kScratch) {
+            int64_t tt = 0;
+            if (lane == 0) tt = atomicAdd(a.tile_ctr, 1u);
+            t = __shfl_sync(kFull, tt, 0);
+            if (t >= ntiles) break;
+        } else {
+            if (threadIdx.x == 0) s_ctile = atomicAdd(a.tile_ctr, 1u);
+            __syncthreads();
+            ct = s_ctile;
+            if (ct >= nctiles) break;
+            t = ct * kWarps + warp;
+        }
         const int64_t idx = t * 32 + lane;
         const int64_t r = idx < nact ? (a.act_rows ? a.act_rows[idx] : idx) : -1;
         int kind = kRowNone;
@@ -1325,12 +1347,34 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
             }
         }
         __syncwarp();
-        if (lane == 0) lb_store(a.tile_state + t, (t == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
         int64_t goff = 0;
-        if (t > 0) goff = (int64_t)lookback_warp(a.tile_state, t, &a.hdr->status);
-        if (lane == 0) {
-            if (t > 0) lb_store(a.tile_state + t, kFlagIncl | (uint64_t)(goff + tot));
-            if (t == ntiles - 1) a.hdr->nnz_c = goff + tot;
+        if constexpr (kScratch) {
+            // lane 0's row exists (t < ntiles): products before it
+            goff = __shfl_sync(kFull, pb, 0);
+            if (lane == 0) {
+                a.tile_cnt[t] = tot;
+                a.tile_base[t] = goff;
+            }
+        } else {
+            if (lane == 0) s_wtot[warp] = tot;
+            __syncthreads();
+            if (warp == 0) {
+                int64_t ctot = 0;
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) ctot += s_wtot[w];
+                if (lane == 0) lb_store(a.tile_state + ct, (ct == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)ctot);
+                int64_t cg = 0;
+                if (ct > 0) cg = (int64_t)lookback_warp(a.tile_state, ct, &a.hdr->status);
+                if (lane == 0) {
+                    if (ct > 0) lb_store(a.tile_state + ct, kFlagIncl | (uint64_t)(cg + ctot));
+                    if (ct == nctiles - 1) a.hdr->nnz_c = cg + ctot;
+                    s_goff = cg;
+                }
+            }
+            __syncthreads();
+            goff = s_goff;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) goff += w < warp ? s_wtot[w] : 0;
         }
         const int64_t obase = goff + off;
         const int64_t cbase = rid * a.nR;
@@ -1448,6 +1492,107 @@ __global__ void __launch_bounds__(256) k_copy_rows(const __grid_constant__ RowsA
                 }
             }
         }
+    }
+}
+
+// ------------------------------------------------------------------------
+// Placement of scratch-mode tiles: C receives tile t's outputs (scratch
+// [tile_base[t], + tile_cnt[t])) at the exclusive prefix of the counts.  The
+// counts are all known before this kernel, so its look-back never waits on
+// slow work.  A block is 32 tiles when there are many tiles per CTA, else 8
+// (more blocks to spread); a block's entries are spread over the CTA.
+// ------------------------------------------------------------------------
+constexpr int kCompactTiles = 32;   // largest block (tiles)
+constexpr int kCompactThreads = 256;
+constexpr int kCompactCtas = 6;      // resident per SM
+constexpr int kCompactUnroll = 4;
+
+struct CompactArgs {
+    const int64_t *s_liv;
+    const double *s_val;
+    const int64_t *tile_cnt;
+    const int64_t *tile_base;
+    const int64_t *act_rows;
+    const unsigned long long *nact;
+    int64_t *c_liv;
+    double *c_val;
+    int64_t cap;
+    uint64_t *state;
+    uint32_t *ctr;
+    WsHeader *hdr;
+};
+
+__global__ void __launch_bounds__(kCompactThreads, kCompactCtas) k_compact(const __grid_constant__ CompactArgs a) {
+    __shared__ int64_t s_blk, s_goff;
+    __shared__ int64_t s_pre[kCompactTiles + 1];
+    __shared__ int64_t s_src[kCompactTiles];
+    if (a.hdr->f > a.cap) return;
+    const int64_t nact = a.act_rows ? (int64_t)*a.nact : a.hdr->nrows_l;
+    const int64_t ntiles = (nact + 31) / 32;
+    const bool wide = ntiles >= 64 * (int64_t)gridDim.x;
+    const int tpb = wide ? 32 : 8, steps = wide ? 5 : 3;
+    const int64_t nblk = (ntiles + tpb - 1) / tpb;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (;;) {
+        if (tid == 0) s_blk = atomicAdd(a.ctr, 1u);
+        __syncthreads();
+        const int64_t b = s_blk;
+        if (b >= nblk) break;
+        if (tid < 32) {
+            const int64_t t = b * tpb + lane;
+            const bool mine = lane < tpb && t < ntiles;
+            const int64_t c = mine ? a.tile_cnt[t] : 0;
+            s_src[lane] = mine ? a.tile_base[t] : 0;
+            int64_t x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t u = __shfl_up_sync(kFull, x, o);
+                if (lane >= o) x += u;
+            }
+            const int64_t tot = __shfl_sync(kFull, x, 31);
+            s_pre[lane] = x - c;
+            if (lane == 31) s_pre[kCompactTiles] = tot;
+            if (lane == 0) lb_store(a.state + b, (b == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
+            int64_t g = 0;
+            if (b > 0) g = (int64_t)lookback_warp(a.state, b, &a.hdr->status);
+            if (lane == 0) {
+                if (b > 0) lb_store(a.state + b, kFlagIncl | (uint64_t)(g + tot));
+                if (b == nblk - 1) a.hdr->nnz_c = g + tot;
+                s_goff = g;
+            }
+        }
+        __syncthreads();
+        const int64_t n = s_pre[tpb], g = s_goff;
+        // kCompactUnroll entries per thread per step, all loads issued first
+        for (int64_t i0 = tid; i0 < n; i0 += kCompactThreads * kCompactUnroll) {
+            int64_t src[kCompactUnroll];
+#pragma unroll
+            for (int u = 0; u < kCompactUnroll; ++u) {
+                const int64_t i = i0 + kCompactThreads * u;
+                // the tile holding entry i: the last one whose prefix is <= i
+                int lo = 0, hi = tpb;
+                for (int step = 0; step < steps; ++step) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_pre[mid] <= i) lo = mid; else hi = mid;
+                }
+                src[u] = i < n ? s_src[lo] + (i - s_pre[lo]) : -1;
+            }
+            int64_t lv[kCompactUnroll];
+            double vv[kCompactUnroll];
+#pragma unroll
+            for (int u = 0; u < kCompactUnroll; ++u) {
+                lv[u] = src[u] >= 0 ? a.s_liv[src[u]] : 0;
+                vv[u] = src[u] >= 0 ? a.s_val[src[u]] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kCompactUnroll; ++u) {
+                if (src[u] >= 0) {
+                    a.c_liv[g + i0 + kCompactThreads * u] = lv[u];
+                    a.c_val[g + i0 + kCompactThreads * u] = vv[u];
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -1632,7 +1777,8 @@ struct P2Layout {
     int64_t capc, nchunks_max;
     size_t chunk_state, chunk_ctr, reduce_state, table_state, zero_bytes;
     size_t act_rows;
-    size_t arr[6];          // cap-sized scratch arrays (8 bytes per entry; 4 used off SOP)
+    size_t arr[6];          // cap-sized scratch arrays (8 bytes per entry; 4 used off SOP, 6 with placement by scratch)
+    size_t tile_cnt, tile_base;   // placement by scratch: per 32-row tile
     size_t sop_radix;
     int sop_D, sop_P;
     size_t total;
@@ -1641,6 +1787,13 @@ struct P2Layout {
 P2Layout p2_layout(const lco_plan *p, int64_t cap);
 
 size_t contract_phase2_bytes(const lco_plan *p, int64_t cap) { return p2_layout(p, cap).total; }
+
+// Row kernels place their outputs through scratch (k_rows<., true> +
+// k_compact) when L has this many entries: with thousands of 32-row tiles in
+// flight, ordering them by look-back makes every tile wait for the slowest
+// of its predecessors.
+constexpr int64_t kScratchMinEntries = 1 << 16;
+bool rows_scratch(const lco_plan *p) { return p->acc != 2 && p->nnz_l >= kScratchMinEntries; }
 
 }  // namespace
 }  // namespace lco
@@ -2104,8 +2257,10 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         if (!(attr_done.load() & bit)) {
             cudaFuncSetAttribute(k_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(HeavySmem));
             const int rows_smem = (int)sizeof(RowsSmem) * (kRowsThreads / 32);
-            cudaFuncSetAttribute(k_rows<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem);
-            cudaFuncSetAttribute(k_rows<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem);
+            cudaFuncSetAttribute(k_rows<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem);
+            cudaFuncSetAttribute(k_rows<uint64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem);
+            cudaFuncSetAttribute(k_rows<uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem);
+            cudaFuncSetAttribute(k_rows<uint64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem);
             attr_done.fetch_or(bit);
         }
         LCO_LAUNCH("k_heavy", s, k_heavy<<<(unsigned)sms, kCT, sizeof(HeavySmem), s>>>(ha));
@@ -2138,15 +2293,50 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         ra.tile_state = chunk_state;
         ra.tile_ctr = chunk_ctr;
         ra.hdr = hdr;
+        const bool scratch = rows_scratch(p);
+        if (scratch) {
+            ra.c_liv = reinterpret_cast<int64_t *>(p2 + L.arr[4]);
+            ra.c_val = reinterpret_cast<double *>(p2 + L.arr[5]);
+            ra.tile_cnt = reinterpret_cast<int64_t *>(p2 + L.tile_cnt);
+            ra.tile_base = reinterpret_cast<int64_t *>(p2 + L.tile_base);
+        }
         const int warps = kRowsThreads / 32;
         int64_t grid = (nchunks_max + warps - 1) / warps;
         if (grid > (int64_t)sms * 16) grid = (int64_t)sms * 16;
-        if (p->nR <= (int64_t)0xfffffffell) {
-            LCO_LAUNCH("k_rows", s, k_rows<uint32_t><<<(unsigned)grid, kRowsThreads, sizeof(RowsSmem) * warps, s>>>(ra));
+        const size_t rows_smem = sizeof(RowsSmem) * warps;
+        const bool narrow = p->nR <= (int64_t)0xfffffffell;
+        if (scratch) {
+            if (narrow) {
+                LCO_LAUNCH("k_rows", s, k_rows<uint32_t, true><<<(unsigned)grid, kRowsThreads, rows_smem, s>>>(ra));
+            } else {
+                LCO_LAUNCH("k_rows", s, k_rows<uint64_t, true><<<(unsigned)grid, kRowsThreads, rows_smem, s>>>(ra));
+            }
         } else {
-            LCO_LAUNCH("k_rows", s, k_rows<uint64_t><<<(unsigned)grid, kRowsThreads, sizeof(RowsSmem) * warps, s>>>(ra));
+            if (narrow) {
+                LCO_LAUNCH("k_rows", s, k_rows<uint32_t, false><<<(unsigned)grid, kRowsThreads, rows_smem, s>>>(ra));
+            } else {
+                LCO_LAUNCH("k_rows", s, k_rows<uint64_t, false><<<(unsigned)grid, kRowsThreads, rows_smem, s>>>(ra));
+            }
         }
         LCO_LAUNCH("k_copy_rows", s, k_copy_rows<<<(unsigned)(sms * 2), 256, 0, s>>>(ra));
+        if (scratch) {
+            CompactArgs ca{};
+            ca.s_liv = ra.c_liv;
+            ca.s_val = ra.c_val;
+            ca.tile_cnt = ra.tile_cnt;
+            ca.tile_base = ra.tile_base;
+            ca.act_rows = ra.act_rows;
+            ca.nact = nact;
+            ca.c_liv = c_liv;
+            ca.c_val = c_val;
+            ca.cap = cap;
+            ca.state = chunk_state;
+            ca.ctr = chunk_ctr + 12;
+            ca.hdr = hdr;
+            const int64_t nblk = (nchunks_max + 7) / 8;
+            int64_t cgrid = nblk < (int64_t)sms * kCompactCtas ? nblk : (int64_t)sms * kCompactCtas;
+            LCO_LAUNCH("k_compact", s, k_compact<<<(unsigned)(cgrid > 0 ? cgrid : 1), kCompactThreads, 0, s>>>(ca));
+        }
     } else {
         SopArgs sa{};
         sa.l_liv = o.l_liv;
@@ -2209,7 +2399,8 @@ P2Layout p2_layout(const lco_plan *p, int64_t cap) {
     size_t off = 0;
     L.chunk_state = off;
     // counters: [0] row tiles, [1] reduce tiles, [2] heavy rows, [4..5] heavy
-    // count, [6..7] long copies, [8] row-table tiles, [10..11] active rows
+    // count, [6..7] long copies, [8] row-table tiles, [10..11] active rows,
+    // [12] compaction blocks
     L.chunk_ctr = (size_t)L.nchunks_max * 8;
     off += align_up((size_t)L.nchunks_max * 8 + 64);
     L.reduce_state = off;
@@ -2221,11 +2412,16 @@ P2Layout p2_layout(const lco_plan *p, int64_t cap) {
     off += align_up((size_t)(p->nnz_l > 0 ? p->nnz_l : 1) * 8);
     // SOP: products, sorted products and the radix tmp buffer (6 arrays);
     // row kernels: heavy-row scratch and its ping-pong buffer (4 arrays)
-    const int narr = p->acc == 2 ? 6 : 4;
+    const bool scratch = rows_scratch(p);
+    const int narr = (p->acc == 2 || scratch) ? 6 : 4;
     for (int i = 0; i < 6; ++i) {
         L.arr[i] = off;
         if (i < narr) off += align_up((size_t)L.capc * 8);
     }
+    L.tile_cnt = off;
+    if (scratch) off += align_up((size_t)L.nchunks_max * 8);
+    L.tile_base = off;
+    if (scratch) off += align_up((size_t)L.nchunks_max * 8);
     L.sop_radix = off;
     radix_digits(p->sop_bits, &L.sop_D, &L.sop_P);
     if (p->acc == 2) off += radix_state_bytes(L.capc, L.sop_D, L.sop_P);

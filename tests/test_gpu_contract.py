@@ -213,6 +213,23 @@ def test_row_kinds_in_one_product(alg):
     assert_contract_matches(C, A, B, [1], [0])
 
 
+def test_row_kinds_placed_through_scratch():
+    """With more than 65,536 entries in L the row kernel writes each 32-row
+    tile at the product offset of its first row and a compaction pass places
+    the tiles: every row kind mixed, checked against the oracle and bit for
+    bit against SOP (which has no row tiles)."""
+    spec = ([(5, 3)] * 40 + [(12, 3)] * 10 + [(20, 15)] * 3 + [(1, 1)] * 30 +
+            [(40, 40)] * 2 + [(3, 2)] * 20 + [(30, 120)] + [(6, 2)] * 50 + [(1, 400)] * 2) * 80
+    A, B = _matrix_pair(spec, n_cols_r=3000, seed=53)
+    assert len(A["liv"]) > 65536
+    ref, _ = _run(A, B, [1], [0], "SOP")
+    assert_contract_matches(ref, A, B, [1], [0])
+    for alg in ("CSR", "CSRNA", "DCSR"):
+        C, _ = _run(A, B, [1], [0], alg)
+        assert torch.equal(C.liv, ref.liv), alg
+        assert torch.equal(C.val.view(torch.int64), ref.val.view(torch.int64)), alg
+
+
 def test_plan_reuse_gives_identical_results():
     """Running the same plan twice (as the benchmark does) reproduces C bit-for-bit."""
     cfg = synth.config_fd3d(n=24, seed=2)
