@@ -10,6 +10,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kUpItems = 8;   // histogram kernels: loads in flight per thread
 constexpr int kOffItems = 16; // offsets kernel: ranges per lane (G <= 512)
+constexpr int kScatterCtas = 4; // scatter CTAs resident per SM (9-bit digits)
 
 // In-place exclusive scan of n (<= 256 * 8) 32-bit values held in shared
 // memory, by a block of kRadixThreads threads.  Returns the total.
@@ -282,27 +283,44 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_offsets(const __grid_co
     }
 }
 
+// Staging buffer and digit tables of a scatter CTA, rounded up to 128 bytes
+// (the bulk form's input buffers follow: copy destinations must be aligned).
+__host__ __device__ constexpr size_t scatter_smem_bytes_base(int D) {
+    return ((size_t)kRadixTile * 16 + ((size_t)1 << D) * 16 + ((size_t)1 << D) * 4 +
+            (size_t)kRadixWarps * ((size_t)1 << D) * 2 + 127) & ~(size_t)127;
+}
+
 // ---------------------------------------------------------------------------
 // One stable scatter pass: CTA r walks range r tile by tile (kRadixTile
-// elements), ranking each tile with warp ballots and placing it from running
-// per-digit offsets; the tile is staged in shared memory so that the writes
-// of each digit's run are contiguous.
+// elements), ranking each tile with warp match instructions and placing it
+// from running per-digit offsets; the tile is staged in shared memory so
+// that the writes of each digit's run are contiguous.  Digit tables use
+// 16-bit warp counts and digits are recomputed at write-out, to keep shared
+// memory small.  Two forms:
+//   kBulk: the next input tile comes in by bulk copy while the current one
+//     is ranked (double-buffered input, two CTAs per SM) -- for ranges of
+//     many tiles;
+//   otherwise: tiles are loaded directly and only the staging buffer and
+//     the digit tables are in shared memory, so four CTAs fit on an SM and
+//     their tiles fill each other's barrier gaps -- for ranges of few tiles.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(const __grid_constant__ RadixJob j, int pass) {
+template <bool kBulk>
+__global__ void __launch_bounds__(kRadixThreads, kBulk ? 2 : kScatterCtas)
+    k_radix_scatter(const __grid_constant__ RadixJob j, int pass) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const PassIO io = pass_io(j, pass);
     if (!io.run) return;
     const int NB = 1 << j.D;
     int64_t *s_key = reinterpret_cast<int64_t *>(smem_raw);
     double *s_val = reinterpret_cast<double *>(s_key + kRadixTile);
-    int64_t *in_key = reinterpret_cast<int64_t *>(s_val + kRadixTile);   // bulk-copied input tile
+    int64_t *s_run = reinterpret_cast<int64_t *>(s_val + kRadixTile);
+    int64_t *s_gbase = s_run + NB;
+    uint32_t *s_tstart = reinterpret_cast<uint32_t *>(s_gbase + NB);
+    uint16_t *s_whist = reinterpret_cast<uint16_t *>(s_tstart + NB);
+    // bulk form only: the input buffers and their barrier, after the tables
+    int64_t *in_key = reinterpret_cast<int64_t *>(smem_raw + scatter_smem_bytes_base(j.D));
     double *in_val = reinterpret_cast<double *>(in_key + kRadixTile);
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(in_val + kRadixTile);
-    int64_t *s_run = reinterpret_cast<int64_t *>(s_bar + 2);
-    int64_t *s_gbase = s_run + NB;
-    uint32_t *s_whist = reinterpret_cast<uint32_t *>(s_gbase + NB);
-    uint32_t *s_tstart = s_whist + kRadixWarps * NB;
-    uint16_t *s_dig = reinterpret_cast<uint16_t *>(s_tstart + NB);
 
     const int64_t n = job_n(j);
     int64_t lo, hi;
@@ -319,11 +337,11 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(const __grid
     const int shift = pass * j.D;
     for (int d = tid; d < NB; d += kRadixThreads) s_run[d] = (int64_t)j.roffs[(int64_t)blockIdx.x * NB + d];
     const unsigned lt = lanemask_lt();
-    uint32_t *wh = s_whist + warp * NB;
-    // Input tiles come in by bulk copy, the next one while the current one is
-    // ranked and scattered, when both input arrays are 16-byte aligned (tile
-    // starts are even element offsets).  An odd last element is read directly.
-    const bool bulk = ((reinterpret_cast<uintptr_t>(io.sl) | reinterpret_cast<uintptr_t>(io.sv)) & 15) == 0;
+    uint16_t *wh = s_whist + warp * NB;
+    // bulk form: the next tile is copied in while the current one is ranked
+    // and scattered, when both input arrays are 16-byte aligned (tile starts
+    // are even element offsets); an odd last element is read directly
+    const bool bulk = kBulk && ((reinterpret_cast<uintptr_t>(io.sl) | reinterpret_cast<uintptr_t>(io.sv)) & 15) == 0;
     uint32_t parity = 0;
     auto issue = [&](int64_t base) {
         const int64_t m = (hi - base < (int64_t)kRadixTile ? hi - base : (int64_t)kRadixTile) & ~(int64_t)1;
@@ -345,7 +363,7 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(const __grid
     for (int64_t tile_base = lo; tile_base < hi; tile_base += kRadixTile) {
         const int tile_n = (int)((hi - tile_base) < (int64_t)kRadixTile ? (hi - tile_base) : (int64_t)kRadixTile);
         const int64_t bulk_end = bulk ? tile_base + (tile_n & ~1) : tile_base;
-        for (int i = tid; i < kRadixWarps * NB; i += kRadixThreads) s_whist[i] = 0;
+        for (int i = tid; i < kRadixWarps * NB / 2; i += kRadixThreads) reinterpret_cast<uint32_t *>(s_whist)[i] = 0;
         if (bulk && bulk_end > tile_base) {
             const bool ok = mbar_wait_bounded(s_bar, parity);
             parity ^= 1u;
@@ -361,23 +379,21 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(const __grid
 #pragma unroll
         for (int i = 0; i < kRadixItems; ++i) {
             const int64_t e = wbase + i * 32 + lane;
-            if (e < hi) {
-                int64_t k;
-                if (e < bulk_end) {
-                    k = in_key[e - tile_base];
-                    vals[i] = in_val[e - tile_base];
-                } else {
-                    k = io.sl[e];
-                    vals[i] = io.sv[e];
-                }
-                if (io.first) k = relin(j.relin, k);
-                keys[i] = k;
-                digs[i] = (uint32_t)((divu(j.key_div, (uint64_t)k) >> shift) & mask);
-            } else {
-                keys[i] = 0;
-                vals[i] = 0.0;
-                digs[i] = 0;
+            keys[i] = 0;
+            vals[i] = 0.0;
+            if (e < bulk_end) {
+                keys[i] = in_key[e - tile_base];
+                vals[i] = in_val[e - tile_base];
+            } else if (e < hi) {
+                keys[i] = __ldg(io.sl + e);
+                vals[i] = __ldg(io.sv + e);
             }
+        }
+#pragma unroll
+        for (int i = 0; i < kRadixItems; ++i) {
+            const int64_t e = wbase + i * 32 + lane;
+            if (io.first && e < hi) keys[i] = relin(j.relin, keys[i]);
+            digs[i] = e < hi ? (uint32_t)((divu(j.key_div, (uint64_t)keys[i]) >> shift) & mask) : 0u;
         }
         __syncthreads();
         // the input buffer is free: fetch the next tile behind this one's work
@@ -396,7 +412,7 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(const __grid
             uint32_t basev = 0;
             if (valid && lane == leader) {
                 basev = wh[d];
-                wh[d] = basev + (uint32_t)__popc(peers);
+                wh[d] = (uint16_t)(basev + (uint32_t)__popc(peers));
             }
             basev = __shfl_sync(kFull, basev, leader);
             digs[i] = d | ((basev + (uint32_t)__popc(peers & lt)) << 16);
@@ -408,7 +424,7 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(const __grid
             uint32_t run = 0;
             for (int w = 0; w < kRadixWarps; ++w) {
                 const uint32_t c = s_whist[w * NB + d];
-                s_whist[w * NB + d] = run;
+                s_whist[w * NB + d] = (uint16_t)run;
                 run += c;
             }
             s_tstart[d] = run;
@@ -431,24 +447,22 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(const __grid
                 const uint32_t lp = s_tstart[d] + wh[d] + (digs[i] >> 16);
                 s_key[lp] = keys[i];
                 s_val[lp] = vals[i];
-                s_dig[lp] = (uint16_t)d;
             }
         }
         __syncthreads();
         for (int i = tid; i < tile_n; i += kRadixThreads) {
-            const uint32_t d = s_dig[i];
+            const int64_t k = s_key[i];
+            const uint32_t d = (uint32_t)((divu(j.key_div, (uint64_t)k) >> shift) & mask);
             const int64_t g = s_gbase[d] + i;
-            io.dl[g] = s_key[i];
+            io.dl[g] = k;
             io.dv[g] = s_val[i];
         }
         __syncthreads();
     }
 }
 
-size_t scatter_smem_bytes(int D) {
-    size_t NB = (size_t)1 << D;
-    return (size_t)kRadixTile * 16 * 2 + 16 + NB * 16 + (size_t)kRadixWarps * NB * 4 + NB * 4 +
-           (size_t)kRadixTile * 2;
+size_t scatter_smem_bytes(int D, bool bulk) {
+    return scatter_smem_bytes_base(D) + (bulk ? (size_t)kRadixTile * 16 + 16 : 0);
 }
 
 size_t upsweep_smem_bytes(int D, int P) {
@@ -475,10 +489,21 @@ int radix_sm_count() {
 // the histogram table zeroed, and a zero-filled region starts that way.
 constexpr size_t kHistTableBytes = (size_t)kMaxPasses * ((size_t)1 << kMaxDigitBits) * 8;
 
+// Up to kBulkMinTiles tiles per CTA of a four-per-SM wave, the direct
+// scatter runs (at least two tiles per range); beyond, the bulk-copy form
+// (two CTAs per SM, at least four tiles per range).
+constexpr int64_t kBulkMinTiles = 4;
+
+bool radix_bulk(int64_t n_cap) {
+    const int64_t tiles = (n_cap + kRadixTile - 1) / kRadixTile;
+    return tiles > kBulkMinTiles * kScatterCtas * (int64_t)radix_sm_count();
+}
+
 int radix_ranges(int64_t n_cap) {
     const int64_t tiles = (n_cap + kRadixTile - 1) / kRadixTile;
-    int64_t g = (tiles + 3) / 4;                 // at least four tiles per range
-    int64_t gmax = 2 * (int64_t)radix_sm_count();  // two scatter CTAs per SM (9-bit digits)
+    const bool bulk = radix_bulk(n_cap);
+    int64_t g = bulk ? (tiles + 3) / 4 : (tiles + 1) / 2;
+    int64_t gmax = (bulk ? 2 : kScatterCtas) * (int64_t)radix_sm_count();   // one wave of scatter CTAs
     if (gmax > 32 * kOffItems) gmax = 32 * kOffItems;
     if (g > gmax) g = gmax;
     if (g < 1) g = 1;
@@ -520,8 +545,10 @@ cudaError_t radix_enqueue(const RadixJob &job, cudaStream_t stream) {
     cudaGetDevice(&dev);
     const uint64_t bit = 1ull << (dev & 63);
     if (!(attr_done.load() & bit)) {
-        cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)scatter_smem_bytes(kMaxDigitBits));
+        cudaFuncSetAttribute(k_radix_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scatter_smem_bytes(kMaxDigitBits, true));
+        cudaFuncSetAttribute(k_radix_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scatter_smem_bytes(kMaxDigitBits, false));
         cudaFuncSetAttribute(k_radix_upsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)upsweep_smem_bytes(kMaxDigitBits, kMaxPasses));
         attr_done.fetch_or(bit);
@@ -540,8 +567,13 @@ cudaError_t radix_enqueue(const RadixJob &job, cudaStream_t stream) {
         }
         LCO_LAUNCH("k_radix_offsets", stream,
                    k_radix_offsets<<<(unsigned)((NB + kRadixWarps - 1) / kRadixWarps), kRadixThreads, 0, stream>>>(job, p));
-        LCO_LAUNCH("k_radix_scatter", stream,
-                   k_radix_scatter<<<G, kRadixThreads, scatter_smem_bytes(job.D), stream>>>(job, p));
+        if (radix_bulk(job.n_cap)) {
+            LCO_LAUNCH("k_radix_scatter", stream,
+                       k_radix_scatter<true><<<G, kRadixThreads, scatter_smem_bytes(job.D, true), stream>>>(job, p));
+        } else {
+            LCO_LAUNCH("k_radix_scatter", stream,
+                       k_radix_scatter<false><<<G, kRadixThreads, scatter_smem_bytes(job.D, false), stream>>>(job, p));
+        }
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
     }
