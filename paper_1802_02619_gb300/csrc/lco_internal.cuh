@@ -79,10 +79,24 @@ struct RelinParams {
     int32_t identity;
     DivU64 seg_div[kMaxOrder];
     int64_t seg_stride[kMaxOrder];
+    // every segment range and stride a power of two (every dimension is):
+    // a segment is a bit field, moved by masks and shifts
+    int32_t all_pow2;
+    uint32_t stride_shift[kMaxOrder];
 };
 
 __host__ __device__ __forceinline__ int64_t relin(const RelinParams &p, int64_t liv) {
     if (p.identity) return liv;
+    if (p.all_pow2) {
+        uint64_t r = (uint64_t)liv, out = 0;
+#pragma unroll 1
+        for (int t = 0; t < p.nseg - 1; ++t) {
+            const uint32_t w = p.seg_div[t].shift;
+            out |= (r & ((1ull << w) - 1)) << p.stride_shift[t];
+            r >>= w;
+        }
+        return (int64_t)(out | (r << p.stride_shift[p.nseg - 1]));
+    }
     uint64_t r = (uint64_t)liv;
     int64_t out = 0;
 #pragma unroll 1

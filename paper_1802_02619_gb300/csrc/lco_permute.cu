@@ -63,6 +63,12 @@ RelinParams make_relin(int32_t order, const int64_t *dims, const int32_t *sig_ol
     }
     r.seg_div[nseg - 1] = make_div(range);
     r.nseg = nseg;
+    r.all_pow2 = 1;
+    for (int t = 0; t < nseg; ++t) {
+        const uint64_t st = (uint64_t)r.seg_stride[t];
+        if (!r.seg_div[t].pow2 || (st & (st - 1)) != 0) r.all_pow2 = 0;
+        r.stride_shift[t] = st ? (uint32_t)__builtin_ctzll(st) : 0;
+    }
     return r;
 }
 
