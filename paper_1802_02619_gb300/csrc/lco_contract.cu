@@ -399,14 +399,20 @@ struct ScanArgs {
     WsHeader *hdr;
 };
 
-__global__ void __launch_bounds__(kCT) k_work_scan(const __grid_constant__ ScanArgs a) {
+// Item i of thread t keeps its work and row id in shared memory at
+// i * kCT + t (conflict-free), not in registers.  With CSR lookups (two
+// loads) six CTAs then fit on an SM, so that more tiles are in flight at
+// once and fewer wait on their look-backs; DCSR lookups (a search per item)
+// keep the registers that let the items' searches overlap.
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kCT, kMinBlocks) k_work_scan(const __grid_constant__ ScanArgs a) {
     __shared__ int64_t s_tmp[kCW + 1];
     __shared__ int64_t s_tile, s_ew, s_eh;
+    __shared__ int64_t s_w[kScanTile], s_rows[kScanTile];
     if (threadIdx.x == 0) s_tile = atomicAdd(&a.hdr->counters[kCtrScan], 1u);
     __syncthreads();
     const int64_t tile = s_tile;
     const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    int64_t w[kScanItems], rows[kScanItems];
     int64_t wsum = 0, hsum = 0;
     uint32_t heads = 0;
     int64_t prev = -1;
@@ -414,8 +420,7 @@ __global__ void __launch_bounds__(kCT) k_work_scan(const __grid_constant__ ScanA
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         const int64_t e = base + i;
-        w[i] = 0;
-        rows[i] = -1;
+        int64_t wi = 0, ri = -1;
         if (e < a.nnz_l) {
             const uint64_t liv = (uint64_t)a.l_liv[e];
             const uint64_t row = divu(a.div_k, liv);
@@ -423,12 +428,14 @@ __global__ void __launch_bounds__(kCT) k_work_scan(const __grid_constant__ ScanA
             int64_t b0, len;
             mdt_lookup(a.mdt, c, b0, len);
             if (a.ec) a.ec[e] = ec_pack(b0, len);
-            w[i] = 1 + len;
-            rows[i] = (int64_t)row;
+            wi = 1 + len;
+            ri = (int64_t)row;
             if ((int64_t)row != prev) heads |= 1u << i;
             prev = (int64_t)row;
         }
-        wsum += w[i];
+        s_w[i * kCT + threadIdx.x] = wi;
+        s_rows[i * kCT + threadIdx.x] = ri;
+        wsum += wi;
     }
     hsum = __popc(heads);
     int64_t wtot, htot;
@@ -473,12 +480,12 @@ __global__ void __launch_bounds__(kCT) k_work_scan(const __grid_constant__ ScanA
             if (a.P) a.P[e] = run;
             if (heads & (1u << i)) {
                 a.row_start[h] = e;
-                a.row_id[h] = rows[i];
+                a.row_id[h] = s_rows[i * kCT + threadIdx.x];
                 a.row_work[h] = run;
                 ++h;
             }
         }
-        run += w[i];
+        run += s_w[i * kCT + threadIdx.x];
     }
 }
 
@@ -2159,7 +2166,11 @@ int32_t symbolic_enqueue(const lco_plan *p, const int64_t *a_liv, const double *
     sa.state_h = scan_state + ((p->nnz_l + kScanTile - 1) / kScanTile) + 1;
     sa.hdr = hdr;
     const int64_t tiles = (p->nnz_l + kScanTile - 1) / kScanTile;
-    LCO_LAUNCH("k_work_scan", s, k_work_scan<<<(unsigned)tiles, kCT, 0, s>>>(sa));
+    if (p->lookup == kLookupCsr) {
+        LCO_LAUNCH("k_work_scan", s, k_work_scan<6><<<(unsigned)tiles, kCT, 0, s>>>(sa));
+    } else {
+        LCO_LAUNCH("k_work_scan", s, k_work_scan<1><<<(unsigned)tiles, kCT, 0, s>>>(sa));
+    }
     return cudaGetLastError() == cudaSuccess ? LCO_OK : LCO_ERR_CUDA;
 }
 

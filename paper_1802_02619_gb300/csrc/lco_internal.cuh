@@ -185,7 +185,7 @@ __device__ __forceinline__ uint64_t lookback(const uint64_t *state, int64_t tile
 // kLookbackBlocks predecessor words at once; the nearest inclusive word ends
 // the walk.  A word that is needed but not yet published is re-read (bounded
 // wait).  Positions before tile 0 count as an inclusive prefix of zero.
-constexpr int kLookbackBlocks = 4;
+constexpr int kLookbackBlocks = 1;
 
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 #pragma unroll
