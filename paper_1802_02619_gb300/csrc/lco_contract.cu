@@ -376,6 +376,24 @@ __global__ void __launch_bounds__(256) k_dcsr_aux(const int64_t *row_id, const W
 }
 
 // ------------------------------------------------------------------------
+// Phase 1 (DCSR R): every L entry's R row, found by searching R's row ids,
+// into the entry cache -- one entry per thread, so that the searches (chains
+// of dependent loads) of many entries overlap; the ordered scan below then
+// reads the cache.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_entry_lookup(const int64_t *l_liv, int64_t nnz_l, DivU64 div_k, int64_t k,
+                                                      DivU64 div_h, const __grid_constant__ Mdt mdt, uint64_t *ec) {
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < nnz_l; e += (int64_t)gridDim.x * 256) {
+        const uint64_t liv = (uint64_t)l_liv[e];
+        const uint64_t row = divu(div_k, liv);
+        const int64_t c = r_row(div_h, k, row, (int64_t)(liv - row * (uint64_t)k));
+        int64_t b0, len;
+        mdt_lookup(mdt, c, b0, len);
+        ec[e] = ec_pack(b0, len);
+    }
+}
+
+// ------------------------------------------------------------------------
 // Phase 1: work scan over L entries.  An entry costs 1 + |R row of its
 // column| work units.  The scan produces the row table of L (first entry,
 // row id, work offset of every non-empty row) and, for SOP, the per-entry
@@ -388,9 +406,8 @@ struct ScanArgs {
     DivU64 div_k;
     int64_t k;
     DivU64 div_h;          // L rows per value of the entrywise indices
-    Mdt mdt;
+    Mdt mdt;               // with the entry cache (DCSR) already filled
     int64_t *P;            // [nnz_l + 1] or null
-    uint64_t *ec;          // [nnz_l] entry cache (DCSR) or null
     int64_t *row_start;    // [nrows + 1]
     int64_t *row_id;       // [nrows]
     int64_t *row_work;     // [nrows + 1]
@@ -400,12 +417,10 @@ struct ScanArgs {
 };
 
 // Item i of thread t keeps its work and row id in shared memory at
-// i * kCT + t (conflict-free), not in registers.  With CSR lookups (two
-// loads) six CTAs then fit on an SM, so that more tiles are in flight at
-// once and fewer wait on their look-backs; DCSR lookups (a search per item)
-// keep the registers that let the items' searches overlap.
-template <int kMinBlocks>
-__global__ void __launch_bounds__(kCT, kMinBlocks) k_work_scan(const __grid_constant__ ScanArgs a) {
+// i * kCT + t (conflict-free), not in registers: six CTAs fit on an SM, so
+// that more tiles are in flight at once and fewer wait on their look-backs.
+// The lookups are two loads (CSR R) or read from the entry cache (DCSR R).
+__global__ void __launch_bounds__(kCT, 6) k_work_scan(const __grid_constant__ ScanArgs a) {
     __shared__ int64_t s_tmp[kCW + 1];
     __shared__ int64_t s_tile, s_ew, s_eh;
     __shared__ int64_t s_w[kScanTile], s_rows[kScanTile];
@@ -426,8 +441,7 @@ __global__ void __launch_bounds__(kCT, kMinBlocks) k_work_scan(const __grid_cons
             const uint64_t row = divu(a.div_k, liv);
             const int64_t c = r_row(a.div_h, a.k, row, (int64_t)(liv - row * (uint64_t)a.k));
             int64_t b0, len;
-            mdt_lookup(a.mdt, c, b0, len);
-            if (a.ec) a.ec[e] = ec_pack(b0, len);
+            mdt_lookup_entry(a.mdt, e, c, b0, len);
             wi = 1 + len;
             ri = (int64_t)row;
             if ((int64_t)row != prev) heads |= 1u << i;
@@ -2156,9 +2170,16 @@ int32_t symbolic_enqueue(const lco_plan *p, const int64_t *a_liv, const double *
     sa.k = p->k;
     sa.div_h = make_div((uint64_t)p->rows_h);
     sa.mdt = mdt;
-    sa.mdt.ec = nullptr;   // written by this scan
     sa.P = p->acc == 2 ? reinterpret_cast<int64_t *>(ws + p->off_P) : nullptr;
-    sa.ec = p->lookup == kLookupDcsr ? reinterpret_cast<uint64_t *>(ws + p->off_ec) : nullptr;
+    if (p->lookup == kLookupDcsr) {
+        Mdt m0 = mdt;
+        m0.ec = nullptr;
+        int64_t grid = (p->nnz_l + 255) / 256;
+        if (grid > (int64_t)sms * 16) grid = (int64_t)sms * 16;
+        LCO_LAUNCH("k_entry_lookup", s, k_entry_lookup<<<(unsigned)grid, 256, 0, s>>>(
+                                            o.l_liv, p->nnz_l, sa.div_k, p->k, sa.div_h, m0,
+                                            reinterpret_cast<uint64_t *>(ws + p->off_ec)));
+    }
     sa.row_start = reinterpret_cast<int64_t *>(ws + p->off_row_start);
     sa.row_id = reinterpret_cast<int64_t *>(ws + p->off_row_id);
     sa.row_work = reinterpret_cast<int64_t *>(ws + p->off_row_work);
@@ -2166,11 +2187,7 @@ int32_t symbolic_enqueue(const lco_plan *p, const int64_t *a_liv, const double *
     sa.state_h = scan_state + ((p->nnz_l + kScanTile - 1) / kScanTile) + 1;
     sa.hdr = hdr;
     const int64_t tiles = (p->nnz_l + kScanTile - 1) / kScanTile;
-    if (p->lookup == kLookupCsr) {
-        LCO_LAUNCH("k_work_scan", s, k_work_scan<6><<<(unsigned)tiles, kCT, 0, s>>>(sa));
-    } else {
-        LCO_LAUNCH("k_work_scan", s, k_work_scan<1><<<(unsigned)tiles, kCT, 0, s>>>(sa));
-    }
+    LCO_LAUNCH("k_work_scan", s, k_work_scan<<<(unsigned)tiles, kCT, 0, s>>>(sa));
     return cudaGetLastError() == cudaSuccess ? LCO_OK : LCO_ERR_CUDA;
 }
 
