@@ -880,7 +880,16 @@ struct RowsArgs {
     // arrays, tile t's outputs start at tile_base[t] and number tile_cnt[t]
     int64_t *tile_cnt;
     int64_t *tile_base;
+    unsigned long long *blk_tot;  // per kBlkTiles tiles: sum of their counts
+    unsigned long long *sup_tot;  // per kSupTiles tiles: sum of their counts
 };
+
+// Placement by scratch: the row kernel adds every tile's count into the
+// totals of its block and super-block, so that the compaction finds a
+// block's place by summing at most kSupTiles / kBlkTiles block totals and
+// the super-block totals before it, with no look-back.
+constexpr int kBlkTiles = 8;
+constexpr int kSupTiles = 2048;
 
 constexpr int kStage = 32 * 16;           // staged outputs of a tile's register-sorted rows
 constexpr int kLaneEnt = 16;              // rows with more entries look their R rows up warp-wide
@@ -1375,6 +1384,10 @@ __global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant_
             if (lane == 0) {
                 a.tile_cnt[t] = tot;
                 a.tile_base[t] = goff;
+                if (tot) {
+                    atomicAdd(a.blk_tot + t / kBlkTiles, (unsigned long long)tot);
+                    atomicAdd(a.sup_tot + t / kSupTiles, (unsigned long long)tot);
+                }
             }
         } else {
             if (lane == 0) s_wtot[warp] = tot;
@@ -1518,49 +1531,58 @@ __global__ void __launch_bounds__(256) k_copy_rows(const __grid_constant__ RowsA
 
 // ------------------------------------------------------------------------
 // Placement of scratch-mode tiles: C receives tile t's outputs (scratch
-// [tile_base[t], + tile_cnt[t])) at the exclusive prefix of the counts.  The
-// counts are all known before this kernel, so its look-back never waits on
-// slow work.  A block is 32 tiles when there are many tiles per CTA, else 8
-// (more blocks to spread); a block's entries are spread over the CTA.
+// [tile_base[t], + tile_cnt[t])) at the exclusive prefix of the counts.  A
+// CTA takes a block of tiles (8, or 32 when there are many tiles), finds the
+// block's prefix from the super-block and block totals the row kernel
+// accumulated (all known: nothing waits), and spreads the block's entries
+// over its threads.
 // ------------------------------------------------------------------------
 constexpr int kCompactTiles = 32;   // largest block (tiles)
 constexpr int kCompactThreads = 256;
 constexpr int kCompactCtas = 6;      // resident per SM
 constexpr int kCompactUnroll = 4;
+constexpr int64_t kCompactWideTiles = 32768;   // from this many tiles, 32-tile blocks
+static_assert(kCompactTiles % kBlkTiles == 0 && kSupTiles % kCompactTiles == 0, "compaction block shape");
 
 struct CompactArgs {
     const int64_t *s_liv;
     const double *s_val;
     const int64_t *tile_cnt;
     const int64_t *tile_base;
+    const unsigned long long *blk_tot;
+    const unsigned long long *sup_tot;
     const int64_t *act_rows;
     const unsigned long long *nact;
     int64_t *c_liv;
     double *c_val;
     int64_t cap;
-    uint64_t *state;
-    uint32_t *ctr;
     WsHeader *hdr;
 };
 
 __global__ void __launch_bounds__(kCompactThreads, kCompactCtas) k_compact(const __grid_constant__ CompactArgs a) {
-    __shared__ int64_t s_blk, s_goff;
+    __shared__ int64_t s_goff;
     __shared__ int64_t s_pre[kCompactTiles + 1];
     __shared__ int64_t s_src[kCompactTiles];
     if (a.hdr->f > a.cap) return;
     const int64_t nact = a.act_rows ? (int64_t)*a.nact : a.hdr->nrows_l;
     const int64_t ntiles = (nact + 31) / 32;
-    const bool wide = ntiles >= 64 * (int64_t)gridDim.x;
+    const bool wide = ntiles >= kCompactWideTiles;
     const int tpb = wide ? 32 : 8, steps = wide ? 5 : 3;
     const int64_t nblk = (ntiles + tpb - 1) / tpb;
     const int tid = threadIdx.x, lane = tid & 31;
-    for (;;) {
-        if (tid == 0) s_blk = atomicAdd(a.ctr, 1u);
-        __syncthreads();
-        const int64_t b = s_blk;
-        if (b >= nblk) break;
+    for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
         if (tid < 32) {
-            const int64_t t = b * tpb + lane;
+            const int64_t t0 = b * tpb;
+            // the block's prefix: super-blocks before it, then the blocks
+            // before it in its super-block
+            unsigned long long pre = 0;
+            const int64_t ns = t0 / kSupTiles;
+            for (int64_t q = lane; q < ns; q += 32) pre += a.sup_tot[q];
+            const int64_t b8_end = t0 / kBlkTiles;
+            for (int64_t q = ns * (kSupTiles / kBlkTiles) + lane; q < b8_end; q += 32) pre += a.blk_tot[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(kFull, pre, o);
+            const int64_t t = t0 + lane;
             const bool mine = lane < tpb && t < ntiles;
             const int64_t c = mine ? a.tile_cnt[t] : 0;
             s_src[lane] = mine ? a.tile_base[t] : 0;
@@ -1573,13 +1595,9 @@ __global__ void __launch_bounds__(kCompactThreads, kCompactCtas) k_compact(const
             const int64_t tot = __shfl_sync(kFull, x, 31);
             s_pre[lane] = x - c;
             if (lane == 31) s_pre[kCompactTiles] = tot;
-            if (lane == 0) lb_store(a.state + b, (b == 0 ? kFlagIncl : kFlagAgg) | (uint64_t)tot);
-            int64_t g = 0;
-            if (b > 0) g = (int64_t)lookback_warp(a.state, b, &a.hdr->status);
             if (lane == 0) {
-                if (b > 0) lb_store(a.state + b, kFlagIncl | (uint64_t)(g + tot));
-                if (b == nblk - 1) a.hdr->nnz_c = g + tot;
-                s_goff = g;
+                s_goff = (int64_t)pre;
+                if (b == nblk - 1) a.hdr->nnz_c = (int64_t)pre + tot;
             }
         }
         __syncthreads();
@@ -1800,6 +1818,7 @@ struct P2Layout {
     size_t act_rows;
     size_t arr[6];          // cap-sized scratch arrays (8 bytes per entry; 4 used off SOP, 6 with placement by scratch)
     size_t tile_cnt, tile_base;   // placement by scratch: per 32-row tile
+    size_t blk_tot, sup_tot;      // placement by scratch: block and super-block totals (zeroed)
     size_t sop_radix;
     int sop_D, sop_P;
     size_t total;
@@ -2327,6 +2346,8 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
             ra.c_val = reinterpret_cast<double *>(p2 + L.arr[5]);
             ra.tile_cnt = reinterpret_cast<int64_t *>(p2 + L.tile_cnt);
             ra.tile_base = reinterpret_cast<int64_t *>(p2 + L.tile_base);
+            ra.blk_tot = reinterpret_cast<unsigned long long *>(p2 + L.blk_tot);
+            ra.sup_tot = reinterpret_cast<unsigned long long *>(p2 + L.sup_tot);
         }
         const int warps = kRowsThreads / 32;
         int64_t grid = (nchunks_max + warps - 1) / warps;
@@ -2353,13 +2374,13 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
             ca.s_val = ra.c_val;
             ca.tile_cnt = ra.tile_cnt;
             ca.tile_base = ra.tile_base;
+            ca.blk_tot = ra.blk_tot;
+            ca.sup_tot = ra.sup_tot;
             ca.act_rows = ra.act_rows;
             ca.nact = nact;
             ca.c_liv = c_liv;
             ca.c_val = c_val;
             ca.cap = cap;
-            ca.state = chunk_state;
-            ca.ctr = chunk_ctr + 12;
             ca.hdr = hdr;
             const int64_t nblk = (nchunks_max + 7) / 8;
             int64_t cgrid = nblk < (int64_t)sms * kCompactCtas ? nblk : (int64_t)sms * kCompactCtas;
@@ -2427,14 +2448,17 @@ P2Layout p2_layout(const lco_plan *p, int64_t cap) {
     size_t off = 0;
     L.chunk_state = off;
     // counters: [0] row tiles, [1] reduce tiles, [2] heavy rows, [4..5] heavy
-    // count, [6..7] long copies, [8] row-table tiles, [10..11] active rows,
-    // [12] compaction blocks
+    // count, [6..7] long copies, [8] row-table tiles, [10..11] active rows
     L.chunk_ctr = (size_t)L.nchunks_max * 8;
     off += align_up((size_t)L.nchunks_max * 8 + 64);
     L.reduce_state = off;
     off += align_up((size_t)((L.capc + kScanTile - 1) / kScanTile + 2) * 8);
     L.table_state = off;
     off += align_up((size_t)((p->nnz_l + kTabTile - 1) / kTabTile + 2) * 8);
+    L.blk_tot = off;
+    off += align_up((size_t)(L.nchunks_max / kBlkTiles + 2) * 8);
+    L.sup_tot = off;
+    off += align_up((size_t)(L.nchunks_max / kSupTiles + 2) * 8);
     L.zero_bytes = off;
     L.act_rows = off;
     off += align_up((size_t)(p->nnz_l > 0 ? p->nnz_l : 1) * 8);
