@@ -54,7 +54,11 @@ KERNEL_SOURCES = {
     "k_radix_scatter": "paper_1802_02619_gb300/csrc/lco_radix.cu",
     "k_radix_upsweep": "paper_1802_02619_gb300/csrc/lco_radix.cu",
     "k_radix_hist": "paper_1802_02619_gb300/csrc/lco_radix.cu",
+    "k_compact": "paper_1802_02619_gb300/csrc/lco_contract.cu",
+    "k_entry_lookup": "paper_1802_02619_gb300/csrc/lco_contract.cu",
 }
+# headers every kernel source includes: a change there changes the kernels too
+KERNEL_HEADERS = ["paper_1802_02619_gb300/csrc/lco_internal.cuh", "paper_1802_02619_gb300/csrc/lco_radix.cuh"]
 
 
 def parse_args():
@@ -191,12 +195,18 @@ def measured_peak_hbm():
 
 
 def source_digest(kernel):
-    path = os.path.join(ROOT, KERNEL_SOURCES.get(kernel, ""))
+    """sha256 (16 hex digits) of the kernel's source file and the shared
+    device headers, in that order."""
+    if kernel not in KERNEL_SOURCES:
+        return None
+    h = hashlib.sha256()
     try:
-        with open(path, "rb") as fh:
-            return hashlib.sha256(fh.read()).hexdigest()[:16]
+        for rel in [KERNEL_SOURCES[kernel]] + KERNEL_HEADERS:
+            with open(os.path.join(ROOT, rel), "rb") as fh:
+                h.update(fh.read())
     except OSError:
         return None
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic(kernel):
