@@ -123,6 +123,36 @@ def permute(dims, sig_old, sig_new, liv, val):
     return lo, vo
 
 
+def _u64pairs(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.uint64))
+    if a.ndim != 2 or a.shape[1] != 2:
+        raise ValueError("wide LIVs are an (nnz, 2) uint64 array: low word, high word")
+    return a
+
+
+def relinearise_wide(dims, sig_old, sig_new, liv):
+    """Sec. 3.1 LIV shuffle with unsigned 128-bit LIVs (Sec. 7 future work):
+    liv is (nnz, 2) uint64, low word first."""
+    lib = _load()
+    dims, so, sn, liv = _i64(dims), _i32(sig_old), _i32(sig_new), _u64pairs(liv)
+    out = np.empty_like(liv)
+    _check(lib.lco_oracle_relinearise_wide(ctypes.c_int32(len(dims)), _p(dims), _p(so), _p(sn),
+                                           ctypes.c_int64(liv.shape[0]), _p(liv), _p(out)),
+           "relinearise_wide")
+    return out
+
+
+def permute_wide(dims, sig_old, sig_new, liv, val):
+    """Permutation by definition (Sec. 4) with unsigned 128-bit LIVs."""
+    lib = _load()
+    dims, so, sn, liv, val = _i64(dims), _i32(sig_old), _i32(sig_new), _u64pairs(liv), _f64(val)
+    lo, vo = np.empty_like(liv), np.empty_like(val)
+    _check(lib.lco_oracle_permute_wide(ctypes.c_int32(len(dims)), _p(dims), _p(so), _p(sn),
+                                       ctypes.c_int64(liv.shape[0]), _p(liv), _p(val), _p(lo), _p(vo)),
+           "permute_wide")
+    return lo, vo
+
+
 def rp_permute(dims, sig_old, sig_new, liv, val):
     """The RP algorithm of Sec. 4.1 (regions + stable sort on the shaved key)."""
     lib = _load()

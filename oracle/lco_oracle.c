@@ -49,6 +49,13 @@
  *                                        tensors in one order, as in Eq. 4
  *                                        (definition: union of entries,
  *                                        values added).
+ *   lco_oracle_relinearise_wide /        Sec. 3.1 and Sec. 7 (future work:
+ *   lco_oracle_permute_wide              LIVs past 2^63 - 1): the same LIV
+ *                                        formula and the same definition of
+ *                                        a permutation, with unsigned 128-bit
+ *                                        LIVs (dims multiply to at most
+ *                                        2^127 - 1); a wide LIV is two
+ *                                        uint64 words, low word first.
  *
  * Parity pins for every function live under tests/ (test_oracle_*.py).
  */
@@ -703,4 +710,97 @@ int lco_oracle_dispatch(int64_t m, int64_t k, int64_t n, int64_t nnz_a, int64_t 
     case CELL_DCSC_DCSR: return col ? ALG_DCSC : ALG_DCSR;
     default: return col ? ALG_CSCNA : ALG_CSRNA;
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* Wide LIVs (Sec. 3.1 leaves LIVs past 2^63 - 1 to future work;        */
+/* Sec. 7).  Same formula and same permutation definition as above in   */
+/* unsigned 128-bit arithmetic; the dims multiply to at most 2^127 - 1. */
+/* ------------------------------------------------------------------ */
+
+typedef unsigned __int128 u128_t;
+
+static int checked_product_wide(int order, const int64_t *dims, u128_t *out)
+{
+    const u128_t lim = ((u128_t)1 << 127) - 1;
+    u128_t p = 1;
+    if (order < 1 || order > ORC_MAX_ORDER) return ORC_ERR_INVALID;
+    for (int i = 0; i < order; ++i) {
+        if (dims[i] < 1) return ORC_ERR_INVALID;
+        if (p > lim / (u128_t)dims[i]) return ORC_ERR_OVERFLOW;
+        p *= (u128_t)dims[i];
+    }
+    *out = p;
+    return ORC_OK;
+}
+
+int lco_oracle_relinearise_wide(int32_t order, const int64_t *dims, const int32_t *sig_old,
+                                const int32_t *sig_new, int64_t nnz, const uint64_t *liv_in,
+                                uint64_t *liv_out)
+{
+    u128_t total;
+    int rc;
+    u128_t coord[ORC_MAX_ORDER];
+    if (!valid_sig(order, sig_old) || !valid_sig(order, sig_new)) return ORC_ERR_INVALID;
+    if ((rc = checked_product_wide(order, dims, &total)) != ORC_OK) return rc;
+    for (int64_t e = 0; e < nnz; ++e) {
+        u128_t r = ((u128_t)liv_in[2 * e + 1] << 64) | liv_in[2 * e];
+        u128_t out = 0;
+        if (r >= total) return ORC_ERR_INVALID;
+        /* coordinates: least significant mode of the old order first */
+        for (int t = 0; t < order; ++t) {
+            const u128_t n = (u128_t)dims[sig_old[t]];
+            coord[sig_old[t]] = r % n;
+            r /= n;
+        }
+        /* Horner from the most significant mode of the new order */
+        for (int t = order - 1; t >= 0; --t) out = out * (u128_t)dims[sig_new[t]] + coord[sig_new[t]];
+        liv_out[2 * e] = (uint64_t)out;
+        liv_out[2 * e + 1] = (uint64_t)(out >> 64);
+    }
+    return ORC_OK;
+}
+
+typedef struct { u128_t key; int64_t idx; } wideidx_t;
+
+static int cmp_wideidx(const void *pa, const void *pb)
+{
+    const wideidx_t *a = (const wideidx_t *)pa, *b = (const wideidx_t *)pb;
+    if (a->key < b->key) return -1;
+    if (a->key > b->key) return 1;
+    if (a->idx < b->idx) return -1;
+    if (a->idx > b->idx) return 1;
+    return 0;
+}
+
+int lco_oracle_permute_wide(int32_t order, const int64_t *dims, const int32_t *sig_old,
+                            const int32_t *sig_new, int64_t nnz, const uint64_t *liv_in,
+                            const double *val_in, uint64_t *liv_out, double *val_out)
+{
+    int rc;
+    uint64_t *newliv;
+    wideidx_t *ki;
+    if (nnz == 0) {
+        u128_t total;
+        if (!valid_sig(order, sig_old) || !valid_sig(order, sig_new)) return ORC_ERR_INVALID;
+        return checked_product_wide(order, dims, &total);
+    }
+    newliv = (uint64_t *)malloc(sizeof(uint64_t) * 2 * (size_t)nnz);
+    ki = (wideidx_t *)malloc(sizeof(wideidx_t) * (size_t)nnz);
+    if (!newliv || !ki) { free(newliv); free(ki); return ORC_ERR_OOM; }
+    rc = lco_oracle_relinearise_wide(order, dims, sig_old, sig_new, nnz, liv_in, newliv);
+    if (rc != ORC_OK) { free(newliv); free(ki); return rc; }
+    for (int64_t e = 0; e < nnz; ++e) {
+        ki[e].key = ((u128_t)newliv[2 * e + 1] << 64) | newliv[2 * e];
+        ki[e].idx = e;
+    }
+    qsort(ki, (size_t)nnz, sizeof(wideidx_t), cmp_wideidx);
+    for (int64_t e = 0; e < nnz; ++e) {
+        liv_out[2 * e] = (uint64_t)ki[e].key;
+        liv_out[2 * e + 1] = (uint64_t)(ki[e].key >> 64);
+        val_out[e] = val_in[ki[e].idx];
+    }
+    free(newliv);
+    free(ki);
+    return ORC_OK;
 }

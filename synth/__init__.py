@@ -430,3 +430,39 @@ def config_eq17(N=2047):
     co = np.stack([np.repeat(r, N), np.repeat(c, N), np.tile(j, r.shape[0]), np.tile(j, r.shape[0])], 1)
     b = _pack([N] * 4, co, np.repeat(v, N))
     return {"name": f"eq17_b_d_N{N}", "A": b, "B": fd_matrix(N), "modes_a": [1], "modes_b": [0]}
+
+
+def wide_tensor(dims, sig, nnz, seed):
+    """A tensor whose dims multiply past 2^63 (wide LIVs: unsigned 128-bit,
+    stored as an (nnz, 2) uint64 array, low word first): nnz distinct LIVs
+    drawn uniformly from [0, prod dims), ascending, values U(-1, 1).  The
+    LIVs are drawn directly (no coordinates); sig only labels the order."""
+    total = 1
+    for d in dims:
+        total *= int(d)
+    if total > (1 << 127) - 1:
+        raise ValueError("dims multiply past 2^127 - 1")
+    nnz = min(int(nnz), total)
+    rng = np.random.default_rng(seed)
+    hi_max = total >> 64
+    got = np.empty((0, 2), dtype=np.uint64)
+    while got.shape[0] < nnz:
+        m = int((nnz - got.shape[0]) * 1.2) + 16
+        lo = rng.integers(0, 1 << 64, size=m, dtype=np.uint64)
+        hi = rng.integers(0, hi_max + 1, size=m, dtype=np.uint64) if hi_max > 0 else np.zeros(m, np.uint64)
+        if hi_max == 0:
+            lo = lo % np.uint64(total)
+        # keep draws below total: only the top high word can overshoot
+        top_lo = np.uint64(total & ((1 << 64) - 1))
+        ok = (hi < np.uint64(hi_max)) | ((hi == np.uint64(hi_max)) & (lo < top_lo)) if hi_max > 0 else np.ones(m, bool)
+        cand = np.concatenate([got, np.stack([lo[ok], hi[ok]], 1)])
+        order = np.lexsort((cand[:, 0], cand[:, 1]))
+        cand = cand[order]
+        keep = np.ones(cand.shape[0], bool)
+        keep[1:] = (cand[1:, 0] != cand[:-1, 0]) | (cand[1:, 1] != cand[:-1, 1])
+        got = cand[keep]
+    if got.shape[0] > nnz:
+        pick = np.sort(rng.choice(got.shape[0], size=nnz, replace=False))
+        got = got[pick]
+    return {"dims": [int(d) for d in dims], "sig": list(sig), "liv": np.ascontiguousarray(got),
+            "val": rng.uniform(-1, 1, nnz)}

@@ -1,0 +1,101 @@
+"""Pins for the oracle's wide-LIV re-linearisation and permutation (unsigned
+128-bit LIVs, Sec. 3.1's future work on LIVs past 2^63 - 1; Sec. 7).
+
+Each pin checks the oracle against something other than its own formula:
+the 64-bit oracle (pinned separately) where the dims allow both; bit-field
+shuffles where every dim is a power of two (a LIV is then a concatenation of
+bit fields); the round trip back to the old order; and coordinates kept
+with their values."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+def _ints(liv):
+    return [int(a) | (int(b) << 64) for a, b in liv]
+
+
+def _pairs(ints):
+    return np.array([[x & ((1 << 64) - 1), x >> 64] for x in ints], dtype=np.uint64).reshape(-1, 2)
+
+
+def test_equals_the_64_bit_oracle_where_both_apply():
+    rng = np.random.default_rng(1)
+    dims = [37, 50, 29, 41]
+    total = int(np.prod(dims))
+    liv = np.sort(rng.choice(total, size=4000, replace=False)).astype(np.int64)
+    val = rng.uniform(-1, 1, liv.shape[0])
+    for new_sig in ([0, 1, 2, 3], [2, 0, 3, 1], [3, 1, 0, 2]):
+        l64, v64 = oracle.permute(dims, [3, 2, 1, 0], new_sig, liv, val)
+        wl, wv = oracle.permute_wide(dims, [3, 2, 1, 0], new_sig, _pairs(liv.tolist()), val)
+        assert _ints(wl) == [int(x) for x in l64]
+        assert np.array_equal(wv, v64)
+
+
+def test_power_of_two_dims_are_bit_field_shuffles():
+    # dims 2^41, 2^40, 2^30, 2^13: a LIV is four bit fields; re-linearising
+    # moves whole fields, which shifts and masks compute without division
+    widths = [41, 40, 30, 13]
+    dims = [1 << w for w in widths]
+    T = synth.wide_tensor(dims, [3, 2, 1, 0], 3000, seed=2)
+
+    def fields(x, sig):
+        out = {}
+        for m in sig:                       # least significant field first
+            out[m] = x & ((1 << widths[m]) - 1)
+            x >>= widths[m]
+        return out
+
+    def join(f, sig):
+        x, sh = 0, 0
+        for m in sig:
+            x |= f[m] << sh
+            sh += widths[m]
+        return x
+
+    for new_sig in ([0, 1, 2, 3], [1, 3, 0, 2]):
+        got = _ints(oracle.relinearise_wide(dims, [3, 2, 1, 0], new_sig, T["liv"]))
+        want = [join(fields(x, [3, 2, 1, 0]), new_sig) for x in _ints(T["liv"])]
+        assert got == want
+
+
+def test_round_trip_restores_the_tensor():
+    dims = [(1 << 40) + 7, (1 << 35) - 3, 999_983, 1 << 20]   # product ~2^115
+    T = synth.wide_tensor(dims, [3, 2, 1, 0], 5000, seed=3)
+    l1, v1 = oracle.permute_wide(dims, [3, 2, 1, 0], [1, 3, 0, 2], T["liv"], T["val"])
+    l2, v2 = oracle.permute_wide(dims, [1, 3, 0, 2], [3, 2, 1, 0], l1, v1)
+    assert np.array_equal(l2, T["liv"]) and np.array_equal(v2, T["val"])
+
+
+def test_coordinates_keep_their_values_and_the_output_is_sorted():
+    dims = [(1 << 50) + 1, (1 << 45) - 5, 12345]
+    T = synth.wide_tensor(dims, [2, 1, 0], 3000, seed=4)
+    new_sig = [0, 2, 1]
+    lo, vo = oracle.permute_wide(dims, [2, 1, 0], new_sig, T["liv"], T["val"])
+
+    def coords(x, sig):
+        c = [0] * len(dims)
+        for m in sig:
+            x, c[m] = divmod(x, dims[m])
+        return tuple(c)
+
+    before = {coords(x, [2, 1, 0]): v for x, v in zip(_ints(T["liv"]), T["val"])}
+    after_ints = _ints(lo)
+    after = {coords(x, new_sig): v for x, v in zip(after_ints, vo)}
+    assert before == after
+    assert all(a < b for a, b in zip(after_ints, after_ints[1:]))
+
+
+def test_limits():
+    # dims multiplying past 2^127 - 1 are rejected
+    with pytest.raises(oracle.OracleError):
+        oracle.permute_wide([(1 << 63) - 1, (1 << 63) - 1, 4], [2, 1, 0], [0, 1, 2],
+                            np.zeros((1, 2), np.uint64), np.zeros(1))
+    # a LIV outside [0, prod dims) is rejected
+    with pytest.raises(oracle.OracleError):
+        oracle.relinearise_wide([1 << 40, 1 << 40], [1, 0], [0, 1], _pairs([1 << 80]))
+    # empty tensors are fine
+    lo, vo = oracle.permute_wide([1 << 40, 1 << 40], [1, 0], [0, 1], np.zeros((0, 2), np.uint64), np.zeros(0))
+    assert lo.shape == (0, 2) and vo.shape == (0,)
