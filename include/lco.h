@@ -45,7 +45,7 @@ extern "C" {
 typedef enum {
     LCO_OK = 0,
     LCO_ERR_INVALID = 1,    /* malformed arguments (sig, dims, modes, sizes, pointers) */
-    LCO_ERR_OVERFLOW = 2,   /* product of dims (or m*n of a contraction) > 2^63 - 1 */
+    LCO_ERR_OVERFLOW = 2,   /* product of dims (or m*n of a contraction) > 2^63 - 1 (2^127 - 1 for wide LIVs) */
     LCO_ERR_UNSORTED = 3,   /* input LIVs not strictly ascending (checking entry points) */
     LCO_ERR_OOM = 4,        /* workspace smaller than reported, or host allocation failed */
     LCO_ERR_TIMEOUT = 5,    /* a device-side wait ran out (device status only) */
@@ -177,6 +177,55 @@ int32_t lco_radix_permute(const lco_shape *t, const int32_t *new_sig,
 int32_t lco_radix_permute_static(const lco_shape *t, const int32_t *new_sig,
                                  const int64_t *liv_in, const double *val_in,
                                  int64_t *liv_out, double *val_out, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Wide LIVs.  Sec. 3.1 limits LIVs to signed 64 bits (dims multiplying */
+/* to at most 2^63 - 1) and leaves larger LIVs to future work, as does  */
+/* Sec. 7.  A wide LIV is an unsigned 128-bit integer with the same     */
+/* formula, stored as two uint64 words, low word first (16 bytes per    */
+/* non-zero); the dims of a wide tensor multiply to at most 2^127 - 1.  */
+/* lco_shape is used unchanged (each dim still fits int64).             */
+/* ------------------------------------------------------------------ */
+
+/* Wide counterpart of lco_relinearise: liv_in / liv_out are device arrays
+ * of 2 * t->nnz uint64 (low, high word per non-zero).  Errors:
+ * LCO_ERR_INVALID (sig, order, dims, pointers), LCO_ERR_OVERFLOW (product
+ * of dims > 2^127 - 1).  LIVs outside [0, prod dims) give unspecified
+ * output values but never out-of-bounds accesses. */
+int32_t lco_relinearise_wide(const lco_shape *t, const int32_t *new_sig,
+                             const uint64_t *liv_in, uint64_t *liv_out, void *stream);
+
+/* How a wide permutation is carried out: rearrangement indices (Sec. 4.1),
+ * the width of the sort key (the new LIV without its resting suffix), the
+ * 54-bit chunks it is sorted in (least significant first) and the radix
+ * passes before device-side skipping of constant digits. */
+typedef struct {
+    int32_t n_rearr;
+    int32_t key_bits;
+    int32_t chunks;
+    int32_t passes;
+} lco_rp_wide_info;
+
+int32_t lco_radix_permute_wide_info(const lco_shape *t, const int32_t *new_sig, lco_rp_wide_info *info);
+
+/* Workspace bytes for lco_radix_permute_wide (about 100 bytes per non-zero
+ * plus the radix engine's tables). */
+int32_t lco_radix_permute_wide_workspace(const lco_shape *t, const int32_t *new_sig, size_t *ws_bytes);
+
+/* Wide counterpart of lco_radix_permute (Sec. 4.1 with 128-bit LIVs):
+ * rearranges (liv_in, val_in), strictly ascending in order t->sig, into
+ * (liv_out, val_out), strictly ascending in order new_sig.  liv arrays hold
+ * 2 * t->nnz uint64 (low, high word per non-zero), val arrays t->nnz
+ * doubles, all on the device, no aliasing.  The key (new LIV without its
+ * resting suffix) is sorted in 54-bit chunks by the stable radix engine,
+ * least significant chunk first, carrying input positions; the new LIVs and
+ * values are then gathered.  ws: lco_radix_permute_wide_workspace() bytes,
+ * 256-byte aligned, zero-filled before its first use.  Errors as
+ * lco_radix_permute (LCO_ERR_OVERFLOW past 2^127 - 1). */
+int32_t lco_radix_permute_wide(const lco_shape *t, const int32_t *new_sig,
+                               const uint64_t *liv_in, const double *val_in,
+                               uint64_t *liv_out, double *val_out,
+                               void *ws, size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------ */
 /* Contraction C = A x_modes B (Sec. 5: map to matrices, convert to a   */

@@ -24,7 +24,7 @@ ALG_NAMES = ("CSR", "CSC", "DCSR", "DCSC", "CSRNA", "CSCNA", "SOP")
 ALG = {name: i for i, name in enumerate(ALG_NAMES)}
 
 STATUS = {
-    0: "ok", 1: "invalid argument", 2: "index space exceeds 2^63-1", 3: "unsorted input",
+    0: "ok", 1: "invalid argument", 2: "index space exceeds the LIV range (2^63-1; 2^127-1 for wide LIVs)", 3: "unsorted input",
     4: "workspace too small", 5: "device wait timed out", 6: "CUDA runtime error",
     7: "admission refused", 8: "output capacity too small", 9: "input exceeds the fixed scratch",
 }
@@ -46,6 +46,11 @@ class RpInfo(ctypes.Structure):
                 ("m_top", ctypes.c_int64), ("m_low", ctypes.c_int64), ("key_bits", ctypes.c_int32),
                 ("digit_bits", ctypes.c_int32), ("passes", ctypes.c_int32),
                 ("segments", ctypes.c_int32)]
+
+
+class RpWideInfo(ctypes.Structure):
+    _fields_ = [("n_rearr", ctypes.c_int32), ("key_bits", ctypes.c_int32), ("chunks", ctypes.c_int32),
+                ("passes", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -119,6 +124,15 @@ _SIGNATURES = {
                            ctypes.c_void_p], ctypes.c_int32),
     "lco_radix_permute_static": ([ctypes.POINTER(Shape), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "lco_relinearise_wide": ([ctypes.POINTER(Shape), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p], ctypes.c_int32),
+    "lco_radix_permute_wide_info": ([ctypes.POINTER(Shape), ctypes.c_void_p, ctypes.POINTER(RpWideInfo)],
+                                    ctypes.c_int32),
+    "lco_radix_permute_wide_workspace": ([ctypes.POINTER(Shape), ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int32),
+    "lco_radix_permute_wide": ([ctypes.POINTER(Shape), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                ctypes.c_void_p], ctypes.c_int32),
     "lco_contract_plan": ([ctypes.POINTER(Shape), ctypes.POINTER(Shape), ctypes.c_int32, ctypes.c_void_p,
                            ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int32),
     "lco_plan_get_info": ([ctypes.c_void_p, ctypes.POINTER(PlanInfo)], ctypes.c_int32),
@@ -372,6 +386,80 @@ def radix_permute(t: LcoTensor, new_sig, stream=None) -> LcoTensor:
     if st != 0:
         raise LcoError(st, "lco_radix_permute (device)")
     return LcoTensor(list(t.dims), list(new_sig), liv, val)
+
+
+# ---------------------------------------------------------------------------
+# Wide LIVs (unsigned 128-bit; dims multiplying past 2^63 - 1)
+# ---------------------------------------------------------------------------
+
+def _wide(liv: torch.Tensor):
+    if liv.dtype != torch.int64 or liv.dim() != 2 or liv.shape[1] != 2 or not liv.is_contiguous():
+        raise ValueError("wide LIVs are a contiguous (nnz, 2) int64 tensor: low word, high word (bit patterns)")
+
+
+def relinearise_wide(dims, sig, new_sig, liv: torch.Tensor, out: Optional[torch.Tensor] = None,
+                     stream=None) -> torch.Tensor:
+    """LIV shuffle (Sec. 3.1) of wide LIVs; element order kept."""
+    lib = load()
+    _require_cuda(liv)
+    _wide(liv)
+    out = torch.empty_like(liv) if out is None else out
+    sh = make_shape(dims, sig, liv.shape[0])
+    _check(lib.lco_relinearise_wide(ctypes.byref(sh), _sig_arr(new_sig), _ptr(liv), _ptr(out), _stream(stream)),
+           "lco_relinearise_wide")
+    return out
+
+
+def radix_permute_wide_info(dims, sig, new_sig, nnz: int = 0) -> dict:
+    lib = load()
+    sh = make_shape(dims, sig, nnz)
+    info = RpWideInfo()
+    _check(lib.lco_radix_permute_wide_info(ctypes.byref(sh), _sig_arr(new_sig), ctypes.byref(info)),
+           "lco_radix_permute_wide_info")
+    return {"n_rearr": info.n_rearr, "key_bits": info.key_bits, "chunks": info.chunks, "passes": info.passes}
+
+
+class WidePermuter:
+    """Reusable permutation of wide-LIV tensors of one shape to one order."""
+
+    def __init__(self, dims, sig, new_sig, nnz: int, device="cuda"):
+        self.lib = load()
+        self.nnz = int(nnz)
+        self.sh = make_shape(dims, sig, self.nnz)
+        self._new = _sig_arr(new_sig)
+        nb = ctypes.c_size_t()
+        _check(self.lib.lco_radix_permute_wide_workspace(ctypes.byref(self.sh), self._new, ctypes.byref(nb)),
+               "lco_radix_permute_wide_workspace")
+        self.ws = workspace(nb.value, device)
+
+    def __call__(self, liv, val, liv_out=None, val_out=None, stream=None):
+        _require_cuda(liv, val)
+        _wide(liv)
+        if liv.shape[0] != self.nnz or val.numel() != self.nnz:
+            raise ValueError("nnz differs from the planned size")
+        liv_out = torch.empty_like(liv) if liv_out is None else liv_out
+        val_out = torch.empty_like(val) if val_out is None else val_out
+        _check(self.lib.lco_radix_permute_wide(ctypes.byref(self.sh), self._new, _ptr(liv), _ptr(val),
+                                               _ptr(liv_out), _ptr(val_out), _ptr(self.ws),
+                                               ctypes.c_size_t(self.ws.numel()), _stream(stream)),
+               "lco_radix_permute_wide")
+        return liv_out, val_out
+
+    def device_status(self, stream=None) -> int:
+        st = ctypes.c_int32()
+        _check(self.lib.lco_workspace_status(_ptr(self.ws), ctypes.byref(st), _stream(stream)),
+               "lco_workspace_status")
+        return st.value
+
+
+def radix_permute_wide(dims, sig, new_sig, liv: torch.Tensor, val: torch.Tensor, stream=None):
+    """Rearrange a wide-LIV tensor into order new_sig (Sec. 4.1 with 128-bit LIVs)."""
+    p = WidePermuter(dims, sig, new_sig, liv.shape[0], device=liv.device)
+    lo, vo = p(liv, val, stream=stream)
+    st = p.device_status(stream)
+    if st != 0:
+        raise LcoError(st, "lco_radix_permute_wide (device)")
+    return lo, vo
 
 
 # ---------------------------------------------------------------------------

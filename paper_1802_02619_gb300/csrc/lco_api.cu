@@ -98,7 +98,7 @@ const char *lco_status_str(int32_t status) {
     switch (status) {
     case LCO_OK: return "ok";
     case LCO_ERR_INVALID: return "invalid argument";
-    case LCO_ERR_OVERFLOW: return "index space exceeds 2^63-1";
+    case LCO_ERR_OVERFLOW: return "index space exceeds the LIV range (2^63-1; 2^127-1 for wide LIVs)";
     case LCO_ERR_UNSORTED: return "input LIVs not strictly ascending";
     case LCO_ERR_OOM: return "workspace too small or allocation failed";
     case LCO_ERR_TIMEOUT: return "device wait timed out";
