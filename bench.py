@@ -69,7 +69,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["lco", "reference"], default="lco")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["step", "permute", "batch", "serve", "permsweep"], default="step",
+    ap.add_argument("--case", choices=["step", "permute", "batch", "serve", "permsweep", "permute_wide"],
+                    default="step",
                     help="step: the benchmark workload; permute: a stand-alone radix permutation "
                          "of a random 6th-order 64^6 tensor (profiling aid)")
     ap.add_argument("--nnz", type=int, default=16 << 20, help="non-zeros for --case permute")
@@ -1001,6 +1002,72 @@ def run_permsweep_case(args):
     print(json.dumps(out), flush=True)
 
 
+def run_permute_wide_case(args):
+    """Radix permutation of a tensor with wide (128-bit) LIVs: order 4,
+    dims 2^40 x (2^40 - 3) x (2^30 + 3) x 1000 (~2^120 index space), 16M
+    non-zeros drawn uniformly, row-major -> fully reversed order (an 80-bit
+    sort key in two 54-bit chunks).  Inputs resident on the device; L2
+    flushed before every step.  Algorithmic bytes per non-zero: 48 (read and
+    write a 16-byte LIV and an 8-byte value)."""
+    import torch
+    import paper_1802_02619_gb300 as lco
+    import synth
+    dims, sig, new_sig = [1 << 40, (1 << 40) - 3, (1 << 30) + 3, 1000], [3, 2, 1, 0], [0, 1, 2, 3]
+    nnz = args.nnz or 16_000_000
+    T = synth.wide_tensor(dims, sig, nnz, seed=21)
+    n = T["liv"].shape[0]
+    liv = torch.from_numpy(T["liv"].view(np.int64)).cuda()
+    val = torch.as_tensor(T["val"]).cuda()
+    p = lco.WidePermuter(dims, sig, new_sig, n)
+    out_l, out_v = torch.empty_like(liv), torch.empty_like(val)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        p(liv, val, out_l, out_v)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ts = []
+    steps = max(min(args.steps, 50), 5)
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p(liv, val, out_l, out_v)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    assert p.device_status() == 0
+    # output LIVs strictly ascending as unsigned 128-bit numbers (the low word
+    # compared unsigned by flipping its sign bit)
+    hi, lo = out_l[:, 1], out_l[:, 0] ^ torch.iinfo(torch.int64).min
+    assert bool(((hi[1:] > hi[:-1]) | ((hi[1:] == hi[:-1]) & (lo[1:] > lo[:-1]))).all()), "output not ascending"
+    ms = statistics.median(ts)
+    info = lco.radix_permute_wide_info(dims, sig, new_sig, n)
+    peak, kind = measured_peak_hbm()
+    achieved = 48.0 * n / (ms * 1e-3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        m = min(n, 1_000_000)
+        t0 = time.perf_counter()
+        oracle.permute_wide(dims, sig, new_sig, T["liv"][:m], T["val"][:m])
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(m / dt / 1e9, 5), "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+               "sample": f"the first {m} non-zeros of the same tensor, one run, {dt:.2f} s"}
+    out = {"case": "permute_wide", "metric": "wide-LIV permutation Gkeys/s", "value": round(n / (ms * 1e-3) / 1e9, 4),
+           "unit": "Gkeys/s", "ms_per_step": round(ms, 4), "steps": steps, "nnz": n, "dtype": "u128+f64",
+           "config": {"workload": "order-4 wide tensor 2^40 x (2^40-3) x (2^30+3) x 1000, uniform LIVs, "
+                                  "row-major -> reversed", "l2": "flushed before every step"},
+           "key": info, "clocks": clk,
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "peak_kind": kind,
+                        "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                        "algorithmic_bytes": 48 * n},
+           "cpu_baseline": cpu}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.case == "permute":
@@ -1011,6 +1078,9 @@ def main():
         return
     if args.case == "serve":
         run_serve_case(args)
+        return
+    if args.case == "permute_wide":
+        run_permute_wide_case(args)
         return
     if args.case == "permsweep":
         run_permsweep_case(args)
