@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const __grid_co
     __syncthreads();
     for (int i = threadIdx.x; i < nh; i += blockDim.x) {
         const int p = i / NB, d = i - p * NB;
-        j.counts_src[((int64_t)p * j.G + blockIdx.x) * NB + d] = s_hist[i];
+        j.counts_src[((int64_t)p * NB + d) * j.G + blockIdx.x] = s_hist[i];
         if (s_hist[i]) atomicAdd(reinterpret_cast<unsigned long long *>(&j.ghist[i]), (unsigned long long)s_hist[i]);
     }
     __threadfence();
@@ -244,11 +244,12 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const __grid_const
             if (v[i] >= 0) atomicAdd(&s_hist[(uint32_t)(divu(j.key_div, (uint64_t)v[i]) >> shift) & mask], 1u);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < NB; d += blockDim.x) j.counts_hist[(int64_t)blockIdx.x * NB + d] = s_hist[d];
+    for (int d = threadIdx.x; d < NB; d += blockDim.x) j.counts_hist[(int64_t)d * j.G + blockIdx.x] = s_hist[d];
 }
 
 // roffs[r][d] = offs[pass][d] + sum of counts[r'][d] over ranges r' < r.
-// One warp per digit.
+// One warp per digit.  The count tables are digit-major ([d][G]), so a warp
+// reads 32 consecutive ranges per load; lane l holds ranges i * 32 + l.
 __global__ void __launch_bounds__(kRadixThreads) k_radix_offsets(const __grid_constant__ RadixJob j, int pass) {
     const PassIO io = pass_io(j, pass);
     if (!io.run || io.copy) return;
@@ -256,30 +257,26 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_offsets(const __grid_co
     const int lane = threadIdx.x & 31;
     const int d = blockIdx.x * kRadixWarps + (threadIdx.x >> 5);
     if (d >= NB) return;
-    const uint32_t *cnt = io.first ? j.counts_src + (int64_t)pass * j.G * NB : j.counts_hist;
-    // lane l owns ranges [l * per, (l + 1) * per): all its loads are issued
-    // before the scan (G <= 32 * kOffItems)
-    const int per = (j.G + 31) / 32;
+    const uint32_t *cnt = (io.first ? j.counts_src + (int64_t)pass * NB * j.G : j.counts_hist) + (int64_t)d * j.G;
+    // all loads issued before the scans (G <= 32 * kOffItems)
     uint32_t c[kOffItems];
-    uint64_t local = 0;
 #pragma unroll
     for (int i = 0; i < kOffItems; ++i) {
-        const int r = lane * per + i;
-        c[i] = (i < per && r < j.G) ? cnt[(int64_t)r * NB + d] : 0u;
-        local += c[i];
+        const int r = i * 32 + lane;
+        c[i] = r < j.G ? cnt[r] : 0u;
     }
-    uint64_t x = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t u = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += u;
-    }
-    uint64_t run = j.offs[pass * NB + d] + x - local;
+    uint64_t run = j.offs[pass * NB + d];
 #pragma unroll
     for (int i = 0; i < kOffItems; ++i) {
-        const int r = lane * per + i;
-        if (i < per && r < j.G) j.roffs[(int64_t)r * NB + d] = run;
-        run += c[i];
+        uint64_t x = c[i];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t u = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += u;
+        }
+        const int r = i * 32 + lane;
+        if (r < j.G) j.roffs[(int64_t)r * NB + d] = run + x - c[i];
+        run += __shfl_sync(kFull, x, 31);
     }
 }
 

@@ -50,8 +50,8 @@ struct RadixJob {
     uint64_t *ghist;       // [P][NB] global digit counts (left zeroed after use)
     uint64_t *offs;        // [P][NB] exclusive digit offsets
     int32_t *active;       // [kMaxPasses] + count at [16]
-    uint32_t *counts_src;  // [P][G][NB] per-range counts over the source order
-    uint32_t *counts_hist; // [G][NB] per-range counts before a later pass
+    uint32_t *counts_src;  // [P][NB][G] per-range counts over the source order (digit-major)
+    uint32_t *counts_hist; // [NB][G] per-range counts before a later pass (digit-major)
     uint64_t *roffs;       // [G][NB] start of each (range, digit) in the output of a pass
     uint32_t *counters;    // [8] "last block" counter
     int32_t *status;
