@@ -150,3 +150,38 @@ def test_entrywise_plan_validation():
         lco.ContractPlan([3, 4], [1, 0], 5, [4, 3], [1, 0], 5, [], [], entry_a=[0], entry_b=[0])
     p = lco.ContractPlan([3, 4, 5], [2, 1, 0], 30, [3, 5, 6], [2, 1, 0], 40, [2], [1], entry_a=[0], entry_b=[0])
     assert p.c_dims == [3, 4, 6] and p.c_sig == [2, 1, 0]
+
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_wide_plan_matches_the_64_bit_classification(order):
+    """The wide permutation classifies indices like the 64-bit path (Sec.
+    4.1) and its key is the new LIV without the resting suffix."""
+    rng = np.random.default_rng(40 + order)
+    dims = [int(x) for x in rng.integers(2, 9, size=order)]
+    for so in itertools.permutations(range(order)):
+        for sn in itertools.permutations(range(order)):
+            w = lco.radix_permute_wide_info(dims, list(so), list(sn), nnz=10)
+            n = lco.radix_permute_info(dims, list(so), list(sn), nnz=10)
+            assert w["n_rearr"] == n["n_rearr"]
+            if n["n_rearr"]:
+                total = int(np.prod(dims))
+                assert (1 << w["key_bits"]) >= total // n["m_low"] > (1 << w["key_bits"]) // 2
+                assert w["chunks"] == 1
+            else:
+                assert w["key_bits"] == 0 and w["chunks"] == 0
+
+
+def test_wide_limits_and_chunks():
+    # 2^127 - 1 is the wide limit; past it the shape is rejected
+    with pytest.raises(lco.LcoError) as e:
+        lco.radix_permute_wide_info([(1 << 63) - 1, (1 << 63) - 1, 4], [2, 1, 0], [0, 1, 2])
+    assert e.value.status == 2
+    with pytest.raises(lco.LcoError):
+        lco.radix_permute_wide_info([1 << 40, 1 << 40], [0, 0], [1, 0])       # sig not a permutation
+    # a 123-bit key is sorted in three 54-bit chunks, least significant first
+    info = lco.radix_permute_wide_info([15, 1 << 61, 1 << 62], [2, 1, 0], [0, 2, 1])
+    assert info == {"n_rearr": 2, "key_bits": 123, "chunks": 3, "passes": info["passes"]}
+    assert info["passes"] >= 3
+    # the 64-bit entry points still reject such shapes
+    with pytest.raises(lco.LcoError):
+        lco.radix_permute_info([15, 1 << 61, 1 << 62], [2, 1, 0], [0, 2, 1])
