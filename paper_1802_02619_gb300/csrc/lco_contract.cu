@@ -22,9 +22,11 @@
 // Every product is therefore summed in generation order on every path, and
 // results are bit-identical across runs.  The remaining (light) rows go one
 // lane per row, 32 rows per warp: a lane merges a row's sorted B rows, which
-// accumulates and sorts in one go.  Every tile of rows places its output
-// with decoupled look-back, so C is written once, in order.  SOP (Sec. 5.2.5) expands all f products, sorts them by output LIV
-// with the radix engine and sums runs.
+// accumulates and sorts in one go.  Tiles of rows find their place in C by
+// decoupled look-back (small L) or write through scratch at their product
+// offsets and are then moved into C by k_compact (large L).  SOP (Sec.
+// 5.2.5) expands all f products, sorts them by output LIV with the radix
+// engine and sums runs.
 #include <algorithm>
 #include <atomic>
 #include <cstdlib>
@@ -839,9 +841,9 @@ __global__ void __launch_bounds__(kCT, 1) k_heavy(const __grid_constant__ HeavyA
 // L1/L2 directly.  Rows a lane does not merge are taken by the whole warp:
 // a row with a single run is copied (coalesced, scaled) and a row with more
 // runs or more products is gathered into shared memory, sorted (bitonic) and
-// reduced into scratch.  Heavy rows were reduced by k_heavy.  A first pass
-// counts each row's outputs; after the tile's offset is known (decoupled
-// look-back over tiles) a second pass writes C.
+// reduced into scratch.  Heavy rows were reduced by k_heavy.  Network rows
+// are sorted in registers and staged in shared memory; a tile's outputs are
+// placed once its offset is known (see k_rows for the two placements).
 // ------------------------------------------------------------------------
 constexpr int kLaneProd = 64;          // products a lane merges by itself
 constexpr int kRowsThreads = 128;      // 4 warps per CTA
