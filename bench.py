@@ -72,8 +72,10 @@ def parse_args():
     ap.add_argument("--case", choices=["step", "permute", "batch", "serve", "permsweep", "permute_wide"],
                     default="step",
                     help="step: the benchmark workload; permute: a stand-alone radix permutation "
-                         "of a random 6th-order 64^6 tensor (profiling aid)")
-    ap.add_argument("--nnz", type=int, default=16 << 20, help="non-zeros for --case permute")
+                         "of a random 6th-order 64^6 tensor (profiling aid); batch / serve: C4 / C5; "
+                         "permsweep: the Eq. 4 operator into all 23 other orders; permute_wide: a "
+                         "wide-LIV (128-bit) permutation")
+    ap.add_argument("--nnz", type=int, default=16 << 20, help="non-zeros for --case permute / permute_wide")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="C2",
                     help="--case step: C1 fd2d 16^2 L^2, C2 fd3d 64^3 L.Dx + permute (the metric's), "
                          "C3 R-MAT 1e7 DCSR, C3b R-MAT 2^18 CSRNA, E17 the Sec. 6 product at N = 2047")
