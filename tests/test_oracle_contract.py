@@ -287,3 +287,62 @@ def test_configs_take_the_named_branches():
     assert oracle.dispatch(1 << 18, 1 << 18, 1 << 18, 1810432, 532480, 0, 2) == "CSR"
     assert oracle.dispatch(1 << 20, 1 << 32, 1 << 20, 10_000_000, 10_000_000, 1, 1) == "DCSR"
     assert oracle.dispatch(1 << 28, 1 << 12, 1 << 28, 1 << 18, 1 << 18, 0, 2) == "CSRNA"
+
+
+def _rt(dims, nnz, seed):
+    rng = np.random.default_rng(seed)
+    total = int(np.prod(dims))
+    liv = np.sort(rng.choice(total, size=min(nnz, total), replace=False)).astype(np.int64)
+    return {"dims": list(dims), "sig": list(range(len(dims) - 1, -1, -1)), "liv": liv,
+            "val": rng.uniform(-1, 1, liv.shape[0])}
+
+
+def _as_tensor(dims, liv, val):
+    return {"dims": list(dims), "sig": list(range(len(dims) - 1, -1, -1)), "liv": liv, "val": val}
+
+
+def test_chained_products_associate():
+    """(A x B) x C = A x (B x C) for a chain of matrix-like contractions: the
+    output mode order (A's free modes, then B's) must line up across both
+    groupings.  Entry patterns agree exactly; values to rounding."""
+    A = _rt([6, 7, 5], 90, 101)          # (i, j, k)
+    B = _rt([5, 8], 25, 102)             # (k, l)
+    Cm = _rt([8, 4, 3], 60, 103)         # (l, m, n)
+    l1, v1, _ = oracle.contract(A, B, [2], [0])                        # (i, j, l)
+    left = oracle.contract(_as_tensor([6, 7, 8], l1, v1), Cm, [2], [0])  # (i, j, m, n)
+    l2, v2, _ = oracle.contract(B, Cm, [1], [0])                       # (k, m, n)
+    right = oracle.contract(A, _as_tensor([5, 4, 3], l2, v2), [2], [0])  # (i, j, m, n)
+    dense_left = np.zeros([6, 7, 4, 3]); dense_right = np.zeros([6, 7, 4, 3])
+    dense_left.reshape(-1)[left[0]] = left[1]
+    dense_right.reshape(-1)[right[0]] = right[1]
+    assert np.allclose(dense_left, dense_right, rtol=0, atol=1e-12)
+
+
+def test_swapping_operands_transposes_the_product():
+    """contract(B, A) has B's free modes first; moving them behind A's gives
+    contract(A, B) exactly (same products, same summation order per entry)."""
+    A = _rt([5, 6, 4], 70, 111)          # (i, k, j)
+    B = _rt([6, 3, 7], 60, 112)          # (k, l, m)
+    la, va, _ = oracle.contract(A, B, [1], [0])   # (i, j, l, m)
+    lb, vb, _ = oracle.contract(B, A, [0], [1])   # (l, m, i, j)
+    # (l, m, i, j) row-major -> (i, j, l, m) row-major: sig lists modes least significant first
+    lt, vt = oracle.permute([3, 7, 5, 4], [3, 2, 1, 0], [1, 0, 3, 2], lb, vb)
+    assert np.array_equal(lt, la)
+    assert np.allclose(vt, va, rtol=0, atol=1e-15)
+
+
+def test_contraction_is_bilinear():
+    """contract(A + 2 A', B) = contract(A, B) + 2 contract(A', B), with the
+    sum taken by the oracle's add: catches dropped terms and sign errors."""
+    A = _rt([4, 6], 14, 121)
+    A2 = _rt([4, 6], 12, 122)
+    B = _rt([6, 5], 16, 123)
+    s_liv, s_val = oracle.add(1.0, A, 2.0, A2)
+    lhs_l, lhs_v, _ = oracle.contract(_as_tensor([4, 6], s_liv, s_val), B, [1], [0])
+    l1, v1, _ = oracle.contract(A, B, [1], [0])
+    l2, v2, _ = oracle.contract(A2, B, [1], [0])
+    rhs_l, rhs_v = oracle.add(1.0, _as_tensor([4, 5], l1, v1), 2.0, _as_tensor([4, 5], l2, v2))
+    d_l = np.zeros(20); d_r = np.zeros(20)
+    d_l[lhs_l] = lhs_v
+    d_r[rhs_l] = rhs_v
+    assert np.allclose(d_l, d_r, rtol=0, atol=1e-13)

@@ -99,3 +99,16 @@ def test_limits():
     # empty tensors are fine
     lo, vo = oracle.permute_wide([1 << 40, 1 << 40], [1, 0], [0, 1], np.zeros((0, 2), np.uint64), np.zeros(0))
     assert lo.shape == (0, 2) and vo.shape == (0,)
+
+
+def test_relinearisations_compose():
+    """Re-linearising from order a to b and then from b to c equals going
+    from a to c directly."""
+    dims = [(1 << 37) + 5, (1 << 33) - 1, 123_457, 77]
+    T = synth.wide_tensor(dims, [3, 2, 1, 0], 2000, seed=5)
+    a, b, c = [3, 2, 1, 0], [1, 3, 0, 2], [2, 0, 3, 1]
+    ab = oracle.relinearise_wide(dims, a, b, T["liv"])
+    abc = oracle.relinearise_wide(dims, b, c, ab)
+    ac = oracle.relinearise_wide(dims, a, c, T["liv"])
+    assert np.array_equal(abc, ac)
+    assert not np.array_equal(ab, T["liv"])
