@@ -56,8 +56,6 @@ constexpr int kMergeRuns = 8;               // runs a lane merges at once
 // header counter slots
 constexpr int kCtrDcsr = 10;
 constexpr int kCtrScan = 11;
-constexpr int kCtrChunk = 12;
-constexpr int kCtrReduce = 13;
 
 enum Lookup { kLookupCsr = 0, kLookupDcsr = 1 };
 
@@ -266,10 +264,6 @@ __device__ int cta_sort(uint64_t *k0, double *v0, uint64_t *k1, double *v1, int6
         cur ^= 1;
     }
     return cur;
-}
-
-__device__ __forceinline__ int bits_for(uint64_t range) {   // ceil(log2(range)), range >= 1
-    return range <= 1 ? 0 : 64 - __clzll((long long)(range - 1));
 }
 
 // ------------------------------------------------------------------------
