@@ -18,7 +18,7 @@ import statistics
 
 import torch
 
-from . import ALG_NAMES, ContractPlan, LcoTensor
+from . import ContractPlan, LcoTensor
 
 ROW_ALGS = ("CSR", "CSRNA", "DCSR", "SOP")
 COL_ALGS = ("CSC", "CSCNA", "DCSC")

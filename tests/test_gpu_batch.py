@@ -1,7 +1,6 @@
 """Batched contractions: every problem of a batch equals the same problem
 run alone (bit for bit: the same kernels and plan), and a sample matches the
 oracle; the batch replays correctly from a captured CUDA graph."""
-import numpy as np
 import pytest
 import torch
 

@@ -2,7 +2,6 @@
 against the oracle, on every branch of Table 4."""
 import numpy as np
 import pytest
-import torch
 
 import paper_1802_02619_gb300 as lco
 import synth

@@ -2,7 +2,6 @@
 alone through lco_contract (bit for bit: same plan and kernels, summation in
 generation order), a sample matches the oracle, memory comes back on
 release, and a request that cannot fit fails with LCO_ERR_ADMISSION."""
-import numpy as np
 import pytest
 import torch
 

@@ -1,7 +1,6 @@
 """Pins for the oracle's contraction with entrywise (shared, unsummed) modes
 (Sec. 5: such a product is one matrix product per value of the shared
 indices): dense einsum brute force on tiny tensors, and slice by slice."""
-import itertools
 
 import numpy as np
 import pytest
