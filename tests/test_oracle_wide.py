@@ -112,3 +112,19 @@ def test_relinearisations_compose():
     ac = oracle.relinearise_wide(dims, a, c, T["liv"])
     assert np.array_equal(abc, ac)
     assert not np.array_equal(ab, T["liv"])
+
+
+def test_wide_generator_is_seeded_sorted_and_in_range():
+    dims = [(1 << 40) + 11, (1 << 41) - 9, 9_999_991]
+    total = dims[0] * dims[1] * dims[2]
+    T1 = synth.wide_tensor(dims, [2, 1, 0], 20_000, seed=8)
+    T2 = synth.wide_tensor(dims, [2, 1, 0], 20_000, seed=8)
+    assert np.array_equal(T1["liv"], T2["liv"]) and np.array_equal(T1["val"], T2["val"])
+    x = _ints(T1["liv"])
+    assert len(x) == 20_000 and all(a < b for a, b in zip(x, x[1:])) and 0 <= x[0] and x[-1] < total
+    # uniform over the index space: the high words spread over their range
+    hi = T1["liv"][:, 1].astype(np.float64)
+    assert hi.max() > 0.9 * (total >> 64) and hi.min() < 0.1 * (total >> 64)
+    # a product that fits 64 bits gives high words of zero
+    S = synth.wide_tensor([1000, 1000], [1, 0], 500, seed=9)
+    assert not S["liv"][:, 1].any() and S["liv"][:, 0].max() < 1_000_000
