@@ -153,6 +153,37 @@ def permute_wide(dims, sig_old, sig_new, liv, val):
     return lo, vo
 
 
+def contract_wide(A, B, modes_a, modes_b):
+    """Contraction by definition with wide (128-bit) LIVs: A and B are dicts
+    with dims, sig, liv ((nnz, 2) uint64, low word first) and val.  Returns
+    (liv_c (nnz_c, 2) uint64, val_c, abs_c), C row-major over (A free modes,
+    B free modes)."""
+    lib = _load()
+    da, sa, la, va = _i64(A["dims"]), _i32(A["sig"]), _u64pairs(A["liv"]), _f64(A["val"])
+    db, sb, lb, vb = _i64(B["dims"]), _i32(B["sig"]), _u64pairs(B["liv"]), _f64(B["val"])
+    ma, mb = _i32(modes_a), _i32(modes_b)
+    nnz_c = ctypes.c_int64()
+    pl, pv, pa = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    rc = lib.lco_oracle_contract_wide(
+        ctypes.c_int32(len(da)), _p(da), _p(sa), ctypes.c_int64(la.shape[0]), _p(la), _p(va),
+        ctypes.c_int32(len(db)), _p(db), _p(sb), ctypes.c_int64(lb.shape[0]), _p(lb), _p(vb),
+        ctypes.c_int32(len(ma)), _p(ma), _p(mb),
+        ctypes.byref(nnz_c), ctypes.byref(pl), ctypes.byref(pv), ctypes.byref(pa))
+    _check(rc, "contract_wide")
+    n = nnz_c.value
+    try:
+        if n == 0:
+            return np.empty((0, 2), np.uint64), np.empty(0, np.float64), np.empty(0, np.float64)
+        liv = np.ctypeslib.as_array(ctypes.cast(pl, ctypes.POINTER(ctypes.c_uint64)), (n, 2)).copy()
+        val = np.ctypeslib.as_array(ctypes.cast(pv, ctypes.POINTER(ctypes.c_double)), (n,)).copy()
+        ab = np.ctypeslib.as_array(ctypes.cast(pa, ctypes.POINTER(ctypes.c_double)), (n,)).copy()
+        return liv, val, ab
+    finally:
+        for p in (pl, pv, pa):
+            if p.value:
+                lib.lco_oracle_free(p)
+
+
 def rp_permute(dims, sig_old, sig_new, liv, val):
     """The RP algorithm of Sec. 4.1 (regions + stable sort on the shaved key)."""
     lib = _load()

@@ -50,12 +50,13 @@
  *                                        (definition: union of entries,
  *                                        values added).
  *   lco_oracle_relinearise_wide /        Sec. 3.1 and Sec. 7 (future work:
- *   lco_oracle_permute_wide              LIVs past 2^63 - 1): the same LIV
- *                                        formula and the same definition of
- *                                        a permutation, with unsigned 128-bit
- *                                        LIVs (dims multiply to at most
- *                                        2^127 - 1); a wide LIV is two
- *                                        uint64 words, low word first.
+ *   lco_oracle_permute_wide /            LIVs past 2^63 - 1): the same LIV
+ *   lco_oracle_contract_wide             formula and the same definitions of
+ *                                        a permutation and a contraction,
+ *                                        with unsigned 128-bit LIVs (dims
+ *                                        multiply to at most 2^127 - 1); a
+ *                                        wide LIV is two uint64 words, low
+ *                                        word first.
  *
  * Parity pins for every function live under tests/ (test_oracle_*.py).
  */
@@ -803,4 +804,168 @@ int lco_oracle_permute_wide(int32_t order, const int64_t *dims, const int32_t *s
     free(newliv);
     free(ki);
     return ORC_OK;
+}
+
+/* Contraction by definition with wide LIVs (no entrywise modes): C's modes
+ * are A's free modes then B's free modes, row-major, and C's LIV range
+ * (the product of those dims) must stay within 2^127 - 1.  Products are
+ * summed per output LIV in generation order (A entries in ascending LIV
+ * order, then B entries of the matching key in ascending LIV order).
+ * liv_c receives 2 * nnz_c words. */
+typedef struct { u128_t key; u128_t liv; int64_t idx; } wbent_t;
+typedef struct { u128_t out; int64_t seq; double v; double a; } wprod_t;
+typedef struct { u128_t liv; int64_t idx; } wa_t;
+
+static int cmp_wbent(const void *pa, const void *pb)
+{
+    const wbent_t *a = (const wbent_t *)pa, *b = (const wbent_t *)pb;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    if (a->liv != b->liv) return a->liv < b->liv ? -1 : 1;
+    return 0;
+}
+
+static int cmp_wprod(const void *pa, const void *pb)
+{
+    const wprod_t *a = (const wprod_t *)pa, *b = (const wprod_t *)pb;
+    if (a->out != b->out) return a->out < b->out ? -1 : 1;
+    if (a->seq != b->seq) return a->seq < b->seq ? -1 : 1;
+    return 0;
+}
+
+static int cmp_wa(const void *pa, const void *pb)
+{
+    const wa_t *a = (const wa_t *)pa, *b = (const wa_t *)pb;
+    if (a->liv != b->liv) return a->liv < b->liv ? -1 : 1;
+    return 0;
+}
+
+static void wide_coords(int order, const int64_t *dims, const int32_t *sig, u128_t liv, u128_t *coord)
+{
+    for (int t = 0; t < order; ++t) {
+        const u128_t d = (u128_t)dims[sig[t]];
+        coord[sig[t]] = liv % d;
+        liv /= d;
+    }
+}
+
+int lco_oracle_contract_wide(int32_t order_a, const int64_t *dims_a, const int32_t *sig_a,
+                             int64_t nnz_a, const uint64_t *liv_a, const double *val_a,
+                             int32_t order_b, const int64_t *dims_b, const int32_t *sig_b,
+                             int64_t nnz_b, const uint64_t *liv_b, const double *val_b,
+                             int32_t ncontract, const int32_t *modes_a, const int32_t *modes_b,
+                             int64_t *nnz_c, uint64_t **liv_c, double **val_c, double **abs_c)
+{
+    const u128_t lim = ((u128_t)1 << 127) - 1;
+    int is_con_a[ORC_MAX_ORDER] = {0}, is_con_b[ORC_MAX_ORDER] = {0};
+    u128_t tot_a, tot_b, m = 1, n = 1;
+    u128_t coord[ORC_MAX_ORDER];
+    int rc;
+    wbent_t *bs = NULL;
+    wa_t *as = NULL;
+    wprod_t *prods = NULL;
+    int64_t nprod = 0, cap = 0;
+
+    *nnz_c = 0; *liv_c = NULL; *val_c = NULL; *abs_c = NULL;
+    if (!valid_sig(order_a, sig_a) || !valid_sig(order_b, sig_b)) return ORC_ERR_INVALID;
+    if ((rc = checked_product_wide(order_a, dims_a, &tot_a)) != ORC_OK) return rc;
+    if ((rc = checked_product_wide(order_b, dims_b, &tot_b)) != ORC_OK) return rc;
+    if (ncontract < 0 || ncontract > order_a || ncontract > order_b) return ORC_ERR_INVALID;
+    for (int c = 0; c < ncontract; ++c) {
+        int ma = modes_a[c], mb = modes_b[c];
+        if (ma < 0 || ma >= order_a || mb < 0 || mb >= order_b) return ORC_ERR_INVALID;
+        if (is_con_a[ma] || is_con_b[mb]) return ORC_ERR_INVALID;
+        if (dims_a[ma] != dims_b[mb]) return ORC_ERR_INVALID;
+        is_con_a[ma] = 1; is_con_b[mb] = 1;
+    }
+    if ((order_a - ncontract) + (order_b - ncontract) > ORC_MAX_ORDER) return ORC_ERR_INVALID;
+    for (int t = 0; t < order_a; ++t) if (!is_con_a[t]) m *= (u128_t)dims_a[t];
+    for (int t = 0; t < order_b; ++t) if (!is_con_b[t]) n *= (u128_t)dims_b[t];
+    if (m > lim / n) return ORC_ERR_OVERFLOW;
+    if (nnz_a == 0 || nnz_b == 0) return ORC_OK;
+
+    bs = (wbent_t *)malloc(sizeof(wbent_t) * (size_t)nnz_b);
+    as = (wa_t *)malloc(sizeof(wa_t) * (size_t)nnz_a);
+    if (!bs || !as) { rc = ORC_ERR_OOM; goto done; }
+    /* B entries keyed by their contracted coordinates (pairing order, the
+     * first pair most significant), then by B's own LIV */
+    for (int64_t e = 0; e < nnz_b; ++e) {
+        const u128_t lv = ((u128_t)liv_b[2 * e + 1] << 64) | liv_b[2 * e];
+        u128_t key = 0;
+        if (lv >= tot_b) { rc = ORC_ERR_INVALID; goto done; }
+        wide_coords(order_b, dims_b, sig_b, lv, coord);
+        for (int c = 0; c < ncontract; ++c) key = key * (u128_t)dims_b[modes_b[c]] + coord[modes_b[c]];
+        bs[e].key = key; bs[e].liv = lv; bs[e].idx = e;
+    }
+    qsort(bs, (size_t)nnz_b, sizeof(wbent_t), cmp_wbent);
+    for (int64_t e = 0; e < nnz_a; ++e) {
+        as[e].liv = ((u128_t)liv_a[2 * e + 1] << 64) | liv_a[2 * e];
+        as[e].idx = e;
+        if (as[e].liv >= tot_a) { rc = ORC_ERR_INVALID; goto done; }
+    }
+    qsort(as, (size_t)nnz_a, sizeof(wa_t), cmp_wa);
+
+    for (int64_t q = 0; q < nnz_a; ++q) {
+        const int64_t e = as[q].idx;
+        u128_t key = 0, row = 0;
+        int64_t lo, hi;
+        wide_coords(order_a, dims_a, sig_a, as[q].liv, coord);
+        for (int c = 0; c < ncontract; ++c) key = key * (u128_t)dims_a[modes_a[c]] + coord[modes_a[c]];
+        for (int t = 0; t < order_a; ++t) if (!is_con_a[t]) row = row * (u128_t)dims_a[t] + coord[t];
+        lo = 0; hi = nnz_b;
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (bs[mid].key < key) lo = mid + 1; else hi = mid;
+        }
+        for (int64_t j = lo; j < nnz_b && bs[j].key == key; ++j) {
+            u128_t cb[ORC_MAX_ORDER];
+            u128_t col = 0;
+            const double av = val_a[e], bv = val_b[bs[j].idx];
+            wide_coords(order_b, dims_b, sig_b, bs[j].liv, cb);
+            for (int t = 0; t < order_b; ++t) if (!is_con_b[t]) col = col * (u128_t)dims_b[t] + cb[t];
+            if (nprod == cap) {
+                int64_t ncap = cap ? cap * 2 : 1024;
+                wprod_t *np = (wprod_t *)realloc(prods, sizeof(wprod_t) * (size_t)ncap);
+                if (!np) { rc = ORC_ERR_OOM; goto done; }
+                prods = np; cap = ncap;
+            }
+            prods[nprod].out = row * n + col;
+            prods[nprod].seq = nprod;
+            prods[nprod].v = av * bv;
+            prods[nprod].a = fabs(av) * fabs(bv);
+            ++nprod;
+        }
+    }
+    qsort(prods, (size_t)nprod, sizeof(wprod_t), cmp_wprod);
+    {
+        int64_t nc = 0;
+        for (int64_t i = 0; i < nprod; ++i)
+            if (i == 0 || prods[i].out != prods[i - 1].out) ++nc;
+        *liv_c = (uint64_t *)malloc(sizeof(uint64_t) * 2 * (size_t)(nc ? nc : 1));
+        *val_c = (double *)malloc(sizeof(double) * (size_t)(nc ? nc : 1));
+        *abs_c = (double *)malloc(sizeof(double) * (size_t)(nc ? nc : 1));
+        if (!*liv_c || !*val_c || !*abs_c) { rc = ORC_ERR_OOM; goto done; }
+        nc = -1;
+        for (int64_t i = 0; i < nprod; ++i) {
+            if (i == 0 || prods[i].out != prods[i - 1].out) {
+                ++nc;
+                (*liv_c)[2 * nc] = (uint64_t)prods[i].out;
+                (*liv_c)[2 * nc + 1] = (uint64_t)(prods[i].out >> 64);
+                (*val_c)[nc] = 0.0;
+                (*abs_c)[nc] = 0.0;
+            }
+            (*val_c)[nc] += prods[i].v;
+            (*abs_c)[nc] += prods[i].a;
+        }
+        *nnz_c = nc + 1;
+    }
+    rc = ORC_OK;
+done:
+    if (rc != ORC_OK) {
+        free(*liv_c); free(*val_c); free(*abs_c);
+        *liv_c = NULL; *val_c = NULL; *abs_c = NULL; *nnz_c = 0;
+    }
+    free(bs);
+    free(as);
+    free(prods);
+    return rc;
 }

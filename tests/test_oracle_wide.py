@@ -128,3 +128,68 @@ def test_wide_generator_is_seeded_sorted_and_in_range():
     # a product that fits 64 bits gives high words of zero
     S = synth.wide_tensor([1000, 1000], [1, 0], 500, seed=9)
     assert not S["liv"][:, 1].any() and S["liv"][:, 0].max() < 1_000_000
+
+
+def _wide_of(T):
+    liv = np.asarray(T["liv"], dtype=np.int64)
+    return {"dims": list(T["dims"]), "sig": list(T["sig"]), "val": T["val"],
+            "liv": np.stack([liv.view(np.uint64), np.zeros_like(liv).view(np.uint64)], 1)}
+
+
+def _rand64(dims, nnz, seed):
+    rng = np.random.default_rng(seed)
+    total = int(np.prod(dims))
+    liv = np.sort(rng.choice(total, size=min(nnz, total), replace=False)).astype(np.int64)
+    return {"dims": list(dims), "sig": list(range(len(dims) - 1, -1, -1)), "liv": liv,
+            "val": rng.uniform(-1, 1, liv.shape[0])}
+
+
+@pytest.mark.parametrize("ma,mb", [([1], [0]), ([0], [1]), ([1, 2], [0, 1]), ([2, 0], [1, 2]), ([], [])])
+def test_wide_contraction_equals_the_64_bit_oracle_where_both_apply(ma, mb):
+    A = _rand64([6, 5, 4], 60, 31)
+    B = _rand64([5, 4, 7], 70, 32)
+    if ma == [0]:
+        B = _rand64([5, 6, 3], 50, 33)
+    if ma == [2, 0]:
+        B = _rand64([3, 4, 6], 40, 34)
+    l64, v64, a64 = oracle.contract(A, B, ma, mb)
+    lw, vw, aw = oracle.contract_wide(_wide_of(A), _wide_of(B), ma, mb)
+    assert _ints(lw) == [int(x) for x in l64]
+    assert np.array_equal(vw, v64) and np.array_equal(aw, a64)
+
+
+def test_wide_contraction_with_a_large_leading_mode():
+    """A gains a leading free mode of size 2^62 + 3 (four large coordinates
+    x), so C's LIVs pass 2^64.  Per value of x, C's slice is the 64-bit
+    oracle's product of A's slice with B."""
+    X = (1 << 62) + 3
+    A = _rand64([7, 9], 40, 41)            # (i, k)
+    B = _rand64([9, 6], 30, 42)            # (k, j)
+    rng = np.random.default_rng(43)
+    xs = [int(v) << 41 for v in np.sort(rng.choice(1 << 20, size=4, replace=False))]   # four large coordinates
+    x_of = rng.integers(0, 4, size=len(A["liv"]))
+    wide_a = sorted((int(xs[x]) * 63 + int(l), float(v)) for x, l, v in zip(x_of, A["liv"], A["val"]))
+    Aw = {"dims": [X, 7, 9], "sig": [2, 1, 0], "liv": _pairs([w for w, _ in wide_a]),
+          "val": np.array([v for _, v in wide_a])}
+    lw, vw, _ = oracle.contract_wide(Aw, _wide_of(B), [2], [0])
+    expect = []
+    for x in range(4):
+        sel = x_of == x
+        if not sel.any():
+            continue
+        As = {"dims": [7, 9], "sig": [1, 0], "liv": A["liv"][sel], "val": A["val"][sel]}
+        l64, v64, _ = oracle.contract(As, B, [1], [0])
+        expect += [(int(xs[x]) * 42 + int(l), float(v)) for l, v in zip(l64, v64)]
+    expect.sort()
+    got = list(zip(_ints(lw), vw.tolist()))
+    assert [g[0] for g in got] == [e[0] for e in expect]
+    assert np.allclose([g[1] for g in got], [e[1] for e in expect], rtol=0, atol=1e-15)
+    assert max(g[0] for g in got) >= 1 << 64
+
+
+def test_wide_contraction_output_limit():
+    # C's modes (2^62, 8) x (2^63 - 1) span ~2^128: past the wide limit
+    A = {"dims": [1 << 62, 8, 1 << 40], "sig": [2, 1, 0], "liv": _pairs([5]), "val": np.ones(1)}
+    B = {"dims": [1 << 40, (1 << 63) - 1], "sig": [1, 0], "liv": _pairs([7]), "val": np.ones(1)}
+    with pytest.raises(oracle.OracleError):
+        oracle.contract_wide(A, B, [2], [0])
