@@ -541,7 +541,8 @@ def run_e2e(step, device, K, world):
     dt = reduce_max(dt, world)
     # the last result read back equals the device-timed step's output
     last = outs_h[(K - 1) % 2]
-    assert torch.equal(last[0], step.out_liv.cpu()), "e2e result differs"
+    assert torch.equal(last[0], step.out_liv.cpu()), "e2e result LIVs differ"
+    assert torch.equal(last[1].view(torch.int64), step.out_val.cpu().view(torch.int64)), "e2e result values differ"
     return {"value": round(world * step.units * K / dt / 1e9, 4), "unit": UNIT, "steps": K,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": round(dt / K * 1e3, 4),

@@ -170,13 +170,28 @@ int32_t lco_radix_permute(const lco_shape *t, const int32_t *new_sig,
  *   - Every call on a device shares the one array: calls whose device
  *     work overlaps (different streams, or different host threads) race
  *     and corrupt each other's results.  Serialise them.
- *   - Inputs and outputs are device arrays as for lco_radix_permute.
- *     Device-side wait timeouts are not reported by this entry point.
+ *   - The device address is cached per device ordinal for the life of
+ *     the process: after cudaDeviceReset (or a release and re-creation of
+ *     the device's primary context) the cached address is stale, so do not
+ *     call this entry point on that device again in the same process.
+ *   - Inputs and outputs are device arrays as for lco_radix_permute.  The
+ *     return value covers the host-side checks and launches only; the
+ *     device status of the last call on a device is read with
+ *     lco_radix_permute_static_status.  When it is not LCO_OK the output
+ *     of that call is undefined.
  * Errors: LCO_ERR_INVALID, LCO_ERR_OVERFLOW, LCO_ERR_TOO_LARGE,
  * LCO_ERR_CUDA. */
 int32_t lco_radix_permute_static(const lco_shape *t, const int32_t *new_sig,
                                  const int64_t *liv_in, const double *val_in,
                                  int64_t *liv_out, double *val_out, void *stream);
+
+/* Device status of the last lco_radix_permute_static call on the current
+ * device: synchronises `stream` (the stream that call used), then copies the
+ * status word of the fixed scratch array's header to *status (LCO_OK, or a
+ * device error such as LCO_ERR_TIMEOUT; each call clears it first).  It
+ * allocates nothing.  No paper counterpart.
+ * Errors: LCO_ERR_INVALID (null status), LCO_ERR_CUDA. */
+int32_t lco_radix_permute_static_status(int32_t *status, void *stream);
 
 /* ------------------------------------------------------------------ */
 /* Wide LIVs.  Sec. 3.1 limits LIVs to signed 64 bits (dims multiplying */
@@ -415,7 +430,8 @@ int32_t lco_batch_results(const lco_batch *batch, const int64_t *caps, const voi
  * (about one second), records LCO_ERR_TIMEOUT in the status word and lets
  * its kernel finish, so a lost producer never hangs the GPU.  This call
  * makes both kinds of wait run out on purpose: with the budget lowered to
- * budget_cycles (for this test kernel only), one warp looks back over tiles
+ * budget_cycles (an argument of this test kernel only: kernels running at
+ * the same time on other streams keep the full budget), one warp looks back over tiles
  * that never publish and one thread waits on an mbarrier phase that never
  * completes.  scratch: device memory of at least 512 bytes (any content).
  * Synchronises `stream`; *lookback_status and *mbarrier_status receive the

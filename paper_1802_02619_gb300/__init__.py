@@ -124,6 +124,7 @@ _SIGNATURES = {
                            ctypes.c_void_p], ctypes.c_int32),
     "lco_radix_permute_static": ([ctypes.POINTER(Shape), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "lco_radix_permute_static_status": ([ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p], ctypes.c_int32),
     "lco_relinearise_wide": ([ctypes.POINTER(Shape), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.c_void_p], ctypes.c_int32),
     "lco_radix_permute_wide_info": ([ctypes.POINTER(Shape), ctypes.c_void_p, ctypes.POINTER(RpWideInfo)],

@@ -56,13 +56,14 @@ void timing_end(cudaStream_t s) {
 
 // Wait self-test: one warp looks back over predecessors that never publish,
 // then one thread waits on an mbarrier phase that never completes.  Both
-// waits give up after g_spin_budget cycles and record LCO_ERR_TIMEOUT.
-__global__ void k_selftest_wait(uint64_t *state, int32_t *status) {
+// waits give up after `budget` cycles (a kernel argument, so no other
+// kernel's budget changes) and record LCO_ERR_TIMEOUT.
+__global__ void k_selftest_wait(uint64_t *state, int32_t *status, long long budget) {
     __shared__ uint64_t s_bar;
-    lookback_warp(state, 8, status);             // tiles 0..7 never publish
+    lookback_warp(state, 8, status, budget);     // tiles 0..7 never publish
     if (threadIdx.x == 0) {
         mbar_init(&s_bar, 1);                    // nothing arrives
-        if (!mbar_wait_bounded(&s_bar, 0)) set_error(status + 1, LCO_ERR_TIMEOUT);
+        if (!mbar_wait_bounded(&s_bar, 0, budget)) set_error(status + 1, LCO_ERR_TIMEOUT);
     }
 }
 
@@ -77,14 +78,9 @@ int32_t lco_selftest_wait(void *scratch, int64_t budget_cycles, int32_t *lookbac
     char *w = reinterpret_cast<char *>(scratch);
     uint64_t *state = reinterpret_cast<uint64_t *>(w);
     int32_t *status = reinterpret_cast<int32_t *>(w + 256);
-    const long long budget = budget_cycles, restore = lco::kSpinBudgetCycles;
     if (cudaMemsetAsync(w, 0, 512, s) != cudaSuccess) return LCO_ERR_CUDA;
-    if (cudaMemcpyToSymbolAsync(lco::g_spin_budget, &budget, sizeof(budget), 0, cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
-        return LCO_ERR_CUDA;
-    lco::k_selftest_wait<<<1, 32, 0, s>>>(state, status);
+    lco::k_selftest_wait<<<1, 32, 0, s>>>(state, status, (long long)budget_cycles);
     const cudaError_t le = cudaGetLastError();
-    cudaMemcpyToSymbolAsync(lco::g_spin_budget, &restore, sizeof(restore), 0, cudaMemcpyHostToDevice, s);
     int32_t st[2] = {0, 0};
     if (le != cudaSuccess || cudaMemcpyAsync(st, status, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)

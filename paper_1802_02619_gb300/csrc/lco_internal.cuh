@@ -13,11 +13,10 @@ constexpr int kMaxOrder = LCO_MAX_ORDER;
 constexpr int kWsHeaderBytes = 256;
 // Bounded device waits: a look-back spin gives up after this many SM clock
 // cycles (about one second at 2 GHz), records LCO_ERR_TIMEOUT and continues
-// with a zero contribution so that the kernel always terminates.
+// with a zero contribution so that the kernel always terminates.  The wait
+// helpers take the budget as an argument (default kSpinBudgetCycles); only
+// the wait self-test passes a smaller one, to its own kernel.
 constexpr long long kSpinBudgetCycles = 2000000000LL;
-// The budget in force (per translation unit); the wait self-test lowers it
-// to make a wait run out on purpose.
-static __device__ long long g_spin_budget = kSpinBudgetCycles;
 
 // ---------------------------------------------------------------------------
 // Unsigned 64-bit division by an invariant divisor.
@@ -155,7 +154,7 @@ __device__ __forceinline__ uint64_t lb_load(const uint64_t *p) {
 constexpr int kLookbackBatch = 8;
 
 __device__ __forceinline__ uint64_t lookback(const uint64_t *state, int64_t tile, int64_t stride,
-                                             int32_t *status) {
+                                             int32_t *status, long long budget = kSpinBudgetCycles) {
     uint64_t excl = 0;
     const long long t0 = clock64();
     for (int64_t t = tile - 1; t >= 0; t -= kLookbackBatch) {
@@ -166,7 +165,7 @@ __device__ __forceinline__ uint64_t lookback(const uint64_t *state, int64_t tile
         for (int i = 0; i < kLookbackBatch; ++i) {
             if (t - i < 0) return excl;
             while ((s[i] >> 62) == 0) {
-                if (clock64() - t0 > g_spin_budget) {
+                if (clock64() - t0 > budget) {
                     set_error(status, LCO_ERR_TIMEOUT);
                     return excl;
                 }
@@ -193,7 +192,8 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
     return v;
 }
 
-__device__ __forceinline__ uint64_t lookback_warp(const uint64_t *state, int64_t tile, int32_t *status) {
+__device__ __forceinline__ uint64_t lookback_warp(const uint64_t *state, int64_t tile, int32_t *status,
+                                                  long long budget = kSpinBudgetCycles) {
     const int lane = threadIdx.x & 31;
     uint64_t excl = 0;
     const long long t0 = clock64();
@@ -218,7 +218,7 @@ __device__ __forceinline__ uint64_t lookback_warp(const uint64_t *state, int64_t
                     break;
                 }
                 // warp-uniform decision, so that all lanes leave together
-                if (__any_sync(0xffffffffu, clock64() - t0 > g_spin_budget)) {
+                if (__any_sync(0xffffffffu, clock64() - t0 > budget)) {
                     if (lane == 0) set_error(status, LCO_ERR_TIMEOUT);
                     return excl;
                 }
@@ -276,10 +276,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 
 // Waits for the phase with the given parity; false once the spin budget is
 // spent (the caller records the error and leaves).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  long long budget = kSpinBudgetCycles) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > g_spin_budget) return false;
+        if (clock64() - t0 > budget) return false;
     }
     return true;
 }

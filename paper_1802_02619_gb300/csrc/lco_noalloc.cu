@@ -73,4 +73,15 @@ int32_t lco_radix_permute_static(const lco_shape *t, const int32_t *new_sig, con
     return e == cudaSuccess ? LCO_OK : LCO_ERR_CUDA;
 }
 
+int32_t lco_radix_permute_static_status(int32_t *status, void *stream) {
+    if (!status) return LCO_ERR_INVALID;
+    void *scratch = nullptr;
+    int32_t rc = static_scratch(&scratch);
+    if (rc != LCO_OK) return rc;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return LCO_ERR_CUDA;
+    // the status word is the first field of the header at the array's start
+    if (cudaMemcpy(status, scratch, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) return LCO_ERR_CUDA;
+    return LCO_OK;
+}
+
 }  // extern "C"

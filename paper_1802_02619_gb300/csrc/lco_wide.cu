@@ -173,6 +173,10 @@ int32_t wide_plan(const lco_shape *t, const int32_t *new_sig, WidePlan *out) {
         for (int i = p.s.t_low; i < N; ++i) range *= (u128)(uint64_t)t->dims[new_sig[i]];
         int bits = 0;
         while (bits < 127 && ((u128)1 << bits) < range) ++bits;
+        // A key range of 1 (every new-order mode from t_low up has dim 1)
+        // still takes one chunk: its single pass is constant and becomes the
+        // engine's copy, which writes the positions the gather reads.
+        if (bits < 1) bits = 1;
         p.key_bits = bits;
         p.chunks = (bits + kWideChunkBits - 1) / kWideChunkBits;
         for (int c = 0; c < p.chunks; ++c) {

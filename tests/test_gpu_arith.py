@@ -69,22 +69,31 @@ def test_add_cancellation_keeps_explicit_zeros():
 
 
 def _oracle_chain(N):
+    """The Eq. 4 chain by the oracle, with the per-entry bound sum |a||b|
+    of each term carried through the same permutation and addition."""
     d, dl = synth.fd_matrix(N), synth.kronecker_delta(N)
     rm = [3, 2, 1, 0]
     by = dict(zip(("liv", "val"), oracle.contract(d, dl, [], [])[:2]), dims=[N] * 4, sig=rm)
-    cy = dict(zip(("liv", "val"), oracle.contract(by, d, [1], [0])[:2]), dims=[N] * 4, sig=rm)
-    pl, pv = oracle.permute([N] * 4, [2, 3, 0, 1], rm, cy["liv"], cy["val"])
+    cl, cv, cab = oracle.contract(by, d, [1], [0])
+    cy = {"liv": cl, "val": cv, "dims": [N] * 4, "sig": rm}
+    pl, pv = oracle.permute([N] * 4, [2, 3, 0, 1], rm, cl, cv)
+    pl2, pab = oracle.permute([N] * 4, [2, 3, 0, 1], rm, cl, cab)
+    assert np.array_equal(pl, pl2)
     al, av = oracle.add(1.0, cy, 1.0, {"liv": pl, "val": pv})
-    return al, av
+    bl, bab = oracle.add(1.0, {"liv": cl, "val": cab}, 1.0, {"liv": pl, "val": pab})
+    assert np.array_equal(al, bl)
+    return al, av, bab
 
 
 @pytest.mark.parametrize("N", [15, 31])
 def test_laplacian_chain_matches_oracle(N):
     a = combinatorial_laplacian(dev(synth.fd_matrix(N)), dev(synth.kronecker_delta(N)))
-    rl, rv = _oracle_chain(N)
+    rl, rv, rab = _oracle_chain(N)
     gl, gv = _host(a)
     assert np.array_equal(gl, rl)
-    assert np.allclose(gv, rv, rtol=0, atol=1e-12)
+    # each term within 1e-13 sum |a||b| of its products; the sum adds both bounds
+    err = np.abs(gv - rv)
+    assert np.all(err <= 1e-13 * rab), f"worst {err.max()}"
 
 
 @pytest.mark.parametrize("N", [31, 2047])

@@ -54,6 +54,16 @@ def test_ragged_sizes(nnz):
     _check_permute(WIDE, [3, 2, 1, 0], [2, 0, 3, 1], nnz, seed=13 + nnz)
 
 
+@pytest.mark.parametrize("dims,nnz", [([4, 1, 1], 3), ([1 << 61, 1 << 62, 1, 1], 30_001)])
+def test_unit_dims_in_the_key(dims, nnz):
+    # the swapped top modes have dim 1: the key range is 1 and the output
+    # is the input order with every LIV unchanged
+    order = len(dims)
+    sig = list(range(order))
+    info = _check_permute(dims, sig, sig[:-2] + [sig[-1], sig[-2]], nnz, seed=18 + order)
+    assert info["n_rearr"] == 1 and info["chunks"] == 1
+
+
 def test_same_order_is_a_copy():
     info = _check_permute(WIDE, [3, 2, 1, 0], [3, 2, 1, 0], 5000, seed=14)
     assert info["n_rearr"] == 0

@@ -185,3 +185,15 @@ def test_wide_limits_and_chunks():
     # the 64-bit entry points still reject such shapes
     with pytest.raises(lco.LcoError):
         lco.radix_permute_info([15, 1 << 61, 1 << 62], [2, 1, 0], [0, 2, 1])
+
+
+def test_wide_key_of_unit_range_still_takes_a_chunk():
+    """Two unit dims swapped above everything else: one rearrangement index
+    (Sec. 4.1) whose key range is 1.  The plan keeps one 1-bit chunk, so
+    the gather reads positions the radix engine wrote."""
+    for dims in ([4, 1, 1], [1 << 61, 1 << 62, 1, 1]):
+        order = len(dims)
+        sig = list(range(order))
+        new_sig = sig[:-2] + [sig[-1], sig[-2]]
+        info = lco.radix_permute_wide_info(dims, sig, new_sig)
+        assert info["n_rearr"] == 1 and info["key_bits"] == 1 and info["chunks"] == 1
