@@ -69,6 +69,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["lco", "reference"], default="lco")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="--case step: skip the C3, C3b, batch and serve measurements after the headline")
     ap.add_argument("--case", choices=["step", "permute", "batch", "serve", "permsweep", "permute_wide"],
                     default="step",
                     help="step: the benchmark workload; permute: a stand-alone radix permutation "
@@ -311,14 +313,18 @@ def load_config(name):
     return cfg, label
 
 
-def run_lco(args):
+def measure_config(name, device, K, warmup, world=1, local=0, max_digit_bits=0, soak_s=0.0):
+    """Device timing of one configuration's step: the step captured in a CUDA
+    graph, K replays each bracketed by events with L2 flushed before it, then
+    a per-kernel timing pass (direct launches, L2 flushed) and a warm-L2
+    replay.  With soak_s > 0 the graph is first replayed for that long under
+    the clock sampler, so that the clock record covers a loaded GPU.  Returns
+    (record, step)."""
     import torch
     import paper_1802_02619_gb300 as lco
-    rank, world, local = dist_setup()
-    device = f"cuda:{local}"
     lib = lco.load()
-    cfg, workload = load_config(args.config)
-    step = ConfigStep(cfg, device, args.max_digit_bits)
+    cfg, workload = load_config(name)
+    step = ConfigStep(cfg, device, max_digit_bits)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
 
@@ -328,7 +334,7 @@ def run_lco(args):
     assert bool((step.out_liv[1:] > step.out_liv[:-1]).all()), "output LIVs not ascending"
 
     # ---- warm-up and graph capture ----
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         step()
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
@@ -340,16 +346,26 @@ def run_lco(args):
         with torch.cuda.graph(graph, stream=side):
             step()
     stream.wait_stream(side)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         flush.zero_()
         graph.replay()
     torch.cuda.synchronize()
 
-    # ---- timed region ----
-    K = args.steps
+    # ---- clock soak and timed region ----
+    clocks = ClockSampler(local) if soak_s > 0 else None
+    soak = None
+    if clocks:
+        clocks.start()
+        t0 = time.perf_counter()
+        nsoak = 0
+        while time.perf_counter() - t0 < soak_s:
+            for _ in range(64):
+                flush.zero_()
+                graph.replay()
+            nsoak += 64
+            torch.cuda.synchronize()
+        soak = {"s": round(time.perf_counter() - t0, 3), "steps": nsoak}
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    clocks = ClockSampler(local)
-    clocks.start()
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -361,7 +377,9 @@ def run_lco(args):
     torch.cuda.synchronize()
     barrier(world)
     wall = time.perf_counter() - t0
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
+    if clk is not None:
+        clk["soak"] = soak
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
     step_sorted = sorted(step_ms)
@@ -416,12 +434,10 @@ def run_lco(args):
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "algorithmic_bytes": alg_bytes}
-
-    out = {
-        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K,
-        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload, "name": args.config, "nnz_a": step.A.nnz, "nnz_b": step.B.nnz,
+    del graph
+    rec = {
+        "value": round(value, 4), "ms_per_step": round(ms_per_step, 5), "steps": K,
+        "config": {"workload": workload, "name": name, "nnz_a": step.A.nnz, "nnz_b": step.B.nnz,
                    "nnz_c": step.nnz_c, "f": step.f, "alg": step.alg, "permuted_keys": step.permuted,
                    "l2": "flushed before every step (256 MiB memset, outside the step events)",
                    "graph": "each step replayed from one CUDA graph", "parallelism": f"replicas x{world}"},
@@ -440,15 +456,69 @@ def run_lco(args):
                       "kernels": {k: {kk: round(vv, 5) for kk, vv in v.items()} for k, v in kernels.items()},
                       "wall_s_timed_region": round(wall, 4)},
     }
+    return rec, step, cfg
+
+
+def run_lco(args):
+    import torch
+    rank, world, local = dist_setup()
+    device = f"cuda:{local}"
+    # the clock record covers at least 1.5 s of replays just before the timed region
+    rec, step, cfg = measure_config(args.config, device, args.steps, args.warmup, world, local,
+                                    args.max_digit_bits, soak_s=1.5)
+    out = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic"}
+    out.update({k: v for k, v in rec.items() if k not in ("value", "ms_per_step", "steps")})
     if not args.no_e2e:
-        out["e2e"] = run_e2e(step, device, min(K, 200), world)
+        out["e2e"] = run_e2e(step, device, min(args.steps, 200), world)
+    del step
+    torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, budget_s=12.0)
+    del cfg
+    if rank == 0 and world == 1 and not args.no_extras:
+        out["extras"] = run_extras(args, device)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_extras(args, device):
+    """The other configurations, measured in the same run on the same GPU:
+    C3 (R-MAT 1e7 per operand, DCSR) and C3b (R-MAT 2^18, CSRNA) as device-
+    timed steps with their dominant kernel's roofline and the oracle beside
+    them; C4 (the 4096-problem batch) and C5 (served requests) against their
+    plain per-call paths.  Each is skipped with its error recorded rather
+    than failing the headline line."""
+    import torch
+    extras = {}
+    K = max(3, min(args.steps, 20))
+    for name in ("C3", "C3b"):
+        try:
+            rec, step, cfg = measure_config(name, device, K, max(args.warmup, 3), max_digit_bits=args.max_digit_bits)
+            del step
+            torch.cuda.empty_cache()
+            if not args.no_cpu_baseline:
+                rec["cpu_baseline"] = cpu_baseline(cfg, budget_s=6.0, all_cores=False)
+            extras[name] = rec
+        except Exception as e:    # recorded, not fatal for the headline
+            extras[name] = {"error": repr(e)[:300]}
+        torch.cuda.empty_cache()
+    try:
+        extras["batch"] = measure_batch(args.count, K, max(args.warmup, 3), args.streams,
+                                        cpu_budget_s=0.0 if args.no_cpu_baseline else 6.0)
+    except Exception as e:
+        extras["batch"] = {"error": repr(e)[:300]}
+    torch.cuda.empty_cache()
+    try:
+        extras["serve"] = measure_serve(min(args.requests, 4000), args.slots, args.workers)
+    except Exception as e:
+        extras["serve"] = {"error": repr(e)[:300]}
+    torch.cuda.empty_cache()
+    return extras
 
 
 def algorithmic_bytes(kernel, step):
@@ -549,26 +619,76 @@ def run_e2e(step, device, K, world):
             "pipelined": "copy-in of step i+1 and copy-out of step i-1 overlap step i's compute"}
 
 
-def cpu_baseline(cfg, budget_s=12.0):
-    """The oracle as it stands (single-threaded C) on this host: whole
-    workload steps (contraction + permutation) until the budget is used."""
+def _rows_sample(A, frac):
+    """The leading rows of A (A is stored with its row modes most
+    significant, so a prefix of its index space is a set of leading rows)."""
+    if frac >= 1.0:
+        return A
+    total = int(np.prod(np.asarray(A["dims"], dtype=np.float64)))
+    keep = A["liv"] < int(frac * total)
+    return {"dims": A["dims"], "sig": A["sig"], "liv": A["liv"][keep], "val": A["val"][keep]}
+
+
+def _oracle_step(cfg):
+    """One step of the oracle (contraction, then the product's permutation
+    when the configuration has one) on a given A; returns (seconds, units)."""
     import oracle
-    A, B = cfg["A"], cfg["B"]
-    times, units = [], None
-    t_start = time.perf_counter()
-    while True:
+    B = cfg["B"]
+
+    def one(As):
         t0 = time.perf_counter()
-        liv, val, _ = oracle.contract(A, B, cfg["modes_a"], cfg["modes_b"])
+        liv, val, _ = oracle.contract(As, B, cfg["modes_a"], cfg["modes_b"])
         if "permute_sig" in cfg:
             cd = c_dims_of(cfg)
             oracle.permute(cd, list(range(len(cd) - 1, -1, -1)), cfg["permute_sig"], liv, val)
-        times.append(time.perf_counter() - t0)
-        units = len(A["liv"]) + len(B["liv"]) + len(liv)
+        return time.perf_counter() - t0, len(As["liv"]) + len(B["liv"]) + len(liv)
+    return one
+
+
+def cpu_baseline(cfg, budget_s=12.0, all_cores=True):
+    """The oracle as it stands (single-threaded C) on this host, on a
+    bounded sample of the workload: whole steps when one takes at most a
+    third of the budget, else the leading rows of A sized from two probes
+    (1% and 4% of the rows) so that a step takes about a third of it.
+    With all_cores, also `cores` copies of the same step run at once (one
+    host thread each; the C oracle runs outside the interpreter lock): the
+    host's aggregate oracle throughput."""
+    one = _oracle_step(cfg)
+    A = cfg["A"]
+    # step time ~ fixed (B's bucketing) + frac * per-row part: two probes
+    t1, _ = one(_rows_sample(A, 0.01))
+    t4, _ = one(_rows_sample(A, 0.04))
+    t_var = max((t4 - t1) / 0.03, 1e-6)
+    t_fix = max(t1 - 0.01 * t_var, 0.0)
+    est_full = t_fix + t_var
+    frac = 1.0 if est_full <= budget_s / 3 else max(0.01, (budget_s / 3 - t_fix) / t_var)
+    As = _rows_sample(A, frac)
+    times, units = [], None
+    t_start = time.perf_counter()
+    while True:
+        t, units = one(As)
+        times.append(t)
         if time.perf_counter() - t_start > budget_s or len(times) >= 5:
             break
     t = statistics.median(times)
-    return {"value": round(units / t / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{len(times)} full workload step(s), median {t:.3f} s"}
+    what = "full workload" if frac >= 1.0 else f"leading {frac:.3f} of A's rows (B whole)"
+    out = {"value": round(units / t / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{len(times)} step(s) of the {what}, median {t:.3f} s"}
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    out["host_cores"] = cores
+    if all_cores and cores > 1:
+        import concurrent.futures as cf
+        with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+            t0 = time.perf_counter()
+            res = list(ex.map(lambda _i: one(As), range(cores)))
+            wall = time.perf_counter() - t0
+        u = sum(r[1] for r in res)
+        out["all_cores"] = {"value": round(u / wall / 1e9, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{cores} concurrent copies of one step of the {what}, wall {wall:.3f} s"}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -689,7 +809,15 @@ def batch_workload(count, seed, device):
 
 
 def run_batch_case(args):
-    """C4: args.count problems (1/4 2D FD, 1/4 3D FD, 1/2 R-MAT) contracted
+    """C4 on its own (--case batch): the measure_batch record, printed."""
+    out = measure_batch(args.count, args.steps, args.warmup, args.streams,
+                        cpu_budget_s=0.0 if args.no_cpu_baseline else 12.0, tune=args.tune,
+                        per_kind=args.per_kind)
+    print(json.dumps(out), flush=True)
+
+
+def measure_batch(count, K, warmup, streams, cpu_budget_s=12.0, tune=False, per_kind=False):
+    """C4: `count` problems (1/4 2D FD, 1/4 3D FD, 1/2 R-MAT) contracted
     as one batch replayed from a CUDA graph, against the plain loop of one
     contraction call per problem with a stream synchronisation after each
     (plans and workspaces prepared in advance for both)."""
@@ -697,12 +825,12 @@ def run_batch_case(args):
     import paper_1802_02619_gb300 as lco
     device = "cuda"
     t_gen = time.perf_counter()
-    probs, items = batch_workload(args.count, 100, device)
+    probs, items = batch_workload(count, 100, device)
     t_gen = time.perf_counter() - t_gen
     kinds = {}
     for *_x, kind in probs:
         kinds[kind] = kinds.get(kind, 0) + 1
-    batch = lco.Batch(items, nstreams=args.streams)
+    batch = lco.Batch(items, nstreams=streams)
     batch.run()
     outs = batch.results()
     nnz_in = sum(A.nnz + B.nnz for A, B, _a, _b in items)
@@ -730,10 +858,9 @@ def run_batch_case(args):
     batch.run()
     torch.cuda.synchronize()
     launches_per_step = lco.launch_count() - n0
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         graph.replay()
     torch.cuda.synchronize()
-    K = args.steps
     clocks = ClockSampler(0)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -774,21 +901,28 @@ def run_batch_case(args):
 
     out = {
         "metric": "batched contraction GNNZ/s", "value": round(units / (ms_batch * 1e-3) / 1e9, 4),
-        "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_batch, 4),
+        "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": warmup, "ms_per_step": round(ms_batch, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"batch of {args.count}: fd2d/fd3d self-compositions + R-MAT Eq.14/Eq.16/SOP",
+        "config": {"workload": f"batch of {count}: fd2d/fd3d self-compositions + R-MAT Eq.14/Eq.16/SOP",
                    "kinds": kinds, "algs": algs, "nnz_in": nnz_in, "nnz_c": nnz_c, "f": sum(batch.f),
-                   "streams": args.streams, "l2": "inputs larger than L2 (no flush)",
+                   "streams": streams, "l2": "inputs larger than L2 (no flush)",
                    "graph": "whole batch replayed from one CUDA graph",
                    "gen_s": round(t_gen, 2), "capture_s": round(t_cap, 2)},
         "plain_loop": {"value": round(units / (ms_plain * 1e-3) / 1e9, 4), "unit": UNIT,
                        "ms_per_step": round(ms_plain, 3), "steps": Kp,
                        "what": "one contraction call per problem + stream sync, plans/workspaces prepared"},
         "speedup_vs_plain_loop": round(ms_plain / ms_batch, 3),
+        "roofline": {"bound": "hbm", "kernel": "whole batch (all kernels)",
+                     "achieved": round(16 * units / (ms_batch * 1e-3) / 1e9, 1),
+                     "peak": measured_peak_hbm()[0], "unit": "GB/s",
+                     "frac": round(16 * units / (ms_batch * 1e-3) / 1e9 / measured_peak_hbm()[0], 4),
+                     "traffic": None, "algorithmic_bytes": 16 * units,
+                     "note": "16 B per input and output entry over the batch time (operand permutation "
+                             "passes not counted)"},
         "gpu_launches": int(launches_per_step * K),
         "clocks": clk,
     }
-    if args.tune:
+    if tune:
         # the autotuner's per-signature choices (one sample per group), then
         # the same batch rebuilt with them and replayed the same way
         from paper_1802_02619_gb300.tune import Tuner
@@ -796,7 +930,7 @@ def run_batch_case(args):
         tuner = Tuner(cache_path=None, reps=2)
         choice = tuner.tune_batch(items, per_class=1)
         t_tune = time.perf_counter() - t_tune
-        bt = lco.Batch([it + (alg, bits) for it, (alg, bits) in zip(items, choice)], nstreams=args.streams)
+        bt = lco.Batch([it + (alg, bits) for it, (alg, bits) in zip(items, choice)], nstreams=streams)
         bt.run()
         gt = torch.cuda.CUDAGraph()
         side.wait_stream(stream)
@@ -817,12 +951,12 @@ def run_batch_case(args):
         out["tuned"] = {"value": round(units / (ms_t * 1e-3) / 1e9, 4), "ms_per_step": round(ms_t, 4),
                         "groups": len(tuner.cache), "problems_changed": changed, "tune_s": round(t_tune, 1)}
         del gt, bt
-    if args.per_kind:
+    if per_kind:
         # each kind of problem as a batch of its own (same graph replay)
         per = {}
         for kind in sorted(kinds):
             sel = [it for it, pr in zip(items, probs) if pr[4] == kind]
-            bk = lco.Batch(sel, nstreams=args.streams)
+            bk = lco.Batch(sel, nstreams=streams)
             bk.run()
             u = sum(A.nnz + B.nnz for A, B, _a, _b in sel) + sum(C.nnz for C in bk.results())
             g = torch.cuda.CUDAGraph()
@@ -844,7 +978,7 @@ def run_batch_case(args):
                          "gnnz_s": round(u / (ms * 1e-3) / 1e9, 3)}
             del g, bk
         out["per_kind"] = per
-    if not args.no_cpu_baseline:
+    if cpu_budget_s > 0:
         import oracle
         t_start, done_units, done_t = time.perf_counter(), 0, 0.0
         order = np.random.default_rng(1).permutation(len(probs))
@@ -858,11 +992,11 @@ def run_batch_case(args):
             done_t += time.perf_counter() - t1
             done_units += len(Ah["liv"]) + len(Bh["liv"]) + len(liv)
             nprob += 1
-            if time.perf_counter() - t_start > 12.0:
+            if time.perf_counter() - t_start > cpu_budget_s:
                 break
         out["cpu_baseline"] = {"value": round(done_units / done_t / 1e9, 6), "unit": UNIT, "cores": 1,
                                "kind": "oracle", "sample": f"{nprob} random problems of the batch"}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -878,6 +1012,11 @@ def _percentiles(xs):
 
 
 def run_serve_case(args):
+    """C5 on its own (--case serve): the measure_serve record, printed."""
+    print(json.dumps(measure_serve(args.requests, args.slots, args.workers)), flush=True)
+
+
+def measure_serve(N, slots, workers):
     """C5: 128 resident problems (32 2D FD 16^2..256^2, 32 3D FD, 64 R-MAT
     pairs of 1e3..1e6 non-zeros in the batch forms); requests pick a problem
     uniformly (seed 200).  Saturation throughput from a burst of all
@@ -890,9 +1029,8 @@ def run_serve_case(args):
     device = "cuda"
     probs, items = batch_workload(128, 300, device)
     rng = np.random.default_rng(200)
-    N = args.requests
     pick = rng.integers(0, len(items), size=N)
-    srv = lco.Server(pool_bytes=64 << 30, nslots=args.slots, nworkers=args.workers)
+    srv = lco.Server(pool_bytes=64 << 30, nslots=slots, nworkers=workers)
     handles = [(srv.put(A), srv.put(B)) for A, B, _a, _b in items]
     # units of each problem (nnz_A + nnz_B + nnz_C), from one served run
     units = []
@@ -996,12 +1134,12 @@ def run_serve_case(args):
     out = {"metric": "served contraction GNNZ/s", "value": rates["0.8"]["served"]["gnnz_s"], "unit": UNIT,
            "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "128 resident problems (fd2d, fd3d, R-MAT Eq.14/Eq.16/SOP), uniform picks",
-                      "requests": N, "slots": args.slots, "workers": args.workers, "pool_gb": 64},
+                      "requests": N, "slots": slots, "workers": workers, "pool_gb": 64},
            "saturation": {"served": sat, "plain": plain_sat, "plain_api": api_sat,
                           "served_vs_plain": round(sat["requests_per_s"] / plain_sat["requests_per_s"], 2),
                           "served_vs_plain_api": round(sat["requests_per_s"] / api_sat["requests_per_s"], 2)},
            "poisson": rates, "pool_peak_gb": round(st["pool_peak"] / 2**30, 2)}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 # ---------------------------------------------------------------------------

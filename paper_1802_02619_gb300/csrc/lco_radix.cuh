@@ -2,15 +2,16 @@
 //
 // Used for the permutation of Sec. 4 (keys are re-linearised LIVs shaved by
 // the resting suffix, Sec. 4.1) and for sorting product lists by output LIV
-// (SOP, Sec. 5.2.5).  The input is cut into G contiguous ranges, one CTA
-// each.  One launch reads the keys once and computes every pass's digit
-// histogram, globally and per range.  A pass is then: per-range digit
-// offsets (a scan down each digit column), and a scatter in which each CTA
-// walks its range tile by tile, ranking a tile with warp ballots (a
-// multi-split) and advancing running per-digit offsets, so no CTA waits on
-// another.  Passes after the first non-skipped one histogram the
-// intermediate buffer first.  Passes whose digit is the same for every
-// element are detected on the device and skipped.
+// (SOP, Sec. 5.2.5).  The input's tiles are split into G contiguous ranges
+// of whole tiles, one CTA each.  One launch reads the keys once and computes
+// every pass's digit histogram per range, and marks passes whose digit is
+// the same for every element (those are skipped on the device).  A pass is
+// then: the start of every (digit, range) run in the output -- one exclusive
+// scan over the digit-major count table -- and a scatter in which each CTA
+// walks its range tile by tile, ranking each tile with warp match
+// instructions and advancing running per-digit offsets, so no CTA waits on
+// another.  Passes after the first one that runs histogram the intermediate
+// buffer first.
 #pragma once
 
 #include "lco_internal.cuh"
@@ -46,14 +47,14 @@ struct RadixJob {
     double *dst_val;
     int64_t *tmp_liv;
     double *tmp_val;
-    // workspace pieces
-    uint64_t *ghist;       // [P][NB] global digit counts (left zeroed after use)
-    uint64_t *offs;        // [P][NB] exclusive digit offsets
-    int32_t *active;       // [kMaxPasses] + count at [16]
-    uint32_t *counts_src;  // [P][NB][G] per-range counts over the source order (digit-major)
-    uint32_t *counts_hist; // [NB][G] per-range counts before a later pass (digit-major)
-    uint64_t *roffs;       // [G][NB] start of each (range, digit) in the output of a pass
-    uint32_t *counters;    // [8] "last block" counter
+    // workspace pieces (digit-major tables: entry [d][r] at d * G + r)
+    int32_t *active;       // [kMaxPasses] pass runs (digit not constant) + count at [16]
+    int32_t *cdig;         // [kMaxPasses][G] the one digit of a range, -1 several, -2 empty range
+    uint32_t *counts_src;  // [P][NB][G] per-range counts over the source order
+    uint32_t *counts_hist; // [NB][G] per-range counts before a later pass
+    uint64_t *roffs;       // [NB][G] start of each (digit, range) run in the output of a pass
+    uint64_t *scan_state;  // [kMaxPasses][scan tiles] look-back words of the offset scans
+    uint32_t *counters;    // header counters: [8] upsweep "last block", [12 + p] scan tiles of pass p
     int32_t *status;
 };
 
