@@ -655,6 +655,7 @@ struct HeavyArgs {
     double *sv1;
     uint32_t *ctr;
     WsHeader *hdr;
+    int32_t acc;          // 1: accumulator plans (window or hash), 0: no accumulator (sort)
 };
 
 struct HeavySmem {
@@ -809,9 +810,292 @@ __device__ __forceinline__ void heavy_row(const HeavyArgs &a, HeavySmem &S, int6
     }
 }
 
+// ------------------------------------------------------------------------
+// Heavy rows with an accumulator (Sec. 5.2.2: the row-by-row product keeps
+// an accumulator over the columns of C; Sec. 5.2.3's doubly compressed
+// variant keeps it).  On the GPU the accumulator is a per-row structure in
+// shared memory that maps each product's column to the index of its output
+// entry:
+//   - a dense bitmap over the row's column window [min, max] of the R rows
+//     it meets, when the window has at most kAccWin columns -- the prefix
+//     count of the set bits is the output index, already in column order;
+//   - otherwise an open-addressing hash of the row's distinct columns,
+//     whose distinct columns are then sorted so that each slot takes its
+//     rank.
+// The products are then bucketed by output index, each bucket is put in
+// generation order (L entry order; an entry contributes at most one product
+// per column) and summed from its first product: the same rounding as every
+// other path.  The no-accumulator plans (Sec. 5.2.4: CSRNA, CSCNA) expand,
+// sort and sum instead (heavy_row), as do rows whose entry or product count
+// exceeds the shared-memory capacities.
+// ------------------------------------------------------------------------
+constexpr int kAccEnt = 1024;          // L entries of a row
+constexpr int kAccProd = 2048;         // products of a row
+constexpr int kAccWin = 16384;         // columns of the dense window
+constexpr int kAccHash = 2 * kAccProd; // hash slots (load at most 1/2)
+constexpr uint64_t kHashEmpty = ~0ull;
+
+struct AccSmem {
+    int32_t poff[kAccEnt + 1];
+    int64_t b0[kAccEnt];
+    double aval[kAccEnt];
+    uint64_t pcol[kAccProd];           // product columns; hash plans: the sorted distinct columns later
+    double pv[kAccProd];               // product values (rounded products)
+    uint32_t pidx[kAccProd];           // hash slot, then output index of each product
+    uint16_t pe[kAccProd];             // L entry (row-local) of each product
+    union {
+        struct {
+            uint32_t bits[kAccWin / 32];
+            uint32_t wpre[kAccWin / 32 + 1];
+            uint64_t outcol[kAccProd];
+        } win;
+        struct {
+            uint64_t key[kAccHash];
+            uint32_t idx[kAccHash];
+            uint32_t dslot[kAccProd];
+        } hash;
+    };
+    union {
+        struct {                       // sort of the distinct columns (hash plans)
+            uint64_t k0[kAccProd], k1[kAccProd];
+            double v0[kAccProd], v1[kAccProd];
+        } sort;
+        struct {                       // buckets by output index
+            uint32_t start[kAccProd + 1];
+            uint32_t cur[kAccProd];
+            uint16_t be[kAccProd];
+            double bv[kAccProd];
+        } bkt;
+    };
+    uint32_t whist[kCW * 256];
+    int64_t run[256];
+    int64_t tmp64[kCW + 2];
+    int32_t tmp32[kCW + 2];
+    uint32_t ndist;
+    int32_t fits;
+    uint64_t cmin, cmax;
+};
+
+// One heavy row r through the accumulator; false (nothing written) when
+// the row does not fit the shared-memory structures.
+__device__ __noinline__ bool accumulate_row(const HeavyArgs &a, AccSmem &S, int64_t r) {
+    const int tid = threadIdx.x;
+    const int64_t h0 = a.row_start[r], eend = a.row_start[r + 1];
+    const int64_t pbase = a.row_work[r] - h0;
+    const int64_t nprod = (a.row_work[r + 1] - eend) - pbase;
+    const int64_t nent = eend - h0;
+    if (a.acc != 1 || nent > kAccEnt || nprod > kAccProd) return false;
+    // ---- entries: R row of each, products offsets, column range ----
+    if (tid == 0) {
+        S.cmin = ~0ull;
+        S.cmax = 0;
+        S.ndist = 0;
+        S.fits = 1;
+    }
+    int64_t len_i[kAccEnt / kCT];
+    int64_t lsum = 0;
+    uint64_t cmin = ~0ull, cmax = 0;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kAccEnt / kCT; ++q) {
+        const int j = tid * (kAccEnt / kCT) + q;
+        len_i[q] = 0;
+        if (j < nent) {
+            const int64_t e = h0 + j;
+            const uint64_t liv = (uint64_t)a.l_liv[e];
+            const uint64_t row = divu(a.div_k, liv);
+            const int64_t c = r_row(a.div_h, a.k, row, (int64_t)(liv - row * (uint64_t)a.k));
+            int64_t b0, len;
+            mdt_lookup_entry(a.mdt, e, c, b0, len);
+            S.b0[j] = b0;
+            S.aval[j] = a.l_val[e];
+            len_i[q] = len;
+            if (len > 0) {
+                const uint64_t f0 = (uint64_t)a.r_liv[b0], f1 = (uint64_t)a.r_liv[b0 + len - 1];
+                const uint64_t c0 = f0 - divu(a.div_n, f0) * (uint64_t)a.nR;
+                const uint64_t c1 = f1 - divu(a.div_n, f1) * (uint64_t)a.nR;
+                cmin = c0 < cmin ? c0 : cmin;
+                cmax = c1 > cmax ? c1 : cmax;
+            }
+        }
+        lsum += len_i[q];
+    }
+    if (cmax >= cmin) {
+        atomicMin(reinterpret_cast<unsigned long long *>(&S.cmin), (unsigned long long)cmin);
+        atomicMax(reinterpret_cast<unsigned long long *>(&S.cmax), (unsigned long long)cmax);
+    }
+    int32_t ltot;
+    int32_t lex = block_excl<int32_t>((int32_t)lsum, S.tmp32, &ltot);
+#pragma unroll
+    for (int q = 0; q < kAccEnt / kCT; ++q) {
+        const int j = tid * (kAccEnt / kCT) + q;
+        if (j < nent) S.poff[j] = lex;
+        lex += (int32_t)len_i[q];
+    }
+    if (tid == 0) S.poff[nent] = ltot;
+    __syncthreads();
+    const int np = ltot;
+    const uint64_t wmin = S.cmin;
+    // dense window when the columns span at most kAccWin (uniform over the CTA)
+    const bool window = S.cmax >= wmin && S.cmax - wmin < (uint64_t)kAccWin;
+    const int nwin = window ? (int)((S.cmax - wmin) / 32 + 1) : 0;
+    if (window) {
+        for (int w = tid; w < nwin; w += kCT) S.win.bits[w] = 0;
+    } else {
+        for (int i = tid; i < kAccHash; i += kCT) S.hash.key[i] = kHashEmpty;
+    }
+    __syncthreads();
+    // ---- products (rounded, in generation order), columns into the map ----
+    for (int p = tid; p < np; p += kCT) {
+        int lo = 0, hi = (int)nent;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (S.poff[mid] <= p) lo = mid; else hi = mid;
+        }
+        const int64_t b = S.b0[lo] + (p - S.poff[lo]);
+        const uint64_t rl = (uint64_t)a.r_liv[b];
+        const uint64_t col = rl - divu(a.div_n, rl) * (uint64_t)a.nR;
+        S.pcol[p] = col;
+        S.pv[p] = __dmul_rn(S.aval[lo], a.r_val[b]);
+        S.pe[p] = (uint16_t)lo;
+        if (window) {
+            const uint32_t x = (uint32_t)(col - wmin);
+            atomicOr(&S.win.bits[x >> 5], 1u << (x & 31));
+        } else {
+            // linear probing from a multiplicative hash; at most half full
+            uint32_t slot = (uint32_t)((col * 0x9E3779B97F4A7C15ull) >> 40) & (kAccHash - 1);
+            for (int t = 0; t < kAccHash; ++t) {
+                const unsigned long long old = atomicCAS(
+                    reinterpret_cast<unsigned long long *>(&S.hash.key[slot]), (unsigned long long)kHashEmpty,
+                    (unsigned long long)col);
+                if (old == kHashEmpty) {
+                    S.hash.dslot[atomicAdd(&S.ndist, 1u)] = slot;
+                    break;
+                }
+                if (old == col) break;
+                slot = (slot + 1) & (kAccHash - 1);
+            }
+            S.pidx[p] = slot;
+        }
+    }
+    __syncthreads();
+    // ---- output index of every distinct column, in column order ----
+    int nd;
+    if (window) {
+        // exclusive prefix of the set bits per window word
+        constexpr int kPer = kAccWin / 32 / kCT;
+        int c[kPer];
+        int csum = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int w = tid * kPer + q;
+            c[q] = w < nwin ? __popc(S.win.bits[w]) : 0;
+            csum += c[q];
+        }
+        int32_t tot;
+        int32_t ex = block_excl<int32_t>(csum, S.tmp32, &tot);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int w = tid * kPer + q;
+            if (w < nwin) S.win.wpre[w] = (uint32_t)ex;
+            ex += c[q];
+        }
+        nd = tot;
+        __syncthreads();
+        for (int p = tid; p < np; p += kCT) {
+            const uint32_t x = (uint32_t)(S.pcol[p] - wmin);
+            const uint32_t o = S.win.wpre[x >> 5] + (uint32_t)__popc(S.win.bits[x >> 5] & ((1u << (x & 31)) - 1u));
+            S.pidx[p] = o;
+            S.win.outcol[o] = S.pcol[p];   // every product of the column writes the same value
+        }
+    } else {
+        nd = (int)S.ndist;
+        for (int i = tid; i < nd; i += kCT) {
+            const uint32_t sl = S.hash.dslot[i];
+            S.sort.k0[i] = S.hash.key[sl];
+            S.sort.v0[i] = __longlong_as_double((long long)sl);
+        }
+        __syncthreads();
+        const int rs = cta_sort(S.sort.k0, S.sort.v0, S.sort.k1, S.sort.v1, nd, a.colbits, S.whist, S.run, S.tmp64);
+        const uint64_t *sk = rs ? S.sort.k1 : S.sort.k0;
+        const double *sv = rs ? S.sort.v1 : S.sort.v0;
+        for (int i = tid; i < nd; i += kCT) {
+            S.hash.idx[(uint32_t)__double_as_longlong(sv[i])] = (uint32_t)i;
+            S.pcol[i] = sk[i];            // the product columns are no longer needed
+        }
+        __syncthreads();
+        for (int p = tid; p < np; p += kCT) S.pidx[p] = S.hash.idx[S.pidx[p]];
+    }
+    __syncthreads();
+    const uint64_t *outcol = window ? S.win.outcol : S.pcol;
+    // ---- buckets by output index ----
+    for (int o = tid; o <= nd; o += kCT) S.bkt.start[o] = 0;
+    __syncthreads();
+    for (int p = tid; p < np; p += kCT) atomicAdd(&S.bkt.start[S.pidx[p]], 1u);
+    __syncthreads();
+    {
+        constexpr int kPer = kAccProd / kCT;
+        uint32_t c[kPer];
+        uint32_t csum = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int o = tid * kPer + q;
+            c[q] = o < nd ? S.bkt.start[o] : 0u;
+            csum += c[q];
+        }
+        int32_t tot;
+        int32_t ex = block_excl<int32_t>((int32_t)csum, S.tmp32, &tot);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int o = tid * kPer + q;
+            if (o < nd) {
+                S.bkt.start[o] = (uint32_t)ex;
+                S.bkt.cur[o] = 0;
+            }
+            ex += (int32_t)c[q];
+        }
+        if (tid == 0) S.bkt.start[nd] = (uint32_t)tot;
+    }
+    __syncthreads();
+    for (int p = tid; p < np; p += kCT) {
+        const uint32_t o = S.pidx[p];
+        const uint32_t pos = S.bkt.start[o] + atomicAdd(&S.bkt.cur[o], 1u);
+        S.bkt.be[pos] = S.pe[p];
+        S.bkt.bv[pos] = S.pv[p];
+    }
+    __syncthreads();
+    // ---- each output: its products in entry order, summed from the first ----
+    for (int o = tid; o < nd; o += kCT) {
+        const int s0 = (int)S.bkt.start[o], s1 = (int)S.bkt.start[o + 1];
+        for (int i = s0 + 1; i < s1; ++i) {      // insertion sort by entry (buckets are short)
+            const uint16_t e = S.bkt.be[i];
+            const double v = S.bkt.bv[i];
+            int t = i - 1;
+            while (t >= s0 && S.bkt.be[t] > e) {
+                S.bkt.be[t + 1] = S.bkt.be[t];
+                S.bkt.bv[t + 1] = S.bkt.bv[t];
+                --t;
+            }
+            S.bkt.be[t + 1] = e;
+            S.bkt.bv[t + 1] = v;
+        }
+        double sum = S.bkt.bv[s0];
+        for (int i = s0 + 1; i < s1; ++i) sum = __dadd_rn(sum, S.bkt.bv[i]);
+        a.sk0[pbase + o] = outcol[o];
+        a.sv0[pbase + o] = sum;
+    }
+    if (tid == 0) a.row_hout[r] = nd;
+    __syncthreads();
+    return true;
+}
+
+// Heavy-row kernel: persistent CTAs over the heavy-row list; rows of
+// accumulator plans go through the accumulator when they fit, every other
+// row through the sort-based path.
 __global__ void __launch_bounds__(kCT, 1) k_heavy(const __grid_constant__ HeavyArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HeavySmem &S = *reinterpret_cast<HeavySmem *>(smem_raw);
+    AccSmem &SA = *reinterpret_cast<AccSmem *>(smem_raw);
     __shared__ int64_t s_h;
     const int tid = threadIdx.x;
     if (a.hdr->f > a.cap) return;
@@ -821,9 +1105,13 @@ __global__ void __launch_bounds__(kCT, 1) k_heavy(const __grid_constant__ HeavyA
         __syncthreads();
         const int64_t h = s_h;
         if (h >= nheavy) break;
-        heavy_row(a, S, a.heavy_list[h]);
+        const int64_t r = a.heavy_list[h];
+        if (!accumulate_row(a, SA, r)) heavy_row(a, S, r);
     }
 }
+
+constexpr size_t kHeavySmemBytes = sizeof(HeavySmem) > sizeof(AccSmem) ? sizeof(HeavySmem) : sizeof(AccSmem);
+static_assert(kHeavySmemBytes <= 227 * 1024, "heavy-row shared memory exceeds a CTA's limit");
 
 // ------------------------------------------------------------------------
 // Light rows (work <= kHeavyWork): one warp per tile of 32 consecutive rows
@@ -2292,13 +2580,14 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         ha.sv1 = sv1;
         ha.ctr = chunk_ctr + 2;
         ha.hdr = hdr;
+        ha.acc = p->acc;
         // function attributes are per device: set them once on each
         static std::atomic<uint64_t> attr_done{0};
         int dev = 0;
         cudaGetDevice(&dev);
         const uint64_t bit = 1ull << (dev & 63);
         if (!(attr_done.load() & bit)) {
-            cudaFuncSetAttribute(k_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(HeavySmem));
+            cudaFuncSetAttribute(k_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHeavySmemBytes);
             const int rows_smem = (int)sizeof(RowsSmem) * (kRowsThreads / 32);
             cudaFuncSetAttribute(k_rows<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem);
             cudaFuncSetAttribute(k_rows<uint64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem);
@@ -2306,7 +2595,7 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
             cudaFuncSetAttribute(k_rows<uint64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem);
             attr_done.fetch_or(bit);
         }
-        LCO_LAUNCH("k_heavy", s, k_heavy<<<(unsigned)sms, kCT, sizeof(HeavySmem), s>>>(ha));
+        LCO_LAUNCH("k_heavy", s, k_heavy<<<(unsigned)sms, kCT, kHeavySmemBytes, s>>>(ha));
         RowsArgs ra{};
         ra.l_liv = o.l_liv;
         ra.l_val = o.l_val;

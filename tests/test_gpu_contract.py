@@ -305,3 +305,59 @@ def test_row_branches_are_bit_identical():
                 continue
             assert torch.equal(C.liv, ref.liv), alg
             assert torch.equal(C.val.view(torch.int64), ref.val.view(torch.int64)), alg
+
+
+def _heavy_case(seed, nrows, ent, rlen, ncol, window):
+    """A with `nrows` rows of `ent` entries, each meeting an R row of `rlen`
+    entries: every row has ent * rlen > 256 products (a heavy row).  With
+    `window`, R's columns of the rows an A row meets lie within `window`
+    consecutive columns (the dense-window accumulator fits); the R rows of
+    one A row overlap in columns, so outputs sum several products."""
+    rng = np.random.default_rng(seed)
+    k = nrows * ent
+    a_co = np.array([(r, r * ent + t) for r in range(nrows) for t in range(ent)])
+    A = {"dims": [nrows, k], "sig": [1, 0], "liv": np.ravel_multi_index(tuple(a_co.T), (nrows, k)).astype(np.int64),
+         "val": rng.uniform(-1, 1, len(a_co))}
+    b_co = []
+    for c in range(k):
+        base = (c // ent) * 37 % max(ncol - window, 1)
+        cols = base + rng.choice(window, rlen, replace=False) if window else rng.choice(ncol, rlen, replace=False)
+        b_co += [(c, j) for j in cols]
+    b_co = np.array(b_co)
+    b_liv = np.sort(np.ravel_multi_index(tuple(b_co.T), (k, ncol))).astype(np.int64)
+    B = {"dims": [k, ncol], "sig": [1, 0], "liv": b_liv, "val": rng.uniform(-1, 1, len(b_liv))}
+    return A, B
+
+
+@pytest.mark.parametrize("window", [400, 12000, 0])
+def test_heavy_rows_accumulators(window):
+    """Heavy rows (more than 256 products, up to 2048) of the accumulator
+    plans (CSR, CSC, DCSR) go through the shared-memory accumulator: a dense
+    column window when the row's columns span at most 16384 (window 400 and
+    12000), else a column hash (window 0: columns spread over 2^20); the
+    no-accumulator plans (CSRNA, CSCNA) expand, sort and sum.  Each matches
+    the oracle, and every branch gives the same bits (products summed per
+    column in entry order)."""
+    A, B = _heavy_case(50 + window, nrows=24, ent=40, rlen=30, ncol=1 << 20, window=window)
+    ref = None
+    for alg in ("CSR", "CSRNA", "DCSR", "CSC", "CSCNA", "SOP"):
+        C, info = _run(A, B, [1], [0], alg)
+        assert info["f"] == 24 * 40 * 30
+        if ref is None:
+            ref = C
+        assert_contract_matches(C, A, B, [1], [0])
+        if list(C.sig) != list(ref.sig):
+            # column variants give C column-major: compare in row-major order
+            C = lco.radix_permute(C, ref.sig)
+        assert torch.equal(C.liv, ref.liv), alg
+        assert torch.equal(C.val.view(torch.int64), ref.val.view(torch.int64)), alg
+
+
+def test_heavy_rows_at_the_accumulator_limits():
+    """2048 products in a row (the accumulators' capacity) and one beyond it
+    (the sort-based path), with many products per output column."""
+    for ent, rlen in ((64, 32), (41, 50)):
+        A, B = _heavy_case(60 + ent, nrows=8, ent=ent, rlen=rlen, ncol=4096, window=200)
+        for alg in ("CSR", "CSRNA"):
+            C, info = _run(A, B, [1], [0], alg)
+            assert_contract_matches(C, A, B, [1], [0])
