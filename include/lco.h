@@ -331,6 +331,50 @@ int32_t lco_contract(const lco_plan *plan,
 /* Synchronises `stream` and copies the result header of `ws` to *out. */
 int32_t lco_contract_result_get(const void *ws, lco_contract_result *out, void *stream);
 
+/* Contraction of wide tensors (Sec. 5's product with the LIVs of Sec. 3.1
+ * evaluated as unsigned 128-bit integers; Sec. 3.1 and Sec. 7 leave such
+ * index spaces to future work).  C[i, j] = sum_k A[i, k] B[k, j] over the
+ * matricised operands, C's modes being A's free modes then B's (increasing
+ * mode numbers), row-major, every index (row, contracted, column) up to 127
+ * bits; A's and B's dims, and C's, multiply to at most 2^127 - 1.
+ * Implementation: A and B are permuted (lco_radix_permute_wide) into their
+ * matrix orders; every row, contracted and column key is replaced by its
+ * rank among the keys that occur (ranks keep the order); the 64-bit
+ * contraction (lco_contract, Table 4 on the rank matrices) multiplies the
+ * rank matrices, whose shapes (2 nnz_A x (nnz_B + 1), (nnz_B + 1) x nnz_B)
+ * are fixed at planning; each entry of the rank product is mapped back to
+ * row key * n + column key.  Sums run in the same order as every 64-bit
+ * branch (entries of A in order, each B row in order).
+ * Liv arrays are device arrays of 2 * nnz uint64 (low, high word per
+ * entry), values device doubles; ws: lco_contract_wide_workspace bytes,
+ * 256-byte aligned, any content (each call resets what it uses).  The same
+ * ws must carry phase 1's results into phase 2 (a workspace sized for a
+ * larger capacity keeps phase 1's layout).  Phase 1 reports f (the
+ * product count) through lco_contract_wide_result_get; C needs room for f
+ * entries.  Errors: LCO_ERR_INVALID (modes, dims, order, pointers),
+ * LCO_ERR_OVERFLOW (a product of dims past 2^127 - 1, or nnz too large for
+ * the rank matrices' 63-bit LIVs), LCO_ERR_OOM (ws too small), LCO_ERR_CUDA;
+ * device status LCO_ERR_CAPACITY (f > cap), LCO_ERR_TIMEOUT. */
+typedef struct lco_wide_plan lco_wide_plan;   /* opaque host object */
+
+int32_t lco_contract_wide_plan(const lco_shape *a, const lco_shape *b, int32_t ncontract,
+                               const int32_t *modes_a, const int32_t *modes_b, lco_wide_plan **plan);
+int32_t lco_contract_wide_plan_destroy(lco_wide_plan *plan);
+/* C's shape (nnz 0) and the Table-4 branch the rank product takes (may be NULL). */
+int32_t lco_contract_wide_info(const lco_wide_plan *plan, lco_shape *c_shape, int32_t *inner_alg);
+/* Workspace bytes for output capacity cap (0 suffices for phase 1). */
+int32_t lco_contract_wide_workspace(const lco_wide_plan *plan, int64_t cap, size_t *ws_bytes);
+/* Phase 1: permutations, ranks, rank matrices, phase 1 of their product. */
+int32_t lco_contract_wide_symbolic(const lco_wide_plan *plan, const uint64_t *a_liv, const double *a_val,
+                                   const uint64_t *b_liv, const double *b_val, void *ws, size_t ws_bytes,
+                                   void *stream);
+/* Phase 2: the rank product and C (c_liv: 2 * cap uint64, c_val: cap doubles). */
+int32_t lco_contract_wide_numeric(const lco_wide_plan *plan, uint64_t *c_liv, double *c_val, int64_t cap,
+                                  void *ws, size_t ws_bytes, void *stream);
+/* Synchronises `stream`; status, f and the number of entries of C. */
+int32_t lco_contract_wide_result_get(const lco_wide_plan *plan, const void *ws, lco_contract_result *out,
+                                     void *stream);
+
 /* ------------------------------------------------------------------ */
 /* Tuning hints (planner inputs chosen by an autotuner; no paper        */
 /* counterpart beyond Table 4's choice, which they may override)        */

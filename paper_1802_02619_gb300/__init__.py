@@ -134,6 +134,19 @@ _SIGNATURES = {
     "lco_radix_permute_wide": ([ctypes.POINTER(Shape), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                 ctypes.c_void_p], ctypes.c_int32),
+    "lco_contract_wide_plan": ([ctypes.POINTER(Shape), ctypes.POINTER(Shape), ctypes.c_int32, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int32),
+    "lco_contract_wide_plan_destroy": ([ctypes.c_void_p], ctypes.c_int32),
+    "lco_contract_wide_info": ([ctypes.c_void_p, ctypes.POINTER(Shape), ctypes.POINTER(ctypes.c_int32)],
+                               ctypes.c_int32),
+    "lco_contract_wide_workspace": ([ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)],
+                                    ctypes.c_int32),
+    "lco_contract_wide_symbolic": ([ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_void_p, ctypes.c_size_t,
+                                                                                ctypes.c_void_p], ctypes.c_int32),
+    "lco_contract_wide_numeric": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                   ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int32),
+    "lco_contract_wide_result_get": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ContractResult),
+                                      ctypes.c_void_p], ctypes.c_int32),
     "lco_contract_plan": ([ctypes.POINTER(Shape), ctypes.POINTER(Shape), ctypes.c_int32, ctypes.c_void_p,
                            ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int32),
     "lco_plan_get_info": ([ctypes.c_void_p, ctypes.POINTER(PlanInfo)], ctypes.c_int32),
@@ -461,6 +474,93 @@ def radix_permute_wide(dims, sig, new_sig, liv: torch.Tensor, val: torch.Tensor,
     if st != 0:
         raise LcoError(st, "lco_radix_permute_wide (device)")
     return lo, vo
+
+
+class WideContractPlan:
+    """Plan for C = A x_modes B with wide (128-bit) LIVs (lco_contract_wide_*
+    in include/lco.h): shapes as lists (dims may multiply past 2^63 - 1, up
+    to 2^127 - 1), contracted mode pairs.  C is row-major over A's free
+    modes then B's."""
+
+    def __init__(self, a_dims, a_sig, a_nnz, b_dims, b_sig, b_nnz, modes_a, modes_b, device="cuda"):
+        self.lib = load()
+        self.device = device
+        self.sa = make_shape(a_dims, a_sig, a_nnz)
+        self.sb = make_shape(b_dims, b_sig, b_nnz)
+        ma = (ctypes.c_int32 * MAX_ORDER)(*modes_a)
+        mb = (ctypes.c_int32 * MAX_ORDER)(*modes_b)
+        h = ctypes.c_void_p()
+        _check(self.lib.lco_contract_wide_plan(ctypes.byref(self.sa), ctypes.byref(self.sb), len(modes_a), ma, mb,
+                                               ctypes.byref(h)), "lco_contract_wide_plan")
+        self.handle = h
+        cs = Shape()
+        alg = ctypes.c_int32()
+        _check(self.lib.lco_contract_wide_info(h, ctypes.byref(cs), ctypes.byref(alg)), "lco_contract_wide_info")
+        self.c_dims = [cs.dims[i] for i in range(cs.order)]
+        self.c_sig = [cs.sig[i] for i in range(cs.order)]
+        self.inner_alg = ALG_NAMES[alg.value]
+        self.ws = None
+        self.cap = -1
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None) is not None and self.handle.value:
+                self.lib.lco_contract_wide_plan_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+    def ensure_workspace(self, cap: int):
+        if cap > self.cap:
+            nb = ctypes.c_size_t()
+            _check(self.lib.lco_contract_wide_workspace(self.handle, int(cap), ctypes.byref(nb)),
+                   "lco_contract_wide_workspace")
+            self.ws = workspace(nb.value, self.device)
+            self.cap = int(cap)
+
+    def symbolic(self, a_liv, a_val, b_liv, b_val, stream=None):
+        _check(self.lib.lco_contract_wide_symbolic(self.handle, _ptr(a_liv), _ptr(a_val), _ptr(b_liv), _ptr(b_val),
+                                                   _ptr(self.ws), ctypes.c_size_t(self.ws.numel()), _stream(stream)),
+               "lco_contract_wide_symbolic")
+
+    def numeric(self, c_liv, c_val, stream=None):
+        _check(self.lib.lco_contract_wide_numeric(self.handle, _ptr(c_liv), _ptr(c_val), int(self.cap),
+                                                  _ptr(self.ws), ctypes.c_size_t(self.ws.numel()), _stream(stream)),
+               "lco_contract_wide_numeric")
+
+    def result(self, stream=None) -> dict:
+        r = ContractResult()
+        _check(self.lib.lco_contract_wide_result_get(self.handle, _ptr(self.ws), ctypes.byref(r), _stream(stream)),
+               "lco_contract_wide_result_get")
+        return {"status": r.status, "alg": ALG_NAMES[r.alg] if 0 <= r.alg < len(ALG_NAMES) else r.alg,
+                "nnz_c": int(r.nnz_c), "f": int(r.f)}
+
+
+def contract_wide(a_dims, a_sig, a_liv, a_val, b_dims, b_sig, b_liv, b_val, modes_a, modes_b, stream=None):
+    """C = A x_modes B for wide-LIV tensors (liv: (nnz, 2) int64 device
+    tensors holding uint64 words, low first).  Phase 1 sizes C by the
+    product count f; returns (c_liv (nnz_c, 2), c_val, plan)."""
+    for t in (a_liv, b_liv):
+        _require_cuda(t)
+        _wide(t)
+    p = WideContractPlan(a_dims, a_sig, a_liv.shape[0], b_dims, b_sig, b_liv.shape[0], modes_a, modes_b,
+                         device=a_liv.device)
+    p.ensure_workspace(0)
+    p.symbolic(a_liv, a_val, b_liv, b_val, stream)
+    r = p.result(stream)
+    if r["status"] != 0:
+        raise LcoError(r["status"], "lco_contract_wide_symbolic (device)")
+    f = r["f"]
+    p.ensure_workspace(f)
+    c_liv = torch.empty((max(f, 1), 2), dtype=torch.int64, device=a_liv.device)
+    c_val = torch.empty(max(f, 1), dtype=torch.float64, device=a_liv.device)
+    p.symbolic(a_liv, a_val, b_liv, b_val, stream)
+    p.numeric(c_liv, c_val, stream)
+    r = p.result(stream)
+    if r["status"] != 0:
+        raise LcoError(r["status"], "lco_contract_wide_numeric (device)")
+    n = r["nnz_c"]
+    return c_liv[:n], c_val[:n], p
 
 
 # ---------------------------------------------------------------------------
