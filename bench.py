@@ -34,6 +34,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# The batch and the server run work on 16 and 64 streams; by default CUDA
+# maps all streams of a process onto 8 hardware work queues, so kernels of
+# unrelated streams wait on each other.  32 queues (read when the CUDA
+# context is created, so before torch touches the GPU) let them overlap.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 import numpy as np  # noqa: E402
 
 METRIC = "contraction GNNZ/s"

@@ -7,10 +7,14 @@
 // thread admits queued requests in arrival order into stream slots and runs
 // each one as the two phases of Sec. 5.2 -- phase 1 gives f, the product
 // count; phase 2 multiplies into an output of f entries -- with an
-// asynchronous read of the workspace header between them.  Completion is
-// observed with CUDA events, so requests overlap on the device and none
-// waits for another's host round trip.  The arithmetic of a request is
-// exactly that of lco_contract (same plan, same kernels).
+// asynchronous read of the workspace header between them.  Operands are
+// immutable while resident, so the plan and f of an (operand pair, modes)
+// combination are kept after its first request: a repeated request is
+// admitted with its whole output and workspace and runs both phases back
+// to back, with one completion read.  Completion is observed with CUDA
+// events, so requests overlap on the device and none waits for another's
+// host round trip.  The arithmetic of a request is exactly that of
+// lco_contract (same plan, same kernels).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -153,10 +157,38 @@ struct Operand {
 
 enum ReqState { kQueued = 0, kPhase1 = 1, kPhase2 = 2, kDone = 3 };
 
+// The plan of an (operand pair, modes) combination, shared by its requests,
+// and its product count once a request has computed it.
+struct PlanEntry {
+    lco_plan *plan = nullptr;
+    lco_plan_info info{};
+    std::atomic<int64_t> f{-1};
+    ~PlanEntry() {
+        if (plan) lco_plan_destroy(plan);
+    }
+};
+
+struct PlanKey {
+    int64_t ha, hb;
+    int32_t nc;
+    int32_t ma[LCO_MAX_ORDER], mb[LCO_MAX_ORDER];
+    bool operator<(const PlanKey &o) const {
+        if (ha != o.ha) return ha < o.ha;
+        if (hb != o.hb) return hb < o.hb;
+        if (nc != o.nc) return nc < o.nc;
+        for (int i = 0; i < nc; ++i) {
+            if (ma[i] != o.ma[i]) return ma[i] < o.ma[i];
+            if (mb[i] != o.mb[i]) return mb[i] < o.mb[i];
+        }
+        return false;
+    }
+};
+
 struct Request {
     uint64_t id = 0;
     std::shared_ptr<Operand> a, b;
-    lco_plan *plan = nullptr;
+    std::shared_ptr<PlanEntry> pe;
+    lco_plan *plan = nullptr;  // pe->plan
     lco_plan_info info{};
     std::atomic<int> state{kQueued};
     int slot = -1;
@@ -197,6 +229,7 @@ struct lco_server {
     std::deque<Request *> queue;
     std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
     std::unordered_map<int64_t, std::shared_ptr<Operand>> operands;
+    std::map<PlanKey, std::shared_ptr<PlanEntry>> plans;   // dropped with either operand
     uint64_t next_req = 1;
     int64_t next_handle = 1;
     uint64_t submitted = 0, completed = 0, failed = 0;
@@ -241,10 +274,9 @@ void lco_server::finish_locked(Request *r, int32_t status) {
     }
     r->a.reset();
     r->b.reset();
-    if (r->plan) {
-        lco_plan_destroy(r->plan);
-        r->plan = nullptr;
-    }
+    if (r->pe && r->status == LCO_OK && r->f >= 0) r->pe->f.store(r->f);
+    r->pe.reset();
+    r->plan = nullptr;
     r->state = kDone;
     r->t_done = now_us();
     if (r->slot >= 0) {
@@ -260,6 +292,48 @@ void lco_server::finish_locked(Request *r, int32_t status) {
 // its workspace yet (the request stays queued).
 bool lco_server::admit(Request *r, Slot &sl, int si) {
     const int64_t na = r->a->shape.nnz, nb = r->b->shape.nnz;
+    const int64_t fk = r->pe->f.load();
+    if (fk >= 0) {
+        // the product count is known: output and workspace at once, both
+        // phases back to back, one completion read
+        const int64_t cap = fk > 0 ? fk : 1;
+        size_t wb = 0;
+        if (lco_contract_workspace(r->plan, cap, &wb) != LCO_OK) {
+            finish(r, LCO_ERR_INVALID);
+            return true;
+        }
+        if (lco_pool_alloc(pool, wb, &r->ws) != LCO_OK) return false;
+        if (lco_pool_alloc(pool, (size_t)cap * 16, &r->cbuf) != LCO_OK) {
+            pfree(r->ws);
+            return false;
+        }
+        r->ws_cap = cap;
+        r->cap = cap;
+        r->f = fk;
+        r->slot = si;
+        sl.req = r;
+        {
+            std::lock_guard<std::mutex> g(mu);
+            in_flight++;
+        }
+        r->state = kPhase2;
+        cudaStream_t s = sl.stream;
+        int64_t *c_liv = reinterpret_cast<int64_t *>(r->cbuf);
+        double *c_val = reinterpret_cast<double *>(c_liv + cap);
+        int32_t rc = LCO_OK;
+        if (lco::contract_ws_init(r->plan, r->ws, cap, s) != cudaSuccess) rc = LCO_ERR_CUDA;
+        if (rc == LCO_OK)
+            rc = lco_contract(r->plan, r->a->liv, r->a->val, r->b->liv, r->b->val, c_liv, c_val, cap, r->ws, wb, s);
+        if (rc == LCO_OK &&
+            cudaMemcpyAsync(sl.hdr, r->ws, sizeof(lco::WsHeader), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            rc = LCO_ERR_CUDA;
+        if (rc == LCO_OK && cudaEventRecord(sl.ev, s) != cudaSuccess) rc = LCO_ERR_CUDA;
+        if (rc != LCO_OK) {
+            cudaStreamSynchronize(s);
+            finish(r, rc);
+        }
+        return true;
+    }
     // room for phase 2 too when f turns out to be at most this guess
     r->ws_cap = 4 * (na + nb) + 1024;
     size_t wb = 0;
@@ -546,9 +620,8 @@ int32_t lco_serve_destroy(lco_server *srv) {
         if (sl.hdr) cudaFreeHost(sl.hdr);
     }
     if (srv->put_stream) cudaStreamDestroy(srv->put_stream);
-    for (auto &kv : srv->reqs)
-        if (kv.second->plan) lco_plan_destroy(kv.second->plan);
     srv->reqs.clear();
+    srv->plans.clear();
     srv->operands.clear();
     lco_pool_destroy(srv->pool);
     if (srv->own_pool) cudaFree(srv->pool_mem);
@@ -591,6 +664,10 @@ int32_t lco_serve_drop(lco_server *srv, int64_t handle) {
     if (it == srv->operands.end()) return LCO_ERR_INVALID;
     auto op = it->second;
     srv->operands.erase(it);
+    for (auto pit = srv->plans.begin(); pit != srv->plans.end();) {
+        if (pit->first.ha == handle || pit->first.hb == handle) pit = srv->plans.erase(pit);
+        else ++pit;
+    }
     op->dropped = true;
     if (op->refs == 0 && op->block) {
         lco_pool_free(srv->pool, op->block);
@@ -602,20 +679,41 @@ int32_t lco_serve_drop(lco_server *srv, int64_t handle) {
 int32_t lco_serve_submit(lco_server *srv, int64_t ha, int64_t hb, int32_t ncontract, const int32_t *modes_a,
                          const int32_t *modes_b, uint64_t *req) {
     if (!srv || !req) return LCO_ERR_INVALID;
+    if (ncontract < 0 || ncontract > LCO_MAX_ORDER || (ncontract > 0 && (!modes_a || !modes_b)))
+        return LCO_ERR_INVALID;
     std::shared_ptr<Operand> a, b;
+    PlanKey key{};
+    key.ha = ha;
+    key.hb = hb;
+    key.nc = ncontract;
+    for (int i = 0; i < ncontract; ++i) {
+        key.ma[i] = modes_a[i];
+        key.mb[i] = modes_b[i];
+    }
+    std::shared_ptr<PlanEntry> pe;
     {
         std::lock_guard<std::mutex> g(srv->mu);
         auto ia = srv->operands.find(ha), ib = srv->operands.find(hb);
         if (ia == srv->operands.end() || ib == srv->operands.end()) return LCO_ERR_INVALID;
         a = ia->second;
         b = ib->second;
+        auto pit = srv->plans.find(key);
+        if (pit != srv->plans.end()) pe = pit->second;
     }
-    lco_plan *plan = nullptr;
-    int32_t rc = lco_contract_plan(&a->shape, &b->shape, ncontract, modes_a, modes_b, LCO_ALG_AUTO, &plan);
-    if (rc != LCO_OK) return rc;
+    if (!pe) {
+        auto fresh = std::make_shared<PlanEntry>();
+        int32_t rc = lco_contract_plan(&a->shape, &b->shape, ncontract, modes_a, modes_b, LCO_ALG_AUTO,
+                                       &fresh->plan);
+        if (rc != LCO_OK) return rc;
+        lco_plan_get_info(fresh->plan, &fresh->info);
+        std::lock_guard<std::mutex> g(srv->mu);
+        auto ins = srv->plans.emplace(key, fresh);   // another thread may have made it meanwhile
+        pe = ins.first->second;
+    }
     auto r = std::make_unique<Request>();
-    r->plan = plan;
-    lco_plan_get_info(plan, &r->info);
+    r->pe = pe;
+    r->plan = pe->plan;
+    r->info = pe->info;
     std::lock_guard<std::mutex> g(srv->mu);
     r->id = srv->next_req++;
     r->a = a;
