@@ -880,6 +880,40 @@ def measure_batch(count, K, warmup, streams, cpu_budget_s=12.0, tune=False, per_
     ms_batch = e0.elapsed_time(e1) / K
     for C, C2 in zip(outs, batch.results()):
         assert torch.equal(C.liv, C2.liv), "graph replay changed a result"
+    # per-kernel times of one stacked run (direct launches, kernel events)
+    lco.timing_enable(True)
+    batch.run()
+    torch.cuda.synchronize()
+    recs = lco.timing_read()
+    lco.timing_enable(False)
+    per_kernel = {}
+    for nm, ms in recs:
+        t = per_kernel.setdefault(nm, [0, 0.0])
+        t[0] += 1
+        t[1] += ms
+    top = sorted(per_kernel.items(), key=lambda kv: -kv[1][1])[:12]
+    kernels = {nm: {"launches": c, "ms": round(ms, 3)} for nm, (c, ms) in top}
+    # the per-problem path (every problem's phases on the stream pool), same graph form
+    gpp = torch.cuda.CUDAGraph()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        batch.run_per_problem()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(gpp, stream=side):
+            batch.run_per_problem()
+    stream.wait_stream(side)
+    for _ in range(3):
+        gpp.replay()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        gpp.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_pp = e0.elapsed_time(e1) / K
+    for C, C2 in zip(outs, batch.results()):
+        assert torch.equal(C.liv, C2.liv), "per-problem path differs from the stacked one"
+    del gpp
 
     # ---- plain loop: one call per problem, stream sync after each ----
     plans = []
@@ -918,6 +952,9 @@ def measure_batch(count, K, warmup, streams, cpu_budget_s=12.0, tune=False, per_
                        "ms_per_step": round(ms_plain, 3), "steps": Kp,
                        "what": "one contraction call per problem + stream sync, plans/workspaces prepared"},
         "speedup_vs_plain_loop": round(ms_plain / ms_batch, 3),
+        "per_problem_graph": {"value": round(units / (ms_pp * 1e-3) / 1e9, 4), "ms_per_step": round(ms_pp, 4),
+                              "what": "every problem's two phases on the stream pool, one graph replay"},
+        "kernels_stacked_run": kernels,
         "roofline": {"bound": "hbm", "kernel": "whole batch (all kernels)",
                      "achieved": round(16 * units / (ms_batch * 1e-3) / 1e9, 1),
                      "peak": measured_peak_hbm()[0], "unit": "GB/s",

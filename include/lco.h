@@ -453,7 +453,17 @@ int32_t lco_batch_workspace(const lco_batch *batch, const int64_t *caps, size_t 
  * the batch's worker streams (events) and joined back into `stream`, so a
  * whole call can be captured into one CUDA graph.  ops[nprob]: device
  * pointers; caps must be the same array (values) the workspace was sized
- * with.  No host synchronisation. */
+ * with.  No host synchronisation.
+ * lco_batch_symbolic / _numeric run each problem's phases on its own.
+ * lco_batch_contract runs the problems whose operands are already in their
+ * matrix orders as a few stacked products (Sec. 5's entrywise modes read
+ * the other way: independent products are one product over a shared
+ * problem index; grouped by row-kernel family), each problem's results
+ * bit-identical to a single call; the other problems run on their own.  It
+ * copies a table of the problems' pointers into the workspace from a host
+ * buffer the batch owns: a CUDA graph captured from it replays with the
+ * pointers of the latest lco_batch_contract call on this batch, and calls
+ * with different ops must not overlap in time. */
 int32_t lco_batch_symbolic(lco_batch *batch, const lco_operands *ops, const int64_t *caps,
                            void *ws, size_t ws_bytes, void *stream);
 int32_t lco_batch_numeric(lco_batch *batch, const lco_operands *ops, const int64_t *caps,

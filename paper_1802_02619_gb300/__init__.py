@@ -771,8 +771,18 @@ class Batch:
             pass
 
     def run(self, stream=None):
+        """The whole batch as stacked products (lco_batch_contract)."""
         _check(self.lib.lco_batch_contract(self.handle, self._ops, self._caps, _ptr(self.ws),
                                            ctypes.c_size_t(self.ws.numel()), _stream(stream)), "lco_batch_contract")
+
+    def run_per_problem(self, stream=None):
+        """Every problem's two phases on their own over the stream pool
+        (lco_batch_symbolic + lco_batch_numeric): the same results."""
+        n = ctypes.c_size_t(self.ws.numel())
+        _check(self.lib.lco_batch_symbolic(self.handle, self._ops, self._caps, _ptr(self.ws), n, _stream(stream)),
+               "lco_batch_symbolic")
+        _check(self.lib.lco_batch_numeric(self.handle, self._ops, self._caps, _ptr(self.ws), n, _stream(stream)),
+               "lco_batch_numeric")
 
     def results(self, stream=None):
         res = (ContractResult * self.n)()

@@ -2787,6 +2787,29 @@ cudaError_t contract_ws_init(const lco_plan *p, void *ws, int64_t cap, cudaStrea
 
 size_t contract_phase1_bytes(const lco_plan *p) { return p->phase1_end; }
 
+void plan_view(const lco_plan *p, PlanView *v) {
+    v->l_is_a = p->l_is_a;
+    v->need_l = p->need_l;
+    v->need_r = p->need_r;
+    v->alg = p->info.alg;
+    v->lookup = p->lookup;
+    v->mL = p->mL;
+    v->k = p->k;
+    v->nR = p->nR;
+    v->nnz_l = p->nnz_l;
+    v->nnz_r = p->nnz_r;
+    v->relin_l = p->rp_l.relin;
+    v->relin_r = p->rp_r.relin;
+}
+
+void plan_row_table(const lco_plan *p, const void *ws, const int64_t **row_start, const int64_t **row_id,
+                    const int64_t **row_work) {
+    const char *w = reinterpret_cast<const char *>(ws);
+    *row_start = reinterpret_cast<const int64_t *>(w + p->off_row_start);
+    *row_id = reinterpret_cast<const int64_t *>(w + p->off_row_id);
+    *row_work = reinterpret_cast<const int64_t *>(w + p->off_row_work);
+}
+
 namespace {
 
 int32_t check_ws(const lco_plan *p, void *ws, size_t ws_bytes, int64_t cap) {

@@ -45,4 +45,22 @@ cudaError_t contract_ws_init(const lco_plan *p, void *ws, int64_t cap, cudaStrea
 // Bytes of the phase-1 region at the start of a contraction workspace.
 size_t contract_phase1_bytes(const lco_plan *p);
 
+// The matrix view a plan multiplies (row variants: L = A, R = B; column
+// variants: L = B, R = A): L is mL x k, R is k x nR, and relin_l / relin_r
+// map an operand's source LIV to its matrix-order LIV (row * k + column for
+// L, row * nR + column for R).
+struct PlanView {
+    int32_t l_is_a, need_l, need_r, alg, lookup;
+    int64_t mL, k, nR, nnz_l, nnz_r;
+    RelinParams relin_l, relin_r;
+};
+void plan_view(const lco_plan *p, PlanView *v);
+
+// L's row table of a contraction after its phase 1, in workspace `ws`:
+// row_start[r] / row_work[r] are the first entry and the work prefix of
+// L's r-th non-empty row (both with one closing element), row_id[r] its
+// row index; the number of rows is the header's nrows_l.
+void plan_row_table(const lco_plan *p, const void *ws, const int64_t **row_start, const int64_t **row_id,
+                    const int64_t **row_work);
+
 }  // namespace lco
