@@ -66,6 +66,61 @@ __host__ __device__ __forceinline__ uint64_t divu(const DivU64 &v, uint64_t n) {
 }
 
 // ---------------------------------------------------------------------------
+// Unsigned 128-bit dividend, 64-bit invariant divisor (wide LIVs).
+//
+// The high word goes through DivU64; the rest is one "2-by-1" step of
+// Moeller & Granlund, "Improved division by invariant integers" (IEEE
+// Trans. Computers 60(2), 2011), Algorithm 4: with the divisor normalised
+// (d_n = d << s, top bit set) and its reciprocal v = floor((2^128 - 1) /
+// d_n) - 2^64, a two-word numerator (u1, u0) with u1 < d_n gives q and r
+// from one 64x64 product, a two-word add and at most two corrections.
+// ---------------------------------------------------------------------------
+struct DivU128by64 {
+    DivU64 hi;     // for the high word
+    uint64_t dn;   // d << s
+    uint64_t v;    // reciprocal of dn
+    uint32_t s;    // normalisation shift
+    uint32_t pad;
+};
+
+inline DivU128by64 make_div128(uint64_t d) {
+    DivU128by64 w{};
+    w.hi = make_div(d);
+    w.s = (uint32_t)__builtin_clzll(d);
+    w.dn = d << w.s;
+    const unsigned __int128 all = ~(unsigned __int128)0;
+    w.v = (uint64_t)(all / w.dn - ((unsigned __int128)1 << 64));
+    return w;
+}
+
+// x = q * d + r, 0 <= r < d; returns q, writes r.
+__host__ __device__ __forceinline__ unsigned __int128 divu128(const DivU128by64 &w, unsigned __int128 x,
+                                                             uint64_t &r) {
+    const uint64_t xh = (uint64_t)(x >> 64), xl = (uint64_t)x;
+    const uint64_t d = w.hi.d;
+    const uint64_t qh = divu(w.hi, xh);
+    const uint64_t rh = xh - qh * d;
+    // normalise the two-word remainder (rh, xl): rh < d, so u1 < dn
+    const uint64_t u1 = w.s ? (rh << w.s) | (xl >> (64 - w.s)) : rh;
+    const uint64_t u0 = xl << w.s;
+    const unsigned __int128 p = (unsigned __int128)w.v * u1;
+    const unsigned __int128 qq = p + ((((unsigned __int128)(u1 + 1)) << 64) | u0);
+    uint64_t q1 = (uint64_t)(qq >> 64);
+    const uint64_t q0 = (uint64_t)qq;
+    uint64_t rr = u0 - q1 * w.dn;
+    if (rr > q0) {
+        --q1;
+        rr += w.dn;
+    }
+    if (rr >= w.dn) {
+        ++q1;
+        rr -= w.dn;
+    }
+    r = rr >> w.s;
+    return ((unsigned __int128)qh << 64) | q1;
+}
+
+// ---------------------------------------------------------------------------
 // Re-linearisation (Sec. 3.1 "LIV shuffle").  Modes that are adjacent and in
 // the same relative order in both the old and the new order are merged into
 // one "segment" on the host, so an order-N shuffle costs (segments - 1)

@@ -28,7 +28,10 @@ constexpr int kMaxDigitBits = 11;
 // the scattered writes no longer coalesce (measured: an 11-bit pass cost 3x
 // an 8-bit pass on 32-bit random keys), so wider digits only pay when they
 // remove a pass and the keys are clustered.  A tuning hint may raise it.
-constexpr int kDefaultDigitBits = 9;
+#ifndef LCO_DEFAULT_DIGIT_BITS
+#define LCO_DEFAULT_DIGIT_BITS 9
+#endif
+constexpr int kDefaultDigitBits = LCO_DEFAULT_DIGIT_BITS;   // a build may override it to measure others
 constexpr int kMaxPasses = 6;
 constexpr int kUpsweepCtasPerSm = 4;
 

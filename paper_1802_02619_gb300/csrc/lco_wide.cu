@@ -29,6 +29,7 @@ struct WideShape {
     int64_t dims[kMaxOrder];
     int32_t sig_old[kMaxOrder];
     int32_t sig_new[kMaxOrder];
+    DivU128by64 div[kMaxOrder];    // division of a wide LIV by each mode's dim
 };
 
 struct WidePlan {
@@ -51,20 +52,21 @@ __device__ __forceinline__ void store_wide(uint64_t *p, int64_t e, u128 x) {
 
 // New LIV and sort key of one wide LIV (coordinates from the old order, least
 // significant first; Horner from the most significant new mode).
+// Each coordinate comes off with one 128-by-64 division by an invariant dim
+// (a reciprocal multiply, not a software long division).
 __device__ __forceinline__ void wide_relin(const WideShape &s, u128 liv, u128 &newliv, u128 &key) {
-    u128 c[kMaxOrder];
+    uint64_t c[kMaxOrder];
     u128 r = liv;
     for (int t = 0; t < s.order; ++t) {
         const int m = s.sig_old[t];
-        const u128 d = (u128)(uint64_t)s.dims[m];
-        const u128 q = r / d;
-        c[m] = r - q * d;
-        r = q;
+        uint64_t rem;
+        r = divu128(s.div[m], r, rem);
+        c[m] = rem;
     }
     u128 x = 0;
     for (int t = s.order - 1; t >= 0; --t) {
         const int m = s.sig_new[t];
-        x = x * (u128)(uint64_t)s.dims[m] + c[m];
+        x = x * (uint64_t)s.dims[m] + c[m];
         if (t == s.t_low) key = x;
     }
     newliv = x;
@@ -154,6 +156,7 @@ int32_t wide_plan(const lco_shape *t, const int32_t *new_sig, WidePlan *out) {
     int pos_old[kMaxOrder], pos_new[kMaxOrder];
     for (int i = 0; i < N; ++i) {
         p.s.dims[i] = t->dims[i];
+        p.s.div[i] = make_div128((uint64_t)t->dims[i]);
         p.s.sig_old[i] = t->sig[i];
         p.s.sig_new[i] = new_sig[i];
         pos_old[t->sig[i]] = i;
