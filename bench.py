@@ -75,6 +75,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["lco", "reference"], default="lco")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--soak-s", type=float, default=1.5,
+                    help="seconds of clock-sampled graph replays before the timed region (0 = none, e.g. under ncu)")
     ap.add_argument("--no-extras", action="store_true",
                     help="--case step: skip the C3, C3b, batch and serve measurements after the headline")
     ap.add_argument("--case", choices=["step", "permute", "batch", "serve", "permsweep", "permute_wide"],
@@ -471,7 +473,7 @@ def run_lco(args):
     device = f"cuda:{local}"
     # the clock record covers at least 1.5 s of replays just before the timed region
     rec, step, cfg = measure_config(args.config, device, args.steps, args.warmup, world, local,
-                                    args.max_digit_bits, soak_s=1.5)
+                                    args.max_digit_bits, soak_s=args.soak_s)
     out = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic"}

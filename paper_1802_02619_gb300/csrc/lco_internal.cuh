@@ -134,22 +134,28 @@ struct RelinParams {
     DivU64 seg_div[kMaxOrder];
     int64_t seg_stride[kMaxOrder];
     // every segment range and stride a power of two (every dimension is):
-    // a segment is a bit field, moved by masks and shifts
+    // a segment is a bit field, moved by masks and shifts -- segment t is
+    // bits [in_shift[t], in_shift[t] + width) of the old LIV (seg_mask[t] =
+    // 2^width - 1) and lands at bit stride_shift[t] of the new one
     int32_t all_pow2;
     uint32_t stride_shift[kMaxOrder];
+    uint32_t in_shift[kMaxOrder];
+    uint64_t seg_mask[kMaxOrder];
 };
 
 __host__ __device__ __forceinline__ int64_t relin(const RelinParams &p, int64_t liv) {
     if (p.identity) return liv;
     if (p.all_pow2) {
-        uint64_t r = (uint64_t)liv, out = 0;
-#pragma unroll 1
-        for (int t = 0; t < p.nseg - 1; ++t) {
-            const uint32_t w = p.seg_div[t].shift;
-            out |= (r & ((1ull << w) - 1)) << p.stride_shift[t];
-            r >>= w;
+        // independent fields (no chain through the remaining LIV); the loop
+        // is unrolled so that every segment's constants are direct operands
+        const uint64_t x = (uint64_t)liv;
+        uint64_t out = 0;
+#pragma unroll
+        for (int t = 0; t < kMaxOrder; ++t) {
+            if (t >= p.nseg) break;
+            out |= ((x >> p.in_shift[t]) & p.seg_mask[t]) << p.stride_shift[t];
         }
-        return (int64_t)(out | (r << p.stride_shift[p.nseg - 1]));
+        return (int64_t)out;
     }
     uint64_t r = (uint64_t)liv;
     int64_t out = 0;

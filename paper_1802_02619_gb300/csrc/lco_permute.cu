@@ -64,10 +64,15 @@ RelinParams make_relin(int32_t order, const int64_t *dims, const int32_t *sig_ol
     r.seg_div[nseg - 1] = make_div(range);
     r.nseg = nseg;
     r.all_pow2 = 1;
+    uint32_t bit = 0;
     for (int t = 0; t < nseg; ++t) {
         const uint64_t st = (uint64_t)r.seg_stride[t];
         if (!r.seg_div[t].pow2 || (st & (st - 1)) != 0) r.all_pow2 = 0;
         r.stride_shift[t] = st ? (uint32_t)__builtin_ctzll(st) : 0;
+        const uint32_t w = r.seg_div[t].shift;   // log2 of the segment's range when it is a power of two
+        r.in_shift[t] = bit;
+        r.seg_mask[t] = w >= 64 ? ~0ull : (1ull << w) - 1;
+        bit += w;
     }
     return r;
 }

@@ -1,4 +1,4 @@
-// lco_radix.cu -- histogram, offset-scan and scatter kernels of the stable LSD radix engine.
+// lco_radix.cu -- counting and single-sweep scatter kernels of the stable LSD radix engine.
 #include <atomic>
 
 #include "lco_radix.cuh"
@@ -8,19 +8,15 @@ namespace lco {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kUpItems = 8;       // histogram kernels: loads in flight per thread
-// direct-form scatter CTAs resident per SM (80 registers each, no spills;
-// measured 46.6 us per pass on the 3.4M-entry product permutation vs 48.3
-// at four per SM with spills); a build may
-// override it (and the bulk-form threshold below) to measure other shapes
+constexpr int kUpItems = 8;       // counting kernel: consecutive keys per thread and round
+// scatter CTAs resident per SM; a build may override it to measure others
 #ifndef LCO_SCATTER_CTAS
 #define LCO_SCATTER_CTAS 3
 #endif
 constexpr int kScatterCtas = LCO_SCATTER_CTAS;
-constexpr int kScanItems = 16;    // offset scan: counts per thread
-constexpr int kScanTile = kRadixThreads * kScanItems;
-constexpr int kCtrUpsweep = 8;    // header counter: upsweep blocks finished
-constexpr int kCtrScan = 12;      // header counters [12, 12 + kMaxPasses): offset-scan tiles
+constexpr int kUpsweepCtasPerSm = 4;
+constexpr int kCtrUpsweep = 8;    // header counter: counting blocks finished
+constexpr int kCtrTile = 12;      // header counters [12, 12 + kMaxPasses): tiles taken by the q-th run pass
 
 // Element count; a device-side count never exceeds the capacity the
 // buffers were sized for.
@@ -30,26 +26,29 @@ __device__ __forceinline__ int64_t job_n(const RadixJob &j) {
     return n < j.n_cap ? n : j.n_cap;
 }
 
-// Range r of the G ranges: tiles [r T / G, (r + 1) T / G) of the T tiles
-// of n elements, so that ranges differ by at most one tile; the last tile
-// of the input is ragged.
+__host__ __device__ __forceinline__ int64_t tiles_of(int64_t n) { return (n + kRadixTile - 1) / kRadixTile; }
+
+// Range r of the G counting ranges: tiles [r T / G, (r + 1) T / G) of the
+// T tiles of n elements, so that ranges differ by at most one tile.
 __device__ __forceinline__ void range_of(const RadixJob &j, int64_t n, int64_t r, int64_t &lo, int64_t &hi) {
-    const int64_t T = (n + kRadixTile - 1) / kRadixTile;
+    const int64_t T = tiles_of(n);
     lo = (r * T / j.G) * kRadixTile;
     hi = ((r + 1) * T / j.G) * kRadixTile;
     if (lo > n) lo = n;
     if (hi > n) hi = n;
 }
 
-// Which buffers a pass reads and writes.  Active passes ping-pong between
-// dst and tmp so that the last active pass writes dst; the first active pass
-// reads the source (and re-linearises it).  With no active pass, the last
-// pass copies the re-linearised source to dst.
+// Which buffers a pass reads and writes.  Passes that run ping-pong between
+// dst and tmp so that the last one writes dst; the first one reads the
+// source (and re-linearises it).  With no pass to run, the last pass copies
+// the re-linearised source to dst.  q is the pass's rank among those that
+// run (it selects the look-back region and the tile counter).
 struct PassIO {
     const int64_t *sl;
     const double *sv;
     int64_t *dl;
     double *dv;
+    int q;
     bool run, first, copy;
 };
 
@@ -61,6 +60,7 @@ __device__ __forceinline__ PassIO pass_io(const RadixJob &j, int pass) {
     io.run = act || io.copy;
     int q = 0;
     for (int p = 0; p < pass; ++p) q += j.active[p] != 0;
+    io.q = q;
     io.first = io.copy || q == 0;
     const bool prev_in_dst = q > 0 && ((Q - 1 - (q - 1)) & 1) == 0;
     io.sl = io.first ? j.src_liv : (prev_in_dst ? j.dst_liv : j.tmp_liv);
@@ -71,214 +71,185 @@ __device__ __forceinline__ PassIO pass_io(const RadixJob &j, int pass) {
     return io;
 }
 
-// Look-back words of one offset scan: its tiles over the NB x G table.
-__host__ __device__ __forceinline__ int64_t scan_tiles(int NB, int G) {
-    return ((int64_t)NB * G + kScanTile - 1) / kScanTile;
-}
+// Look-back words, [flag:2 | value]: flag 0 = not yet published, 1 = the
+// tile's own count of the digit, 2 = the count over the tile and every tile
+// before it.  32-bit words when fewer than 2^30 elements can occur.  A
+// thread owns digits 2k and 2k + 1, whose words are adjacent: they are
+// published and read as one pair (each word is still written whole, so a
+// pair read may see one word newer than the other; each is judged by its
+// own flag).
+template <typename W>
+struct LbWord;
+
+template <>
+struct LbWord<uint32_t> {
+    static constexpr uint32_t kAgg = 1u << 30;
+    static constexpr uint32_t kIncl = 2u << 30;
+    static constexpr uint32_t kMask = (1u << 30) - 1;
+    __device__ static __forceinline__ uint32_t flag(uint32_t v) { return v >> 30; }
+    __device__ static __forceinline__ void store(uint32_t *p, uint32_t v) {
+        asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    }
+    __device__ static __forceinline__ void store2(uint32_t *p, uint32_t a, uint32_t b) {
+        asm volatile("st.relaxed.gpu.global.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(a), "r"(b) : "memory");
+    }
+    __device__ static __forceinline__ void load2(const uint32_t *p, uint32_t &a, uint32_t &b) {
+        asm volatile("ld.relaxed.gpu.global.v2.u32 {%0, %1}, [%2];" : "=r"(a), "=r"(b) : "l"(p) : "memory");
+    }
+    static constexpr int kBatch = 4;    // predecessor pairs fetched per look-back round
+};
+
+template <>
+struct LbWord<uint64_t> {
+    static constexpr uint64_t kAgg = 1ull << 62;
+    static constexpr uint64_t kIncl = 2ull << 62;
+    static constexpr uint64_t kMask = (1ull << 62) - 1;
+    __device__ static __forceinline__ uint64_t flag(uint64_t v) { return v >> 62; }
+    __device__ static __forceinline__ void store2(uint64_t *p, uint64_t a, uint64_t b) {
+        asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+    }
+    __device__ static __forceinline__ void load2(const uint64_t *p, uint64_t &a, uint64_t &b) {
+        asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+    }
+    static constexpr int kBatch = 4;
+};
 
 // ---------------------------------------------------------------------------
-// One read of the source keys: every pass's digit histogram per range
-// (counts_src) and, per range and pass, the one digit the range holds (-1
-// when it holds several, -2 when it is empty).  The last block to finish
+// One read of the source keys: every pass's digit counts over the whole
+// input (per-CTA counts in shared memory, added into the global table).
+// The last block to finish turns each pass's counts into the start of every
+// digit's run in that pass's output (an exclusive scan over the digits) and
 // marks the passes whose digit is the same over all the data (nothing to
-// do) and resets its counter.  Block 0 first clears the offset scans'
-// look-back words and tile counters (the scans run after this launch).
+// do).  Block 0 resets the scatter passes' tile counters; all blocks clear
+// the look-back words the first scatter pass to run will use.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const __grid_constant__ RadixJob j) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem_raw);
     __shared__ int s_last;
-    __shared__ int s_nz[kMaxPasses], s_dig[kMaxPasses];
+    __shared__ unsigned long long s_part[kRadixWarps + 1];
     const int NB = 1 << j.D;
     const int nh = j.P * NB;
-    if (blockIdx.x == 0) {
-        const int64_t nst = (int64_t)kMaxPasses * scan_tiles(NB, j.G);
-        for (int64_t i = threadIdx.x; i < nst; i += blockDim.x) j.scan_state[i] = 0;
-        if (threadIdx.x < kMaxPasses) j.counters[kCtrScan + threadIdx.x] = 0;
-    }
-    for (int i = threadIdx.x; i < nh; i += blockDim.x) s_hist[i] = 0;
-    if (threadIdx.x < kMaxPasses) {
-        s_nz[threadIdx.x] = 0;
-        s_dig[threadIdx.x] = 0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (blockIdx.x == 0 && tid < kMaxPasses) j.counters[kCtrTile + tid] = 0;
+    for (int i = tid; i < nh; i += blockDim.x) s_hist[i] = 0;
+    const int64_t n = job_n(j);
+    {
+        const int64_t words = tiles_of(n) * NB * (j.wide_lb ? 2 : 1);   // 32-bit words of region 0 in use
+        uint32_t *z = reinterpret_cast<uint32_t *>(j.lb);
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < words; i += (int64_t)gridDim.x * blockDim.x)
+            z[i] = 0;
     }
     __syncthreads();
 
-    const int64_t n = job_n(j);
     int64_t lo, hi;
     range_of(j, n, blockIdx.x, lo, hi);
     const uint32_t mask = (uint32_t)NB - 1;
-    // kUpItems independent loads in flight per thread
-    for (int64_t e0 = lo; e0 < hi; e0 += (int64_t)kUpItems * kRadixThreads) {
-        int64_t v[kUpItems];
+    // Each thread counts kUpItems consecutive keys per round and adds a run
+    // of equal digits with one shared atomic: keys sorted in their old order
+    // repeat digits in runs, and lanes at different places of such runs
+    // rarely hit the same counter at once (with one key per lane, a warp of
+    // neighbouring keys would serialise on a handful of counters).
+    // the next round's keys are loaded before this round's are counted
+    constexpr int64_t kStride = (int64_t)kUpItems * kRadixThreads;
+    int64_t e0 = lo + (int64_t)tid * kUpItems;
+    int64_t nxt[kUpItems];
 #pragma unroll
-        for (int i = 0; i < kUpItems; ++i) {
-            const int64_t e = e0 + i * kRadixThreads + threadIdx.x;
-            v[i] = e < hi ? j.src_liv[e] : -1;
-        }
+    for (int i = 0; i < kUpItems; ++i) nxt[i] = e0 + i < hi ? __ldg(j.src_liv + e0 + i) : 0;
+    for (; e0 < hi; e0 += kStride) {
+        uint64_t key[kUpItems];
+        const int m = hi - e0 < (int64_t)kUpItems ? (int)(hi - e0) : kUpItems;
 #pragma unroll
-        for (int i = 0; i < kUpItems; ++i) {
-            if (v[i] >= 0) {
-                const uint64_t key = divu(j.key_div, (uint64_t)relin(j.relin, v[i]));
-                for (int p = 0; p < j.P; ++p)
-                    atomicAdd(&s_hist[p * NB + (uint32_t)((key >> (p * j.D)) & mask)], 1u);
+        for (int i = 0; i < kUpItems; ++i) key[i] = (uint64_t)nxt[i];
+        const int64_t e1 = e0 + kStride;
+#pragma unroll
+        for (int i = 0; i < kUpItems; ++i) nxt[i] = e1 + i < hi ? __ldg(j.src_liv + e1 + i) : 0;
+#pragma unroll
+        for (int i = 0; i < kUpItems; ++i)
+            if (i < m) key[i] = divu(j.key_div, (uint64_t)relin(j.relin, (int64_t)key[i]));
+        for (int p = 0; p < j.P; ++p) {
+            uint32_t *h = s_hist + p * NB;
+            const int sh = p * j.D;
+            uint32_t cur = (uint32_t)(key[0] >> sh) & mask, cnt = 0;
+#pragma unroll
+            for (int i = 0; i < kUpItems; ++i) {
+                if (i < m) {
+                    const uint32_t d = (uint32_t)(key[i] >> sh) & mask;
+                    if (d != cur) {
+                        atomicAdd(&h[cur], cnt);
+                        cur = d;
+                        cnt = 0;
+                    }
+                    ++cnt;
+                }
             }
+            if (cnt) atomicAdd(&h[cur], cnt);
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nh; i += blockDim.x) {
-        const int p = i / NB, d = i - p * NB;
+    for (int i = tid; i < nh; i += blockDim.x) {
         const uint32_t c = s_hist[i];
-        j.counts_src[((int64_t)p * NB + d) * j.G + blockIdx.x] = c;
-        if (c) {
-            atomicAdd(&s_nz[p], 1);
-            s_dig[p] = d;   // read only when exactly one digit is present
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < j.P) {
-        const int p = threadIdx.x;
-        j.cdig[(int64_t)p * j.G + blockIdx.x] = lo >= hi ? -2 : (s_nz[p] == 1 ? s_dig[p] : -1);
+        if (c) atomicAdd(&j.hist[i], (unsigned long long)c);
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(&j.counters[kCtrUpsweep], 1u) == gridDim.x - 1);
+    if (tid == 0) s_last = (atomicAdd(&j.counters[kCtrUpsweep], 1u) == gridDim.x - 1);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
 
-    // last block: a pass is skipped when every non-empty range holds the same
-    // single digit
-    __shared__ int s_several[kMaxPasses], s_lo[kMaxPasses], s_hi[kMaxPasses];
-    if (threadIdx.x < kMaxPasses) {
-        s_several[threadIdx.x] = 0;
-        s_lo[threadIdx.x] = 1 << 30;
-        s_hi[threadIdx.x] = -1;
-    }
-    __syncthreads();
+    // last block: per pass, thread t owns digits [t * per, (t + 1) * per)
+    const int per = NB > kRadixThreads ? NB / kRadixThreads : 1;
+    const int d0 = tid * per;
+    int nactive = 0;
     for (int p = 0; p < j.P; ++p) {
-        int several = 0, dlo = 1 << 30, dhi = -1;
-        for (int r = threadIdx.x; r < j.G; r += blockDim.x) {
-            const int c = *reinterpret_cast<volatile const int32_t *>(j.cdig + (int64_t)p * j.G + r);
-            if (c == -1) several = 1;
-            if (c >= 0) {
-                dlo = c < dlo ? c : dlo;
-                dhi = c > dhi ? c : dhi;
+        volatile const unsigned long long *h = j.hist + (int64_t)p * NB;
+        unsigned long long c[8];
+        unsigned long long sum = 0;
+        int nz = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            c[i] = (i < per && d0 + i < NB) ? h[d0 + i] : 0ull;
+            sum += c[i];
+            nz += c[i] != 0;
+        }
+        unsigned long long x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += u;
+        }
+        if (lane == 31) s_part[warp] = x;
+        // a pass runs when more than one digit occurs
+        const int holders = __syncthreads_count(nz > 0);
+        const int multi = __syncthreads_or(nz > 1);
+        unsigned long long run = x - sum;
+        for (int w = 0; w < warp; ++w) run += s_part[w];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (i < per && d0 + i < NB) {
+                j.dstart[(int64_t)p * NB + d0 + i] = run;
+                run += c[i];
             }
         }
-        if (several) s_several[p] = 1;
-        if (dhi >= 0) {
-            atomicMin(&s_lo[p], dlo);
-            atomicMax(&s_hi[p], dhi);
-        }
+        const int act = (n > 0) && (holders > 1 || multi);
+        if (tid == 0) j.active[p] = act;
+        nactive += act;
+        __syncthreads();
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int nactive = 0;
-        for (int p = 0; p < j.P; ++p) {
-            const int act = (n > 0) && (s_several[p] || s_lo[p] != s_hi[p]);
-            j.active[p] = act;
-            nactive += act;
-        }
+    if (tid == 0) {
         j.active[16] = nactive;
         j.counters[kCtrUpsweep] = 0;
     }
 }
 
-// Per-range digit histogram of the buffer a later pass reads.
-__global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const __grid_constant__ RadixJob j, int pass) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem_raw);
-    const PassIO io = pass_io(j, pass);
-    if (!io.run || io.first) return;
-    const int NB = 1 << j.D;
-    for (int i = threadIdx.x; i < NB; i += blockDim.x) s_hist[i] = 0;
-    __syncthreads();
-    const int64_t n = job_n(j);
-    int64_t lo, hi;
-    range_of(j, n, blockIdx.x, lo, hi);
-    const uint32_t mask = (uint32_t)NB - 1;
-    const int shift = pass * j.D;
-    for (int64_t e0 = lo; e0 < hi; e0 += (int64_t)kUpItems * kRadixThreads) {
-        int64_t v[kUpItems];
-#pragma unroll
-        for (int i = 0; i < kUpItems; ++i) {
-            const int64_t e = e0 + i * kRadixThreads + threadIdx.x;
-            v[i] = e < hi ? io.sl[e] : -1;
-        }
-#pragma unroll
-        for (int i = 0; i < kUpItems; ++i)
-            if (v[i] >= 0) atomicAdd(&s_hist[(uint32_t)(divu(j.key_div, (uint64_t)v[i]) >> shift) & mask], 1u);
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < NB; d += blockDim.x) j.counts_hist[(int64_t)d * j.G + blockIdx.x] = s_hist[d];
-}
-
-// roffs[d][r] = the number of elements with a smaller digit, plus those with
-// digit d in ranges before r: the exclusive prefix sum of the digit-major
-// count table.  One single-pass scan (tiles taken in launch order, each
-// summing the tiles before it by decoupled look-back).
-__global__ void __launch_bounds__(kRadixThreads) k_radix_offsets(const __grid_constant__ RadixJob j, int pass) {
-    const PassIO io = pass_io(j, pass);
-    if (!io.run || io.copy) return;
-    __shared__ uint64_t s_wsum[kRadixWarps + 1];
-    __shared__ uint32_t s_tile;
-    const int NB = 1 << j.D;
-    const int64_t M = (int64_t)NB * j.G;
-    const uint32_t *cnt = io.first ? j.counts_src + (int64_t)pass * M : j.counts_hist;
-    uint64_t *state = j.scan_state + (int64_t)pass * scan_tiles(NB, j.G);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(&j.counters[kCtrScan + pass], 1u);
-    __syncthreads();
-    const int64_t tile = s_tile;
-    const int64_t base = tile * kScanTile + (int64_t)tid * kScanItems;
-    uint32_t c[kScanItems];
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) c[i] = base + i < M ? cnt[base + i] : 0u;
-    uint64_t sum = 0;
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) sum += c[i];
-    uint64_t x = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t u = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += u;
-    }
-    if (lane == 31) s_wsum[warp] = x;
-    __syncthreads();
-    uint64_t wex = 0, tot = 0;
-#pragma unroll
-    for (int w = 0; w < kRadixWarps; ++w) {
-        const uint64_t v = s_wsum[w];
-        wex += w < warp ? v : 0;
-        tot += v;
-    }
-    if (warp == 0) {
-        if (lane == 0) lb_store(state + tile, (tile == 0 ? kFlagIncl : kFlagAgg) | tot);
-        uint64_t ex = 0;
-        if (tile > 0) ex = lookback_warp(state, tile, j.status);
-        if (lane == 0) {
-            if (tile > 0) lb_store(state + tile, kFlagIncl | (ex + tot));
-            s_wsum[kRadixWarps] = ex;
-        }
-    }
-    __syncthreads();
-    uint64_t run = s_wsum[kRadixWarps] + wex + x - sum;
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        if (base + i < M) j.roffs[base + i] = run;
-        run += c[i];
-    }
-}
-
-// Shared memory of a scatter CTA: the staging buffer (key, value pairs), the
-// per-tile global base and running offset of every digit, the per-warp digit
-// counts (16 bits, warp-major: [warp][digit]) and the digit of every staged
-// element (used when a digit is not a plain shift of the key), rounded up to
-// 128 bytes (the bulk form's input buffers follow: copy destinations must be
-// aligned).
-__host__ __device__ constexpr size_t scatter_smem_bytes_base(int D) {
-    return ((size_t)kRadixTile * 18 + ((size_t)1 << D) * 16 + ((size_t)1 << D) * 2 * kRadixWarps + 64 + 127) &
-           ~(size_t)127;
+// Shared memory of a scatter CTA: the staged tile (key, value pairs), the
+// global base of every digit, the per-warp digit counts (16 bits,
+// warp-major: [warp][digit]) and the digit of every staged element (used
+// when a digit is not a plain shift of the key).
+__host__ __device__ constexpr size_t scatter_smem_bytes(int D) {
+    return (size_t)kRadixTile * 16 + ((size_t)1 << D) * 8 + ((size_t)1 << D) * 2 * kRadixWarps +
+           (size_t)kRadixTile * 2;
 }
 
 // Digit of a key in a pass: a shift when the key divisor is a power of two
@@ -291,252 +262,263 @@ __device__ __forceinline__ uint32_t key_digit(const RadixJob &j, int64_t key, in
 }
 
 // ---------------------------------------------------------------------------
-// One stable scatter pass: CTA r walks range r tile by tile (kRadixTile
-// elements, warp w holding elements w*256 + 32 i + lane of the tile), placing
-// each tile from running per-digit offsets.  Per tile:
-//   1. each warp ranks its items in element order: lanes with equal digits
-//      find each other with one match instruction, and the lowest of them
-//      reads and advances the warp's count of that digit; an item's rank is
-//      the count before it plus its peers in lower lanes;
-//   2. each thread turns the counts of its digits into per-warp slots (the
-//      tile-local start of that warp's run of the digit), the tile's global
-//      base of the digit and the running offset for the next tile -- one
-//      block scan over the digit totals;
-//   3. every item is staged, as one 16-byte (key, value) store, at slot +
-//      rank: the tile sorted by digit, stably;
-//   4. the staged tile is written out in order: each digit's run is a
-//      contiguous stretch of the output.
-// The count table is warp-major (a warp's counts are one row, so the random
-// digits of a warp spread over all shared-memory banks) and each thread of
-// step 2 owns pairs of digits (one 32-bit word per warp row).
-// Two forms:
-//   kBulk: the next input tile comes in by bulk copy while the current one is
-//     processed (double-buffered input, two CTAs per SM) -- ranges of many
-//     tiles;
-//   otherwise: tiles are loaded directly and kScatterCtas CTAs share an SM, filling
-//     each other's barrier gaps -- ranges of few tiles.
+// One stable scatter pass.  Each CTA takes the next tile (kRadixTile
+// elements, in order of a global counter; warp w holds elements
+// w * 256 + 32 i + lane of the tile) and:
+//   1. ranks its items within the warp in element order: lanes with equal
+//      digits find each other with one match instruction per item, and the
+//      lowest of them reads and advances the warp's count of that digit (the
+//      matches of all items first, then the chain of count updates);
+//   2. turns the per-warp counts into per-warp slots (the tile-local start
+//      of that warp's run of each digit) by one block scan over the digit
+//      totals, and publishes each digit's count in the tile;
+//   3. stages every item, as one 16-byte (key, value) store, at slot + rank:
+//      the tile sorted by digit, stably;
+//   2b. sums each digit's counts in the tiles before it by decoupled
+//      look-back (predecessors read a few at a time, the nearest inclusive
+//      word ends the walk) and publishes the inclusive count; the digit's
+//      global base is the start of its run in the pass's output plus that
+//      prefix (the staging of step 3 overlaps the wait);
+//   4. writes the staged tile out in order: each digit's run is a contiguous
+//      stretch of the output.
+// Every CTA also clears its slice of the look-back words of the next pass to
+// run (the previous pass that used them has finished).
 // ---------------------------------------------------------------------------
-template <bool kBulk, bool kShift>
-__global__ void __launch_bounds__(kRadixThreads, kBulk ? 2 : kScatterCtas)
+template <bool kShift, typename W>
+__global__ void __launch_bounds__(kRadixThreads, kScatterCtas)
     k_radix_scatter(const __grid_constant__ RadixJob j, int pass) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_wtot[kRadixWarps];
+    using LB = LbWord<W>;
     const PassIO io = pass_io(j, pass);
     if (!io.run) return;
     const int D = j.D;
     const int NB = 1 << D;
-    double2 *s_kv = reinterpret_cast<double2 *>(smem_raw);                                 // [kRadixTile]
-    int64_t *s_run = reinterpret_cast<int64_t *>(s_kv + kRadixTile);
-    int64_t *s_gb = s_run + NB;
-    uint16_t *s_cnt = reinterpret_cast<uint16_t *>(s_gb + NB);                            // [8][NB]
-    uint16_t *s_dig = s_cnt + (size_t)NB * kRadixWarps;                                    // [kRadixTile]
-    uint32_t *s_wtot = reinterpret_cast<uint32_t *>(s_dig + kRadixTile);                  // [8]
-    // bulk form only: the input buffers and their barrier, after the tables
-    int64_t *in_key = reinterpret_cast<int64_t *>(smem_raw + scatter_smem_bytes_base(D));
-    double *in_val = reinterpret_cast<double *>(in_key + kRadixTile);
-    uint64_t *s_bar = reinterpret_cast<uint64_t *>(in_val + kRadixTile);
-
+    double2 *s_kv = reinterpret_cast<double2 *>(smem_raw);                 // [kRadixTile]
+    int64_t *s_gb = reinterpret_cast<int64_t *>(s_kv + kRadixTile);        // [NB]
+    uint16_t *s_cnt = reinterpret_cast<uint16_t *>(s_gb + NB);             // [warps][NB]
+    uint16_t *s_dig = s_cnt + (size_t)NB * kRadixWarps;                    // [kRadixTile]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n = job_n(j);
-    int64_t lo, hi;
-    range_of(j, n, blockIdx.x, lo, hi);
+    const int64_t T = tiles_of(n);
     if (io.copy) {
-        for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+        const int64_t t = blockIdx.x;
+        if (t >= T) return;
+        const int64_t lo = t * kRadixTile, hi = lo + kRadixTile < n ? lo + kRadixTile : n;
+        for (int64_t e = lo + tid; e < hi; e += kRadixThreads) {
             io.dl[e] = relin(j.relin, io.sl[e]);
             io.dv[e] = io.sv[e];
         }
         return;
     }
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const size_t region = (size_t)tiles_of(j.n_cap) * (size_t)NB;
+    W *lb_cur = reinterpret_cast<W *>(j.lb) + (size_t)(io.q & 1) * region;
+    W *lb_next = reinterpret_cast<W *>(j.lb) + (size_t)((io.q + 1) & 1) * region;
+    if ((int64_t)blockIdx.x < T)
+        for (int d = tid; d < NB; d += kRadixThreads) lb_next[(size_t)blockIdx.x * NB + d] = 0;
+    if (tid == 0) s_tile = atomicAdd(&j.counters[kCtrTile + io.q], 1u);
+    uint32_t *cnt_words = reinterpret_cast<uint32_t *>(s_cnt);
+    const int nwords = NB / 2;    // word k holds the counts of digits 2k and 2k + 1
+    for (int i = tid; i < nwords * kRadixWarps; i += kRadixThreads) cnt_words[i] = 0;
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= T) return;
+    const int64_t tbase = tile * kRadixTile;
+    const int tile_n = (int)(n - tbase < (int64_t)kRadixTile ? n - tbase : (int64_t)kRadixTile);
+    const int wofs = warp * (32 * kRadixItems) + lane;    // tile-local index of item 0
+    const int lim = tile_n - wofs;                        // item i is valid iff 32 i < lim
+
+    // ---- 1. load, digits, stable ranks within the warp ----
+    int64_t keys[kRadixItems];
+    double vals[kRadixItems];
+    {
+        const int64_t *kp = io.sl + tbase + wofs;
+        const double *vp = io.sv + tbase + wofs;
+#pragma unroll
+        for (int i = 0; i < kRadixItems; ++i) {
+            const bool valid = i * 32 < lim;
+            keys[i] = valid ? __ldg(kp + i * 32) : 0;
+            vals[i] = valid ? __ldg(vp + i * 32) : 0.0;
+        }
+    }
     const uint32_t mask = (uint32_t)NB - 1;
     const int shift = kShift ? (int)j.key_div.shift + pass * D : pass * D;
-    // count-table words owned by this thread in step 2: [w0, w0 + wpt) of
-    // each warp row (word k holds digits 2k and 2k + 1)
-    const int nwords = NB >= 2 ? NB / 2 : 1;
-    const int wpt = nwords > kRadixThreads ? nwords / kRadixThreads : 1;
-    const int w0 = tid * wpt;
-    uint32_t *cnt_words = reinterpret_cast<uint32_t *>(s_cnt);
-    for (int d = tid; d < NB; d += kRadixThreads) s_run[d] = (int64_t)j.roffs[(int64_t)d * j.G + blockIdx.x];
-    for (int i = tid; i < NB * kRadixWarps / 2; i += kRadixThreads) cnt_words[i] = 0;
-    const unsigned lt = lanemask_lt();
+    uint32_t lab[kRadixItems];
+#pragma unroll
+    for (int i = 0; i < kRadixItems; ++i) {
+        const bool valid = i * 32 < lim;
+        if (valid && io.first) keys[i] = relin(j.relin, keys[i]);
+        // invalid lanes carry labels no valid lane has (digits are < 2^11)
+        lab[i] = valid ? key_digit<kShift>(j, keys[i], shift, mask) : (0x10000u | (uint32_t)lane);
+    }
+    unsigned peers[kRadixItems];
+#pragma unroll
+    for (int i = 0; i < kRadixItems; ++i) peers[i] = __match_any_sync(kFull, lab[i]);
     uint16_t *wcnt = s_cnt + (size_t)warp * NB;
-    // bulk form: the next tile is copied in while the current one is
-    // processed, when both input arrays are 16-byte aligned (tile starts are
-    // even element offsets); an odd last element is read directly
-    const bool bulk = kBulk && ((reinterpret_cast<uintptr_t>(io.sl) | reinterpret_cast<uintptr_t>(io.sv)) & 15) == 0;
-    uint32_t parity = 0;
-    auto issue = [&](int64_t base) {
-        const int64_t m = (hi - base < (int64_t)kRadixTile ? hi - base : (int64_t)kRadixTile) & ~(int64_t)1;
-        if (m <= 0) return;
-        const uint32_t bytes = (uint32_t)(m * 8);
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(s_bar, 2 * bytes);
-        bulk_copy_g2s(in_key, io.sl + base, bytes, s_bar);
-        bulk_copy_g2s(in_val, io.sv + base, bytes, s_bar);
-    };
-    if (bulk && tid == 0) {
-        mbar_init(s_bar, 1);
-        if (lo < hi) issue(lo);
+    uint32_t cb[kRadixItems];
+#pragma unroll
+    for (int i = 0; i < kRadixItems; ++i) {
+        uint32_t c = 0;
+        if (lane == __ffs(peers[i]) - 1 && lab[i] < 0x10000u) {
+            c = wcnt[lab[i]];
+            wcnt[lab[i]] = (uint16_t)(c + (uint32_t)__popc(peers[i]));
+        }
+        cb[i] = c;
+        __syncwarp();
+    }
+    const unsigned lt = lanemask_lt();
+    uint32_t dr[kRadixItems];    // digit | rank within the warp's run of the digit << 16
+#pragma unroll
+    for (int i = 0; i < kRadixItems; ++i) {
+        const uint32_t c = __shfl_sync(kFull, cb[i], __ffs(peers[i]) - 1);
+        dr[i] = (lab[i] & 0xffffu) | ((c + (uint32_t)__popc(peers[i] & lt)) << 16);
     }
     __syncthreads();
 
-    for (int64_t tile_base = lo; tile_base < hi; tile_base += kRadixTile) {
-        const int tile_n = (int)((hi - tile_base) < (int64_t)kRadixTile ? (hi - tile_base) : (int64_t)kRadixTile);
-        // this warp's valid items: i * 32 + lane < wn
-        const int wn = tile_n - warp * (32 * kRadixItems);
-        const int bulk_n = bulk ? (tile_n & ~1) : 0;     // elements that arrived by bulk copy
-        if (bulk && bulk_n > 0) {
-            const bool ok = mbar_wait_bounded(s_bar, parity);
-            parity ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) set_error(j.status, LCO_ERR_TIMEOUT);
-                return;
-            }
-        }
-        // ---- 1. load, digits, stable ranks within the warp ----
-        int64_t keys[kRadixItems];
-        double vals[kRadixItems];
-        uint32_t dr[kRadixItems];    // digit | rank within the warp's run << 16
-        const int wofs = warp * (32 * kRadixItems) + lane;    // tile-local index of item 0
-        const int64_t *kp = io.sl + tile_base + wofs;
-        const double *vp = io.sv + tile_base + wofs;
-#pragma unroll
-        for (int i = 0; i < kRadixItems; ++i) {
-            const int li = wofs + i * 32;
-            keys[i] = 0;
-            vals[i] = 0.0;
-            if (li < bulk_n) {
-                keys[i] = in_key[li];
-                vals[i] = in_val[li];
-            } else if (i * 32 + lane < wn) {
-                keys[i] = __ldg(kp + i * 32);
-                vals[i] = __ldg(vp + i * 32);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < kRadixItems; ++i) {
-            const bool valid = i * 32 + lane < wn;
-            uint32_t d = 0;
-            if (valid) {
-                if (io.first) keys[i] = relin(j.relin, keys[i]);
-                d = key_digit<kShift>(j, keys[i], shift, mask);
-            }
-            // lanes holding the same digit (invalid lanes carry labels no
-            // valid lane has: digits are < 2^11).  One match instruction;
-            // measured against one ballot per digit bit, it is faster on
-            // keys whose warps hold few distinct digits (the 3.4M-entry
-            // product of the 64^3 Laplacian and a derivative: 48 vs 54 us
-            // per pass) and slower on uniform random keys (69 vs 64).
-            const unsigned peers = __match_any_sync(kFull, valid ? d : 0x10000u | (uint32_t)lane);
-            const int leader = __ffs(peers) - 1;
-            uint32_t c = 0;
-            if (valid && lane == leader) {
-                c = wcnt[d];
-                wcnt[d] = (uint16_t)(c + (uint32_t)__popc(peers));
-            }
-            c = __shfl_sync(kFull, c, leader);
-            dr[i] = d | ((c + (uint32_t)__popc(peers & lt)) << 16);
-            __syncwarp();
-        }
-        __syncthreads();
-        // the input buffer is free: fetch the next tile behind this one's work
-        if (bulk && tid == 0 && tile_base + kRadixTile < hi) issue(tile_base + kRadixTile);
-        // ---- 2. per-warp slots, the tile's global bases, running offsets ----
-        {
-            uint32_t tsum = 0;
-            for (int q = 0; q < wpt; ++q) {
-                const int k = w0 + q;
-                if (k < nwords) {
-                    uint32_t s2 = 0;
-#pragma unroll
-                    for (int w = 0; w < kRadixWarps; ++w) s2 += cnt_words[w * nwords + k];
-                    tsum += (s2 & 0xffffu) + (s2 >> 16);    // a half never carries (< 2^12 per word)
-                }
-            }
-            // exclusive scan of the thread sums (digits are owned in order)
-            uint32_t x = tsum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t u = __shfl_up_sync(kFull, x, o);
-                if (lane >= o) x += u;
-            }
-            if (lane == 31) s_wtot[warp] = x;
-            __syncthreads();
-            uint32_t run = x - tsum;
-#pragma unroll
-            for (int w = 0; w < kRadixWarps; ++w) run += w < warp ? s_wtot[w] : 0u;
-            for (int q = 0; q < wpt; ++q) {
-                const int k = w0 + q;
-                if (k < nwords) {
-                    // low halves (digit 2k) become slots in one sweep down the
-                    // warp rows, high halves (digit 2k + 1) in a second
-                    const uint32_t ts_lo = run;
-#pragma unroll
-                    for (int w = 0; w < kRadixWarps; ++w) {
-                        const uint32_t v = cnt_words[w * nwords + k];
-                        cnt_words[w * nwords + k] = (v & 0xffff0000u) | run;
-                        run += v & 0xffffu;
-                    }
-                    const uint32_t ts_hi = run;
-#pragma unroll
-                    for (int w = 0; w < kRadixWarps; ++w) {
-                        const uint32_t v = cnt_words[w * nwords + k];
-                        cnt_words[w * nwords + k] = (v & 0xffffu) | (run << 16);
-                        run += v >> 16;
-                    }
-                    const int dlo = 2 * k;
-                    if (dlo < NB) {
-                        const int64_t r0 = s_run[dlo];
-                        s_gb[dlo] = r0 - (int64_t)ts_lo;
-                        s_run[dlo] = r0 + (int64_t)(ts_hi - ts_lo);
-                    }
-                    if (dlo + 1 < NB) {
-                        const int64_t r1 = s_run[dlo + 1];
-                        s_gb[dlo + 1] = r1 - (int64_t)ts_hi;
-                        s_run[dlo + 1] = r1 + (int64_t)(run - ts_hi);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // ---- 3. staging at the sorted tile-local position ----
-#pragma unroll
-        for (int i = 0; i < kRadixItems; ++i) {
-            if (i * 32 + lane < wn) {
-                const uint32_t d = dr[i] & 0xffffu;
-                const uint32_t pos = (uint32_t)wcnt[d] + (dr[i] >> 16);
-                s_kv[pos] = make_double2(__longlong_as_double(keys[i]), vals[i]);
-                if (!kShift) s_dig[pos] = (uint16_t)d;
-            }
-        }
-        __syncthreads();
-        // ---- 4. write-out in staged order; reset this thread's count words ----
-#pragma unroll
-        for (int q = 0; q < kRadixItems; ++q) {
-            const int i = tid + q * kRadixThreads;
-            if (i < tile_n) {
-                const double2 kv = s_kv[i];
-                const int64_t k = __double_as_longlong(kv.x);
-                const uint32_t d = kShift ? key_digit<true>(j, k, shift, mask) : (uint32_t)s_dig[i];
-                const int64_t g = s_gb[d] + i;
-                io.dl[g] = k;
-                io.dv[g] = kv.y;
-            }
-        }
+    // ---- 2. per-warp slots and tile counts; the counts are published ----
+    const int wpt = nwords > kRadixThreads ? nwords / kRadixThreads : 1;   // 1, 2 or 4
+    const int w0 = tid * wpt;
+    {
+        uint32_t tsum = 0;
         for (int q = 0; q < wpt; ++q) {
             const int k = w0 + q;
             if (k < nwords) {
+                uint32_t s2 = 0;
 #pragma unroll
-                for (int w = 0; w < kRadixWarps; ++w) cnt_words[w * nwords + k] = 0;
+                for (int w = 0; w < kRadixWarps; ++w) s2 += cnt_words[w * nwords + k];
+                tsum += (s2 & 0xffffu) + (s2 >> 16);    // a half never carries (<= 2048 per digit)
             }
         }
+        // exclusive scan of the thread sums (digits are owned in order)
+        uint32_t x = tsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += u;
+        }
+        if (lane == 31) s_wtot[warp] = x;
         __syncthreads();
+        uint32_t run = x - tsum;
+#pragma unroll
+        for (int w = 0; w < kRadixWarps; ++w) run += w < warp ? s_wtot[w] : 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = w0 + q;
+            if (q >= wpt || k >= nwords) break;
+            uint32_t v[kRadixWarps];
+#pragma unroll
+            for (int w = 0; w < kRadixWarps; ++w) v[w] = cnt_words[w * nwords + k];
+            uint32_t r = run;
+            uint32_t sl[kRadixWarps];
+#pragma unroll
+            for (int w = 0; w < kRadixWarps; ++w) {
+                sl[w] = r;
+                r += v[w] & 0xffffu;
+            }
+            const uint32_t ts_hi = r;
+#pragma unroll
+            for (int w = 0; w < kRadixWarps; ++w) {
+                cnt_words[w * nwords + k] = sl[w] | (r << 16);
+                r += v[w] >> 16;
+            }
+            const uint32_t c_lo = ts_hi - run, c_hi = r - ts_hi;
+            // until step 2b, a digit's base slot holds its tile-local start and count
+            s_gb[2 * k] = (int64_t)((run << 16) | c_lo);
+            s_gb[2 * k + 1] = (int64_t)((ts_hi << 16) | c_hi);
+            run = r;
+            const W flag = tile == 0 ? LB::kIncl : LB::kAgg;
+            LB::store2(lb_cur + (size_t)tile * NB + 2 * k, flag | (W)c_lo, flag | (W)c_hi);
+        }
+    }
+    __syncthreads();
+    // ---- 3. staging at the sorted tile-local position ----
+#pragma unroll
+    for (int i = 0; i < kRadixItems; ++i) {
+        if (i * 32 < lim) {
+            const uint32_t d = dr[i] & 0xffffu;
+            const uint32_t pos = (uint32_t)wcnt[d] + (dr[i] >> 16);
+            s_kv[pos] = make_double2(__longlong_as_double(keys[i]), vals[i]);
+            if (!kShift) s_dig[pos] = (uint16_t)d;
+        }
+    }
+    // ---- 2b. counts of the tiles before (look-back), global bases ----
+    {
+        const unsigned long long *dst = j.dstart + (int64_t)pass * NB;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = w0 + q;
+            if (q >= wpt || k >= nwords) break;
+            const uint32_t x_lo = (uint32_t)s_gb[2 * k], x_hi = (uint32_t)s_gb[2 * k + 1];
+            W e_lo = 0, e_hi = 0;
+            if (tile > 0) {
+                // Predecessors are read kBatch pairs at a time and consumed
+                // nearest first; a digit's walk ends at its first inclusive
+                // word (measured: 16 pairs per round cost more instructions
+                // than the round trips they save).
+                constexpr int B = LB::kBatch;
+                W *my = lb_cur + (size_t)tile * NB + 2 * k;
+                bool f_lo = false, f_hi = false;
+                const long long t0 = clock64();
+                for (int64_t t = tile - 1; !(f_lo && f_hi); t -= B) {
+                    W a[B], b[B];
+#pragma unroll
+                    for (int i = 0; i < B; ++i) {
+                        a[i] = LB::kIncl;
+                        b[i] = LB::kIncl;
+                        if (t - i >= 0) LB::load2(lb_cur + (size_t)(t - i) * NB + 2 * k, a[i], b[i]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < B; ++i) {
+                        if (f_lo && f_hi) break;
+                        while ((!f_lo && LB::flag(a[i]) == 0) || (!f_hi && LB::flag(b[i]) == 0)) {
+                            if (clock64() - t0 > kSpinBudgetCycles) {
+                                set_error(j.status, LCO_ERR_TIMEOUT);
+                                f_lo = f_hi = true;
+                                break;
+                            }
+                            __nanosleep(32);
+                            W a2, b2;
+                            LB::load2(lb_cur + (size_t)(t - i) * NB + 2 * k, a2, b2);
+                            if (LB::flag(a[i]) == 0) a[i] = a2;
+                            if (LB::flag(b[i]) == 0) b[i] = b2;
+                        }
+                        if (!f_lo) {
+                            e_lo += a[i] & LB::kMask;
+                            f_lo = LB::flag(a[i]) == 2;
+                        }
+                        if (!f_hi) {
+                            e_hi += b[i] & LB::kMask;
+                            f_hi = LB::flag(b[i]) == 2;
+                        }
+                    }
+                }
+                LB::store2(my, LB::kIncl | (e_lo + (W)(x_lo & 0xffffu)), LB::kIncl | (e_hi + (W)(x_hi & 0xffffu)));
+            }
+            s_gb[2 * k] = (int64_t)dst[2 * k] + (int64_t)e_lo - (int64_t)(x_lo >> 16);
+            s_gb[2 * k + 1] = (int64_t)dst[2 * k + 1] + (int64_t)e_hi - (int64_t)(x_hi >> 16);
+        }
+    }
+    __syncthreads();
+    // ---- 4. write-out in staged order ----
+#pragma unroll
+    for (int q = 0; q < kRadixItems; ++q) {
+        const int i = tid + q * kRadixThreads;
+        if (i < tile_n) {
+            const double2 kv = s_kv[i];
+            const int64_t k = __double_as_longlong(kv.x);
+            const uint32_t d = kShift ? key_digit<true>(j, k, shift, mask) : (uint32_t)s_dig[i];
+            const int64_t g = s_gb[d] + i;
+            io.dl[g] = k;
+            io.dv[g] = kv.y;
+        }
     }
 }
 
-size_t scatter_smem_bytes(int D, bool bulk) {
-    return scatter_smem_bytes_base(D) + (bulk ? (size_t)kRadixTile * 16 + 16 : 0);
-}
-
 size_t upsweep_smem_bytes(int D, int P) { return (size_t)P * ((size_t)1 << D) * 4; }
+
+// Look-back words are 32-bit below this many elements.
+constexpr int64_t kNarrowLbMax = (int64_t)1 << 30;
 
 }  // namespace
 
@@ -551,24 +533,10 @@ int radix_sm_count() {
     return sms;
 }
 
-// Up to kBulkMinTiles tiles per CTA of a full direct-form wave, the direct
-// scatter runs; beyond, the bulk-copy form (two CTAs per SM, at least eight
-// tiles per range).
-#ifndef LCO_BULK_MIN_TILES
-#define LCO_BULK_MIN_TILES 4
-#endif
-constexpr int64_t kBulkMinTiles = LCO_BULK_MIN_TILES;
-
-bool radix_bulk(int64_t n_cap) {
-    const int64_t tiles = (n_cap + kRadixTile - 1) / kRadixTile;
-    return tiles > kBulkMinTiles * kScatterCtas * (int64_t)radix_sm_count();
-}
-
-// One range per scatter CTA of a full wave (or one per tile, when there are
-// fewer tiles than that).
+// One counting CTA per range of whole tiles, up to kUpsweepCtasPerSm per SM.
 int radix_ranges(int64_t n_cap) {
-    const int64_t tiles = (n_cap + kRadixTile - 1) / kRadixTile;
-    const int64_t gmax = (radix_bulk(n_cap) ? 2 : kScatterCtas) * (int64_t)radix_sm_count();
+    const int64_t tiles = tiles_of(n_cap);
+    const int64_t gmax = (int64_t)kUpsweepCtasPerSm * radix_sm_count();
     int64_t g = tiles < gmax ? tiles : gmax;
     if (g < 1) g = 1;
     return (int)g;
@@ -576,43 +544,34 @@ int radix_ranges(int64_t n_cap) {
 
 size_t radix_state_bytes(int64_t n_cap, int D, int P) {
     const size_t NB = (size_t)1 << D;
-    const size_t G = (size_t)radix_ranges(n_cap);
+    const size_t wsz = n_cap >= kNarrowLbMax ? 8 : 4;
     size_t b = 0;
-    b += align_up(32 * 4);                                                  // active
-    b += align_up((size_t)kMaxPasses * G * 4);                              // cdig
-    b += align_up((size_t)kMaxPasses * scan_tiles((int)NB, (int)G) * 8);   // scan_state
-    b += align_up((size_t)P * G * NB * 4);                                  // counts_src
-    b += align_up(G * NB * 4);                                              // counts_hist
-    b += align_up(G * NB * 8);                                              // roffs
+    b += align_up(32 * 4);                                   // active
+    b += align_up((size_t)P * NB * 8);                       // hist
+    b += align_up((size_t)P * NB * 8);                       // dstart
+    b += align_up(2 * (size_t)tiles_of(n_cap) * NB * wsz);   // look-back regions
     return b;
 }
 
-// Nothing in the engine's region needs to be zero before a call (the
-// upsweep clears what the scans wait on); callers that clear this many
-// leading bytes of it only reset the pass flags, which every call rewrites.
 size_t radix_hist_table_bytes() { return align_up(32 * 4); }
 
 void radix_carve(RadixJob &job, char *region) {
     const size_t NB = (size_t)1 << job.D;
     job.G = radix_ranges(job.n_cap);
-    const size_t G = (size_t)job.G;
+    job.wide_lb = job.n_cap >= kNarrowLbMax ? 1 : 0;
     char *p = region;
     job.active = reinterpret_cast<int32_t *>(p); p += align_up(32 * 4);
-    job.cdig = reinterpret_cast<int32_t *>(p); p += align_up((size_t)kMaxPasses * G * 4);
-    job.scan_state = reinterpret_cast<uint64_t *>(p);
-    p += align_up((size_t)kMaxPasses * scan_tiles((int)NB, (int)G) * 8);
-    job.counts_src = reinterpret_cast<uint32_t *>(p); p += align_up((size_t)job.P * G * NB * 4);
-    job.counts_hist = reinterpret_cast<uint32_t *>(p); p += align_up(G * NB * 4);
-    job.roffs = reinterpret_cast<uint64_t *>(p);
+    job.hist = reinterpret_cast<unsigned long long *>(p); p += align_up((size_t)job.P * NB * 8);
+    job.dstart = reinterpret_cast<unsigned long long *>(p); p += align_up((size_t)job.P * NB * 8);
+    job.lb = p;
 }
 
 namespace {
 
-template <bool kBulk, bool kShift>
-void launch_scatter(const RadixJob &job, int p, cudaStream_t stream) {
+template <bool kShift, typename W>
+void launch_scatter(const RadixJob &job, int p, unsigned grid, cudaStream_t stream) {
     LCO_LAUNCH("k_radix_scatter", stream,
-               (k_radix_scatter<kBulk, kShift><<<(unsigned)job.G, kRadixThreads, scatter_smem_bytes(job.D, kBulk),
-                                                  stream>>>(job, p)));
+               (k_radix_scatter<kShift, W><<<grid, kRadixThreads, scatter_smem_bytes(job.D), stream>>>(job, p)));
 }
 
 }  // namespace
@@ -624,38 +583,33 @@ cudaError_t radix_enqueue(const RadixJob &job, cudaStream_t stream) {
     cudaGetDevice(&dev);
     const uint64_t bit = 1ull << (dev & 63);
     if (!(attr_done.load() & bit)) {
-        const int bulk_bytes = (int)scatter_smem_bytes(kMaxDigitBits, true);
-        const int direct_bytes = (int)scatter_smem_bytes(kMaxDigitBits, false);
-        cudaFuncSetAttribute(k_radix_scatter<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bulk_bytes);
-        cudaFuncSetAttribute(k_radix_scatter<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bulk_bytes);
-        cudaFuncSetAttribute(k_radix_scatter<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, direct_bytes);
-        cudaFuncSetAttribute(k_radix_scatter<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, direct_bytes);
+        const int bytes = (int)scatter_smem_bytes(kMaxDigitBits);
+        cudaFuncSetAttribute(k_radix_scatter<true, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaFuncSetAttribute(k_radix_scatter<false, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaFuncSetAttribute(k_radix_scatter<true, uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaFuncSetAttribute(k_radix_scatter<false, uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         cudaFuncSetAttribute(k_radix_upsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)upsweep_smem_bytes(kMaxDigitBits, kMaxPasses));
         attr_done.fetch_or(bit);
     }
     if (job.n_cap <= 0) return cudaSuccess;
-    const unsigned G = (unsigned)job.G;
     const int NB = 1 << job.D;
-    const unsigned scan_grid = (unsigned)scan_tiles(NB, job.G);
-    LCO_LAUNCH("k_radix_upsweep", stream,
-               k_radix_upsweep<<<G, kRadixThreads, upsweep_smem_bytes(job.D, job.P), stream>>>(job));
-    cudaError_t err = cudaGetLastError();
+    // the counting launch adds into the digit table: clear it first
+    cudaError_t err = cudaMemsetAsync(job.hist, 0, (size_t)job.P * NB * 8, stream);
     if (err != cudaSuccess) return err;
-    const bool bulk = radix_bulk(job.n_cap);
+    LCO_LAUNCH("k_radix_upsweep", stream,
+               k_radix_upsweep<<<(unsigned)job.G, kRadixThreads, upsweep_smem_bytes(job.D, job.P), stream>>>(job));
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    const unsigned grid = (unsigned)tiles_of(job.n_cap);
     const bool shift = job.key_div.pow2 != 0;
     for (int p = 0; p < job.P; ++p) {
-        if (p > 0) {
-            LCO_LAUNCH("k_radix_hist", stream,
-                       k_radix_hist<<<G, kRadixThreads, (size_t)NB * 4, stream>>>(job, p));
-        }
-        LCO_LAUNCH("k_radix_offsets", stream, k_radix_offsets<<<scan_grid, kRadixThreads, 0, stream>>>(job, p));
-        if (bulk) {
-            if (shift) launch_scatter<true, true>(job, p, stream);
-            else launch_scatter<true, false>(job, p, stream);
+        if (job.wide_lb) {
+            if (shift) launch_scatter<true, uint64_t>(job, p, grid, stream);
+            else launch_scatter<false, uint64_t>(job, p, grid, stream);
         } else {
-            if (shift) launch_scatter<false, true>(job, p, stream);
-            else launch_scatter<false, false>(job, p, stream);
+            if (shift) launch_scatter<true, uint32_t>(job, p, grid, stream);
+            else launch_scatter<false, uint32_t>(job, p, grid, stream);
         }
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;

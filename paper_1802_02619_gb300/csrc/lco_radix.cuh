@@ -2,16 +2,15 @@
 //
 // Used for the permutation of Sec. 4 (keys are re-linearised LIVs shaved by
 // the resting suffix, Sec. 4.1) and for sorting product lists by output LIV
-// (SOP, Sec. 5.2.5).  The input's tiles are split into G contiguous ranges
-// of whole tiles, one CTA each.  One launch reads the keys once and computes
-// every pass's digit histogram per range, and marks passes whose digit is
-// the same for every element (those are skipped on the device).  A pass is
-// then: the start of every (digit, range) run in the output -- one exclusive
-// scan over the digit-major count table -- and a scatter in which each CTA
-// walks its range tile by tile, ranking each tile with warp match
-// instructions and advancing running per-digit offsets, so no CTA waits on
-// another.  Passes after the first one that runs histogram the intermediate
-// buffer first.
+// (SOP, Sec. 5.2.5).  One launch reads the keys once and counts every
+// pass's digits over the whole input; its last block turns the counts into
+// the start of every digit's run in each pass's output and marks passes
+// whose digit is the same for every element (those are skipped on the
+// device).  A pass is then a single scatter launch: each CTA takes the next
+// 2048-element tile in order, ranks it with warp match instructions,
+// publishes its per-digit counts and finds the counts of the tiles before it
+// by decoupled look-back, so that the tile's runs land at their final place
+// without a separate counting or offset launch.
 #pragma once
 
 #include "lco_internal.cuh"
@@ -33,14 +32,14 @@ constexpr int kMaxDigitBits = 11;
 #endif
 constexpr int kDefaultDigitBits = LCO_DEFAULT_DIGIT_BITS;   // a build may override it to measure others
 constexpr int kMaxPasses = 6;
-constexpr int kUpsweepCtasPerSm = 4;
 
 struct RadixJob {
     RelinParams relin;     // applied to source keys on first read (identity allowed)
     DivU64 key_div;        // key = relin(liv) div key_div
     int32_t D;             // digit bits
     int32_t P;             // passes
-    int32_t G;             // input ranges (one CTA each), fixed from n_cap
+    int32_t G;             // counting CTAs (contiguous ranges of whole tiles), fixed from n_cap
+    int32_t wide_lb;       // look-back words are 64-bit (capacity of 2^30 elements or more)
     int64_t n_host;        // element count, or
     const int64_t *n_dev;  // device element count (overrides n_host when set)
     int64_t n_cap;         // upper bound on the element count (sizes grids and tables)
@@ -50,14 +49,12 @@ struct RadixJob {
     double *dst_val;
     int64_t *tmp_liv;
     double *tmp_val;
-    // workspace pieces (digit-major tables: entry [d][r] at d * G + r)
-    int32_t *active;       // [kMaxPasses] pass runs (digit not constant) + count at [16]
-    int32_t *cdig;         // [kMaxPasses][G] the one digit of a range, -1 several, -2 empty range
-    uint32_t *counts_src;  // [P][NB][G] per-range counts over the source order
-    uint32_t *counts_hist; // [NB][G] per-range counts before a later pass
-    uint64_t *roffs;       // [NB][G] start of each (digit, range) run in the output of a pass
-    uint64_t *scan_state;  // [kMaxPasses][scan tiles] look-back words of the offset scans
-    uint32_t *counters;    // header counters: [8] upsweep "last block", [12 + p] scan tiles of pass p
+    // workspace pieces
+    int32_t *active;               // [kMaxPasses] pass runs (digit not constant) + count at [16]
+    unsigned long long *hist;      // [P][NB] digit counts over the input (cleared by radix_enqueue)
+    unsigned long long *dstart;    // [P][NB] start of digit d's run in the output of pass p
+    void *lb;                      // [2][tiles][NB] look-back words (two alternating regions)
+    uint32_t *counters;            // header counters: [8] counting "last block", [12 + q] tiles of the q-th run pass
     int32_t *status;
 };
 
@@ -72,7 +69,7 @@ inline void radix_digits(int key_bits, int *D, int *P, int max_bits = kDefaultDi
     *P = p;
 }
 
-// Number of input ranges for up to n_cap elements.
+// Number of counting CTAs for up to n_cap elements.
 int radix_ranges(int64_t n_cap);
 // Bytes of workspace the engine needs for up to n_cap elements (excluding the
 // header and excluding the tmp buffers when those are supplied elsewhere).
@@ -80,9 +77,11 @@ size_t radix_state_bytes(int64_t n_cap, int D, int P);
 // Lays the engine's pieces out in `region` (which must hold
 // radix_state_bytes bytes); counters/status live in the caller's header.
 void radix_carve(RadixJob &job, char *region);
-// Enqueues the histogram launch and P scatter launches.
+// Enqueues the counting launch and P scatter launches (and clears the digit
+// counts before them).
 cudaError_t radix_enqueue(const RadixJob &job, cudaStream_t stream);
-// Bytes of the digit-histogram table at the start of a carved region.
+// Leading bytes of a carved region that a caller may clear before a call
+// (the pass flags; every call rewrites them, so clearing is optional).
 size_t radix_hist_table_bytes();
 int radix_sm_count();
 
