@@ -137,3 +137,46 @@ def test_unaligned_buffers(nnz):
     assert p.device_status() == 0
     assert np.array_equal(out_l[1:].cpu().numpy(), rl)
     assert np.array_equal(out_v[1:].cpu().numpy().view(np.int64), rv.view(np.int64))
+
+
+def _run_with_path(T, new_sig):
+    """Permutes through a Permuter and returns (liv, val, high_digit_first):
+    the last from the radix engine's pass flags at the start of the
+    workspace's region (after the 256-byte header): [17] is set when the
+    device chose to sort by the high digit first."""
+    t = dev(T)
+    p = lco.Permuter(T["dims"], T["sig"], new_sig, T["liv"].shape[0], device="cuda")
+    liv, val = p(t.liv, t.val)
+    torch.cuda.synchronize()
+    assert p.device_status() == 0
+    flags = p.ws[256:256 + 32 * 4].view(torch.int32).cpu().numpy()
+    return liv.cpu().numpy(), val.cpu().numpy(), bool(flags[17])
+
+
+def test_high_digit_first_and_fallback():
+    """Two-pass keys: with every high-digit bucket within one CTA's capacity
+    the device sorts by the high digit first and each bucket locally by the
+    low digit; one oversized bucket sends the same keys through the two LSD
+    passes.  Both must equal the oracle bit for bit."""
+    dims, sig, new = [256, 64, 64], [2, 1, 0], [0, 1, 2]
+    # mode 0 keeps its place (resting): the key is (mode 2, mode 1), 12 bits
+    info = lco.radix_permute_info(dims, sig, new)
+    assert info["passes"] == 2 and info["key_bits"] == 12
+    # uniform: high-digit (mode 2) buckets of ~3,000 entries
+    T = _rand(dims, 200_000, 11)
+    rl, rv = oracle.permute(dims, sig, new, T["liv"], T["val"])
+    gl, gv, hdf = _run_with_path(T, new)
+    assert hdf
+    assert np.array_equal(gl, rl) and np.array_equal(gv.view(np.int64), rv.view(np.int64))
+    # skewed: every (mode 0, mode 1) pair at mode 2 = 5, i.e. 16,384 entries
+    # in one high-digit bucket, more than one CTA's 8,192
+    rng = np.random.default_rng(12)
+    co = np.stack([rng.integers(0, 256, 100_000), rng.integers(0, 64, 100_000), rng.integers(0, 64, 100_000)], 1)
+    a, b = np.meshgrid(np.arange(256), np.arange(64), indexing="ij")
+    hot = np.stack([a.ravel(), b.ravel(), np.full(a.size, 5)], 1)
+    liv = np.unique(oracle.linearise(dims, sig, np.concatenate([co, hot])))
+    S = {"dims": dims, "sig": sig, "liv": liv.astype(np.int64), "val": rng.standard_normal(liv.shape[0])}
+    rl, rv = oracle.permute(dims, sig, new, S["liv"], S["val"])
+    gl, gv, hdf = _run_with_path(S, new)
+    assert not hdf
+    assert np.array_equal(gl, rl) and np.array_equal(gv.view(np.int64), rv.view(np.int64))
