@@ -221,9 +221,12 @@ def source_digest(kernel):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel):
+def profiled_traffic(kernel, config="C2"):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of the kernel (matching digest); else None."""
+    on the current source of the kernel (matching digest) and on this
+    configuration (the summary covers C2 only); else None."""
+    if config != "C2":
+        return None
     try:
         text = open(PROFILE_SUMMARY).read()
     except OSError:
@@ -454,7 +457,7 @@ def measure_config(name, device, K, warmup, world=1, local=0, max_digit_bits=0, 
     alg_bytes = algorithmic_bytes(dominant, step)
     avg_s = kernels[dominant]["work_avg_ms"] * 1e-3
     achieved = alg_bytes / avg_s / 1e9 if avg_s > 0 else 0.0
-    traffic = profiled_traffic(dominant)
+    traffic = profiled_traffic(dominant, name)
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "algorithmic_bytes": alg_bytes}
