@@ -20,6 +20,7 @@ copy, no collective in the data path).
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -994,7 +995,13 @@ def measure_batch(count, K, warmup, streams, cpu_budget_s=12.0, tune=False, per_
         tuner = Tuner(cache_path=None, reps=2)
         choice = tuner.tune_batch(items, per_class=1)
         t_tune = time.perf_counter() - t_tune
-        bt = lco.Batch([it + (alg, bits) for it, (alg, bits) in zip(items, choice)], nstreams=streams)
+        infos = [dict(x) for x in batch.info]
+        # the untuned batch's graph and workspaces go first: a tuned choice
+        # (SOP, wide digits) can need far larger workspaces
+        del graph, batch
+        gc.collect()
+        torch.cuda.empty_cache()
+        bt = lco.Batch([it + tuple(c) for it, c in zip(items, choice)], nstreams=streams)
         bt.run()
         gt = torch.cuda.CUDAGraph()
         side.wait_stream(stream)
@@ -1011,7 +1018,8 @@ def measure_batch(count, K, warmup, streams, cpu_budget_s=12.0, tune=False, per_
         e1.record(stream)
         torch.cuda.synchronize()
         ms_t = e0.elapsed_time(e1) / K
-        changed = sum(1 for inf, (alg, bits) in zip(batch.info, choice) if inf["alg"] != alg or bits != 0)
+        changed = sum(1 for inf, (alg, bits, order) in zip(infos, choice)
+                      if inf["alg"] != alg or bits != 0 or order != 0)
         out["tuned"] = {"value": round(units / (ms_t * 1e-3) / 1e9, 4), "ms_per_step": round(ms_t, 4),
                         "groups": len(tuner.cache), "problems_changed": changed, "tune_s": round(t_tune, 1)}
         del gt, bt

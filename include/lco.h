@@ -384,6 +384,10 @@ typedef struct {
     int32_t alg;             /* LCO_ALG_AUTO (Table 4) or a forced lco_alg */
     int32_t max_digit_bits;  /* radix digit width cap for operand permutations, 1..11; 0 = the
                                 default of 9 bits (wider digits coalesce worse on random keys) */
+    int32_t radix_order;     /* operand permutations: 0 = decided on the device (high digit
+                                first, each high-digit bucket then sorted inside one CTA, when
+                                two passes remain and every bucket holds at most 8,192 entries;
+                                LSD passes otherwise), 1 = LSD passes only */
 } lco_tune;
 
 /* lco_contract_plan with tuning hints (tune may be NULL = defaults). */
@@ -423,6 +427,7 @@ typedef struct {
     int32_t modes_b[LCO_MAX_ORDER];
     int32_t alg;             /* LCO_ALG_AUTO or a forced algorithm */
     int32_t max_digit_bits;  /* radix digit width cap (0 = default), see lco_tune */
+    int32_t radix_order;     /* 0 = decided on the device, 1 = LSD passes only; see lco_tune */
 } lco_problem;
 
 /* Device pointers of one problem's operands and output (C with room for

@@ -71,13 +71,13 @@ class TimingRecord(ctypes.Structure):
 
 
 class Tune(ctypes.Structure):
-    _fields_ = [("alg", ctypes.c_int32), ("max_digit_bits", ctypes.c_int32)]
+    _fields_ = [("alg", ctypes.c_int32), ("max_digit_bits", ctypes.c_int32), ("radix_order", ctypes.c_int32)]
 
 
 class Problem(ctypes.Structure):
     _fields_ = [("a", Shape), ("b", Shape), ("ncontract", ctypes.c_int32),
                 ("modes_a", ctypes.c_int32 * MAX_ORDER), ("modes_b", ctypes.c_int32 * MAX_ORDER),
-                ("alg", ctypes.c_int32), ("max_digit_bits", ctypes.c_int32)]
+                ("alg", ctypes.c_int32), ("max_digit_bits", ctypes.c_int32), ("radix_order", ctypes.c_int32)]
 
 
 class Operands(ctypes.Structure):
@@ -575,10 +575,12 @@ class ContractPlan:
     """Plan for C = A x_modes B (Sec. 5.2 poly-algorithm, Table 4 dispatch).
 
     alg forces an algorithm (name or code); max_digit_bits caps the radix
-    digit width of operand permutations (tuning hints)."""
+    digit width of operand permutations and radix_order = 1 keeps them to
+    LSD passes (0: high digit first when the device finds that two passes
+    remain and every high-digit bucket fits one CTA) -- tuning hints."""
 
     def __init__(self, a_dims, a_sig, a_nnz, b_dims, b_sig, b_nnz, modes_a, modes_b, alg=None,
-                 max_digit_bits=0, entry_a=(), entry_b=()):
+                 max_digit_bits=0, entry_a=(), entry_b=(), radix_order=0):
         self.lib = load()
         self.sa = make_shape(a_dims, a_sig, a_nnz)
         self.sb = make_shape(b_dims, b_sig, b_nnz)
@@ -589,7 +591,7 @@ class ContractPlan:
         self._mb = (ctypes.c_int32 * max(1, nc))(*[int(x) for x in modes_b])
         self._ea = (ctypes.c_int32 * max(1, ne))(*[int(x) for x in entry_a])
         self._eb = (ctypes.c_int32 * max(1, ne))(*[int(x) for x in entry_b])
-        tune = Tune(_alg_code(alg), int(max_digit_bits))
+        tune = Tune(_alg_code(alg), int(max_digit_bits), int(radix_order))
         h = ctypes.c_void_p()
         _check(self.lib.lco_contract_plan_entrywise(ctypes.byref(self.sa), ctypes.byref(self.sb), nc, self._ma,
                                                     self._mb, ne, self._ea, self._eb, ctypes.byref(tune),
@@ -659,13 +661,16 @@ class ContractPlan:
 
 
 def contract(A: LcoTensor, B: LcoTensor, modes_a, modes_b, alg=None, stream=None, return_info=False,
-             entry_a=(), entry_b=()):
+             entry_a=(), entry_b=(), max_digit_bits=0, radix_order=0):
     """C = A x_modes B as an LCO tensor (Sec. 5.2).  entry_a/entry_b pair up
     shared modes kept in C (entrywise products, Sec. 5); C's modes are those
-    pairs, A's free modes, B's free modes.  Synchronises twice: after phase 1
-    to size C by the product count f, and at the end to read nnz_C."""
+    pairs, A's free modes, B's free modes.  max_digit_bits and radix_order
+    are the operand permutations' tuning hints (see ContractPlan).
+    Synchronises twice: after phase 1 to size C by the product count f, and
+    at the end to read nnz_C."""
     plan = ContractPlan(A.dims, A.sig, A.nnz, B.dims, B.sig, B.nnz, modes_a, modes_b, alg,
-                        entry_a=entry_a, entry_b=entry_b)
+                        max_digit_bits=max_digit_bits, entry_a=entry_a, entry_b=entry_b,
+                        radix_order=radix_order)
     dev = A.liv.device
     plan.ensure_workspace(0, dev)
     plan.symbolic(A, B, stream)
@@ -691,7 +696,7 @@ def contract(A: LcoTensor, B: LcoTensor, modes_a, modes_b, alg=None, stream=None
 # Batched contractions
 # ---------------------------------------------------------------------------
 
-def _problem(A: LcoTensor, B: LcoTensor, modes_a, modes_b, alg=None, max_digit_bits=0) -> Problem:
+def _problem(A: LcoTensor, B: LcoTensor, modes_a, modes_b, alg=None, max_digit_bits=0, radix_order=0) -> Problem:
     p = Problem()
     p.a = A.shape()
     p.b = B.shape()
@@ -701,23 +706,24 @@ def _problem(A: LcoTensor, B: LcoTensor, modes_a, modes_b, alg=None, max_digit_b
         p.modes_b[i] = int(y)
     p.alg = _alg_code(alg)
     p.max_digit_bits = int(max_digit_bits or 0)
+    p.radix_order = int(radix_order or 0)
     return p
 
 
 class Batch:
     """Many independent contractions enqueued together (see lco_batch_* in
-    include/lco.h).  items: list of (A, B, modes_a, modes_b[, alg[, max_digit_bits]]).  The
+    include/lco.h).  items: list of (A, B, modes_a, modes_b[, alg[, max_digit_bits[, radix_order]]]).  The
     first call sizes every output by its product count f; `run()` then
     enqueues the whole batch with no host synchronisation and can be
     captured into a CUDA graph."""
 
     def __init__(self, items, nstreams: int = 16, device="cuda"):
         self.lib = load()
-        self.items = [tuple(it) + (None,) * (6 - len(it)) for it in items]
+        self.items = [tuple(it) + (None,) * (7 - len(it)) for it in items]
         n = len(self.items)
         self.n = n
-        self._probs = (Problem * n)(*[_problem(A, B, ma, mb, alg, bits)
-                                      for A, B, ma, mb, alg, bits in self.items])
+        self._probs = (Problem * n)(*[_problem(A, B, ma, mb, alg, bits, order)
+                                      for A, B, ma, mb, alg, bits, order in self.items])
         h = ctypes.c_void_p()
         _check(self.lib.lco_batch_plan(n, self._probs, int(nstreams), ctypes.byref(h)), "lco_batch_plan")
         self.handle = h

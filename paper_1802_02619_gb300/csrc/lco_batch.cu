@@ -415,6 +415,7 @@ int32_t build_groups(lco_batch *b) {
         lco_tune t;
         t.alg = g.family;
         t.max_digit_bits = 0;
+        t.radix_order = 0;
         int32_t rc = lco_contract_plan_entrywise(&g.sl, &g.sr, 1, &ma, &mb, 1, &ea, &eb, &t, &g.plan);
         if (rc != LCO_OK) return rc;
         g.table_bytes = lco::table_layout((size_t)H).bytes;
@@ -537,6 +538,7 @@ int32_t lco_batch_plan(int32_t nprob, const lco_problem *probs, int32_t nstreams
         lco_tune t;
         t.alg = probs[i].alg;
         t.max_digit_bits = probs[i].max_digit_bits;
+        t.radix_order = probs[i].radix_order;
         int32_t rc = lco_contract_plan_ex(&probs[i].a, &probs[i].b, probs[i].ncontract, probs[i].modes_a,
                                           probs[i].modes_b, &t, &p);
         if (rc != LCO_OK) {

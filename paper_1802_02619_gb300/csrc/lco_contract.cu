@@ -2131,6 +2131,7 @@ int32_t lco_contract_plan(const lco_shape *a, const lco_shape *b, int32_t ncontr
     lco_tune t;
     t.alg = force_alg;
     t.max_digit_bits = 0;
+    t.radix_order = 0;
     return lco_contract_plan_ex(a, b, ncontract, modes_a, modes_b, &t, plan_out);
 }
 
@@ -2146,6 +2147,7 @@ int32_t lco_contract_plan_entrywise(const lco_shape *a, const lco_shape *b, int3
     const int32_t force_alg = tune ? tune->alg : LCO_ALG_AUTO;
     const int max_bits = tune && tune->max_digit_bits > 0 ? tune->max_digit_bits : kDefaultDigitBits;
     if (tune && (tune->max_digit_bits < 0 || tune->max_digit_bits > kMaxDigitBits)) return LCO_ERR_INVALID;
+    if (tune && (tune->radix_order < 0 || tune->radix_order > 1)) return LCO_ERR_INVALID;
     if (!plan_out) return LCO_ERR_INVALID;
     *plan_out = nullptr;
     int64_t ta, tb;
@@ -2241,6 +2243,7 @@ int32_t lco_contract_plan_entrywise(const lco_shape *a, const lco_shape *b, int3
     const int32_t *r_target = transposed ? a_col : b_row;
     if ((rc = rp_plan(&p->src_l, l_target, &p->rp_l, max_bits)) != LCO_OK) { delete p; return rc; }
     if ((rc = rp_plan(&p->src_r, r_target, &p->rp_r, max_bits)) != LCO_OK) { delete p; return rc; }
+    p->rp_l.lsd_only = p->rp_r.lsd_only = tune ? tune->radix_order : 0;
     p->need_l = !same_sig(p->src_l.order, p->src_l.sig, l_target);
     p->need_r = !same_sig(p->src_r.order, p->src_r.sig, r_target);
     p->rows_h = transposed ? n : m;

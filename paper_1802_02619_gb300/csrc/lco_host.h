@@ -19,6 +19,7 @@ struct RpPlan {
     DivU64 key_div;      // key = newLIV div m_low
     int64_t total;       // product of dims
     int32_t identity;    // new order equals old order
+    int32_t lsd_only;    // never high digit first (a tuning choice)
 };
 
 int32_t rp_plan(const lco_shape *t, const int32_t *new_sig, RpPlan *out, int max_digit_bits = kDefaultDigitBits);

@@ -163,6 +163,7 @@ cudaError_t rp_enqueue(const RpPlan &plan, int64_t nnz, const int64_t *in_liv, c
     j.n_host = nnz;
     j.n_dev = nullptr;
     j.n_cap = nnz;
+    j.lsd_only = plan.lsd_only;
     j.src_liv = in_liv;
     j.src_val = in_val;
     j.dst_liv = out_liv;

@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const __grid_co
     }
     if (tid == 0) {
         j.active[kFlagQ] = nactive;
-        const int msd = LCO_RADIX_LOCAL && nactive == 2 && j.D <= kLocalMaxBits && !hi_big;
+        const int msd = LCO_RADIX_LOCAL && !j.lsd_only && nactive == 2 && j.D <= kLocalMaxBits && !hi_big;
         j.active[kFlagMsd] = msd;
         j.active[kFlagHi] = p_hi;
         j.active[kFlagLo] = p_lo;
@@ -803,7 +803,7 @@ cudaError_t radix_enqueue(const RadixJob &job, cudaStream_t stream) {
     }
     // high digit first (decided on the device; a no-op otherwise): possible
     // only for digit widths the local sort takes and two or more passes
-    if (LCO_RADIX_LOCAL && job.P >= 2 && job.D <= kLocalMaxBits) {
+    if (LCO_RADIX_LOCAL && !job.lsd_only && job.P >= 2 && job.D <= kLocalMaxBits) {
         if (shift) LCO_LAUNCH("k_radix_local", stream,
                               (k_radix_local<true><<<(unsigned)NB, kLocalThreads, local_smem_bytes(), stream>>>(job)));
         else LCO_LAUNCH("k_radix_local", stream,

@@ -40,6 +40,7 @@ struct RadixJob {
     int32_t P;             // passes
     int32_t G;             // counting CTAs (contiguous ranges of whole tiles), fixed from n_cap
     int32_t wide_lb;       // look-back words are 64-bit (capacity of 2^30 elements or more)
+    int32_t lsd_only;      // never high digit first (a tuning choice)
     int64_t n_host;        // element count, or
     const int64_t *n_dev;  // device element count (overrides n_host when set)
     int64_t n_cap;         // upper bound on the element count (sizes grids and tables)

@@ -3,8 +3,11 @@
 For a problem the tuner times candidate configurations of the library --
 the algorithm (Table 4's choice and the alternatives that are always
 correct on the GPU: CSR, CSRNA, DCSR, SOP and, for column-major inputs, the
-column variants) and the radix digit-width cap of the operand permutations
--- on the problem's own data, and keeps the fastest.  For a batch it groups
+column variants), and for the operand permutations the radix digit-width
+cap (the tile's bucket count) and the sort order (LSD passes only, or high
+digit first with each high-digit bucket sorted inside one CTA when the
+device finds the buckets small enough) -- on the problem's own data, and
+keeps the fastest.  For a batch it groups
 problems by a signature (sparsity classes, which operands need rearranging,
 size bucket) and tunes a few samples per group; decisions are cached in a
 JSON file (``LCO_TUNE_CACHE``) keyed by the signature.
@@ -51,18 +54,21 @@ class Tuner:
                 f"|na{_bucket(A.nnz)}|nb{_bucket(B.nnz)}")
 
     def candidates(self, A, B, modes_a, modes_b):
+        """(alg, max_digit_bits, radix_order) triples to time."""
         base = ContractPlan(A.dims, A.sig, A.nnz, B.dims, B.sig, B.nnz, modes_a, modes_b)
         algs = [base.info["alg"]] + [a for a in ROW_ALGS + COL_ALGS if a != base.info["alg"]]
         out = []
         for alg in algs:
             p = ContractPlan(A.dims, A.sig, A.nnz, B.dims, B.sig, B.nnz, modes_a, modes_b, alg=alg)
-            bits = [0, 6, 11] if (p.info["permute_a"] or p.info["permute_b"]) else [0]
-            out += [(alg, b) for b in bits]
+            if p.info["permute_a"] or p.info["permute_b"]:
+                out += [(alg, b, o) for b in (0, 6, 11) for o in (0, 1)]
+            else:
+                out.append((alg, 0, 0))
         return out
 
-    def time_config(self, A, B, modes_a, modes_b, alg, bits) -> float:
+    def time_config(self, A, B, modes_a, modes_b, alg, bits, order=0) -> float:
         p = ContractPlan(A.dims, A.sig, A.nnz, B.dims, B.sig, B.nnz, modes_a, modes_b, alg=alg,
-                         max_digit_bits=bits)
+                         max_digit_bits=bits, radix_order=order)
         p.ensure_workspace(0, A.liv.device)
         p.symbolic(A, B)
         f = p.result()["f"]
@@ -84,17 +90,18 @@ class Tuner:
         return statistics.median(ts)
 
     def tune(self, A, B, modes_a, modes_b):
-        """(alg, max_digit_bits, {config: ms}) for one problem."""
+        """(alg, max_digit_bits, radix_order, {config: ms}) for one problem."""
         times = {}
-        for alg, bits in self.candidates(A, B, modes_a, modes_b):
-            times[f"{alg}/{bits}"] = self.time_config(A, B, modes_a, modes_b, alg, bits)
+        for alg, bits, order in self.candidates(A, B, modes_a, modes_b):
+            times[f"{alg}/{bits}/{order}"] = self.time_config(A, B, modes_a, modes_b, alg, bits, order)
         best = min(times, key=times.get)
-        alg, bits = best.split("/")
-        return alg, int(bits), times
+        alg, bits, order = best.split("/")
+        return alg, int(bits), int(order), times
 
     def tune_batch(self, items, per_class: int = 2):
-        """Per item (alg, max_digit_bits): groups by signature, tunes up to
-        per_class samples of each new group, reuses cached decisions."""
+        """Per item (alg, max_digit_bits, radix_order): groups by signature,
+        tunes up to per_class samples of each new group, reuses cached
+        decisions."""
         groups = {}
         for idx, (A, B, ma, mb) in enumerate(items):
             groups.setdefault(self.signature(A, B, ma, mb), []).append(idx)
@@ -104,13 +111,14 @@ class Tuner:
                 totals = {}
                 for idx in idxs[:per_class]:
                     A, B, ma, mb = items[idx]
-                    _, _, times = self.tune(A, B, ma, mb)
+                    *_, times = self.tune(A, B, ma, mb)
                     for k, v in times.items():
                         totals[k] = totals.get(k, 0.0) + v
                 best = min(totals, key=totals.get)
                 self.cache[sig] = {"choice": best, "ms": totals}
-            alg, bits = self.cache[sig]["choice"].split("/")
+            parts = self.cache[sig]["choice"].split("/")
+            alg, bits, order = parts[0], int(parts[1]), int(parts[2]) if len(parts) > 2 else 0
             for idx in idxs:
-                decision[idx] = (alg, int(bits))
+                decision[idx] = (alg, bits, order)
         self.save()
         return [decision[i] for i in range(len(items))]

@@ -67,7 +67,7 @@ def test_tuner_choices_are_correct():
     items = [(_dev(A), _dev(B), ma, mb) for A, B, ma, mb, _ in probs]
     t = Tuner(cache_path=None, reps=1)
     choice = t.tune_batch(items, per_class=1)
-    b = lco.Batch([it + (alg, bits) for it, (alg, bits) in zip(items, choice)], nstreams=4)
+    b = lco.Batch([it + tuple(c) for it, c in zip(items, choice)], nstreams=4)
     b.run()
     for (A, B, ma, mb, _), C in zip(probs, b.results()):
         assert_contract_matches(C, _host(A), _host(B), ma, mb)

@@ -361,3 +361,20 @@ def test_heavy_rows_at_the_accumulator_limits():
         for alg in ("CSR", "CSRNA"):
             C, info = _run(A, B, [1], [0], alg)
             assert_contract_matches(C, A, B, [1], [0])
+
+
+def test_radix_order_hint_gives_identical_products():
+    """The operand permutation's sort order is a tuning choice: B of a_ijk
+    b_ljk is rearranged to matrix order by a two-pass key whose high-digit
+    buckets fit one CTA (high digit first on the device) or, with the hint,
+    by LSD passes; the products are bit-identical and match the oracle."""
+    A = _rand([64, 48, 40], None, 21, nnz=30_000)
+    B = _rand([50, 48, 40], None, 22, nnz=30_000)
+    ma, mb = [1, 2], [1, 2]
+    out = []
+    for order in (0, 1):
+        C, info = lco.contract(dev(A), dev(B), ma, mb, return_info=True, radix_order=order)
+        assert info["status"] == 0 and info["permute_b"]
+        out.append(assert_contract_matches(C, A, B, ma, mb))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1].view(np.int64), out[1][1].view(np.int64))
