@@ -14,7 +14,10 @@ constexpr int kUpItems = 8;       // counting kernel: consecutive keys per threa
 #define LCO_SCATTER_CTAS 3
 #endif
 constexpr int kScatterCtas = LCO_SCATTER_CTAS;
-constexpr int kUpsweepCtasPerSm = 4;
+#ifndef LCO_UPSWEEP_CTAS
+#define LCO_UPSWEEP_CTAS 4
+#endif
+constexpr int kUpsweepCtasPerSm = LCO_UPSWEEP_CTAS;   // counting CTAs per SM; a build may override it
 constexpr int kCtrUpsweep = 8;    // header counter: counting blocks finished
 constexpr int kCtrTile = 12;      // header counters [12, 12 + kMaxPasses): tiles taken by the q-th run pass
 // Two-pass keys whose high-digit buckets all fit one CTA's shared memory are
