@@ -126,7 +126,8 @@ typedef struct {
     int64_t m_low;                   /* product of dims of the resting suffix */
     int32_t key_bits;                /* bits of the sort key newLIV / m_low */
     int32_t digit_bits;              /* radix digit width */
-    int32_t passes;                  /* LSD passes (before histogram-based skipping) */
+    int32_t passes;                  /* radix passes of the digit plan (before passes whose digit
+                                        is constant are skipped on the device) */
     int32_t segments;                /* 1 = flat sort */
 } lco_rp_info;
 
@@ -140,10 +141,14 @@ int32_t lco_radix_permute_workspace(const lco_shape *t, const int32_t *new_sig, 
 /* Rearranges (liv_in, val_in), strictly ascending in order t->sig, into
  * (liv_out, val_out), strictly ascending in order new_sig, with liv_out
  * holding the new LIVs.  Values are moved bit-exactly.  Implementation:
- * a fused re-linearise + one-read digit histogram, then one stable
- * least-significant-digit scatter pass per radix digit of the key
- * newLIV div m_low (the resting suffix is supplied by stability); passes
- * whose digit is constant over the data are skipped on the device.
+ * one read of the re-linearised keys counts every pass's digits, then one
+ * stable scatter pass per radix digit of the key newLIV div m_low (the
+ * resting suffix is supplied by stability), least significant first, each
+ * tile finding its digits' offsets by decoupled look-back; passes whose
+ * digit is constant over the data are skipped on the device.  When two
+ * passes remain and every bucket of the high digit holds at most 8,192
+ * entries (decided on the device), the high digit is scattered first and
+ * each bucket is then sorted by the low digit inside one CTA.
  * liv_in/val_in/liv_out/val_out: device, t->nnz elements each, no aliasing.
  * ws: device workspace of lco_radix_permute_workspace() bytes.
  * Errors: LCO_ERR_INVALID, LCO_ERR_OVERFLOW, LCO_ERR_OOM (ws too small),

@@ -19,7 +19,7 @@ namespace {
 
 // Largest tensor (number of non-zeros) the fixed scratch serves.
 constexpr int64_t kStaticMaxNnz = 65536;
-// Header + histogram/offset tables + look-back state for the widest digit
+// Header + digit counts and run starts + look-back words for the widest digit
 // plan + two temporary (LIV, value) buffers, for kStaticMaxNnz elements.
 constexpr size_t kStaticScratchBytes = 3u << 20;   // 3 MiB
 

@@ -10,7 +10,9 @@
 // 2048-element tile in order, ranks it with warp match instructions,
 // publishes its per-digit counts and finds the counts of the tiles before it
 // by decoupled look-back, so that the tile's runs land at their final place
-// without a separate counting or offset launch.
+// without a separate counting or offset launch.  When two passes remain and
+// every high-digit bucket fits one CTA, the high digit goes first and a
+// local-sort launch orders each bucket by the low digit.
 #pragma once
 
 #include "lco_internal.cuh"
