@@ -303,26 +303,42 @@ struct DcsrArgs {
     WsHeader *hdr;
 };
 
-// Head flags -> single-pass scan -> compacted (row_id, row_ptr).
+// Head flags -> single-pass scan -> compacted (row_id, row_ptr).  Rows are
+// computed warp-striped and scanned blocked, through shared memory as in
+// the work scan below.
+constexpr int kScanPitch = kCT + 4;
+
 __global__ void __launch_bounds__(kCT) k_dcsr_build(const __grid_constant__ DcsrArgs a) {
     __shared__ int64_t s_tmp[kCW + 1];
     __shared__ int64_t s_tile, s_excl;
+    __shared__ int64_t s_rows[kScanItems * kScanPitch];
     if (threadIdx.x == 0) s_tile = atomicAdd(&a.hdr->counters[kCtrDcsr], 1u);
     __syncthreads();
     const int64_t tile = s_tile;
-    const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    int64_t rows[kScanItems];
-    int heads = 0;
-    int64_t prev = base > 0 && base - 1 < a.nnz ? (int64_t)divu(a.div_n, (uint64_t)a.liv[base - 1]) : -1;
+    const int64_t tbase = tile * kScanTile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t prev0 = -1;
+    if (threadIdx.x == 0 && tbase > 0 && tbase - 1 < a.nnz)
+        prev0 = (int64_t)divu(a.div_n, (uint64_t)a.liv[tbase - 1]);
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        const int64_t e = base + i;
-        if (e < a.nnz) {
-            rows[i] = (int64_t)divu(a.div_n, (uint64_t)a.liv[e]);
+        const int j = warp * (32 * kScanItems) + 32 * i + lane;
+        const int64_t e = tbase + j;
+        s_rows[(j % kScanItems) * kScanPitch + j / kScanItems] =
+            e < a.nnz ? (int64_t)divu(a.div_n, (uint64_t)a.liv[e]) : -2;
+    }
+    __syncthreads();
+    const int64_t base = tbase + (int64_t)threadIdx.x * kScanItems;
+    if (threadIdx.x > 0) prev0 = s_rows[(kScanItems - 1) * kScanPitch + threadIdx.x - 1];
+    int64_t rows[kScanItems];
+    int heads = 0;
+    int64_t prev = prev0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        rows[i] = s_rows[i * kScanPitch + threadIdx.x];
+        if (base + i < a.nnz) {
             heads += rows[i] != prev;
             prev = rows[i];
-        } else {
-            rows[i] = -2;
         }
     }
     int64_t tot;
@@ -343,7 +359,7 @@ __global__ void __launch_bounds__(kCT) k_dcsr_build(const __grid_constant__ Dcsr
     }
     __syncthreads();
     int64_t pos = s_excl + ex;
-    prev = base > 0 && base - 1 < a.nnz ? (int64_t)divu(a.div_n, (uint64_t)a.liv[base - 1]) : -1;
+    prev = prev0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         const int64_t e = base + i;
@@ -412,25 +428,33 @@ struct ScanArgs {
     WsHeader *hdr;
 };
 
-// Item i of thread t keeps its work and row id in shared memory at
-// i * kCT + t (conflict-free), not in registers: six CTAs fit on an SM, so
-// that more tiles are in flight at once and fewer wait on their look-backs.
-// The lookups are two loads (CSR R) or read from the entry cache (DCSR R).
+// The entries are loaded and looked up warp-striped (entry w * 256 + 32 i +
+// lane in item i of warp w: every load instruction reads consecutive
+// entries, and consecutive entries of a row meet nearby R rows), then
+// scanned blocked (thread t owns the tile's entries 8 t .. 8 t + 7).  Entry
+// j's work and row id pass between the two through shared memory at
+// (j mod 8) * kScanPitch + j / 8: the warp-striped stores hit every bank
+// pair twice and the blocked loads are conflict-free.  Six CTAs fit on an
+// SM, so that more tiles are in flight at once and fewer wait on their
+// look-backs.  The lookups are two loads (CSR R) or read from the entry
+// cache (DCSR R).
 __global__ void __launch_bounds__(kCT, 6) k_work_scan(const __grid_constant__ ScanArgs a) {
     __shared__ int64_t s_tmp[kCW + 1];
     __shared__ int64_t s_tile, s_ew, s_eh;
-    __shared__ int64_t s_w[kScanTile], s_rows[kScanTile];
+    __shared__ int64_t s_w[kScanItems * kScanPitch], s_rows[kScanItems * kScanPitch];
     if (threadIdx.x == 0) s_tile = atomicAdd(&a.hdr->counters[kCtrScan], 1u);
     __syncthreads();
     const int64_t tile = s_tile;
-    const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    int64_t wsum = 0, hsum = 0;
-    uint32_t heads = 0;
+    const int64_t tbase = tile * kScanTile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // row of the entry before the tile (thread 0 only)
     int64_t prev = -1;
-    if (base > 0 && base - 1 < a.nnz_l) prev = (int64_t)divu(a.div_k, (uint64_t)a.l_liv[base - 1]);
+    if (threadIdx.x == 0 && tbase > 0 && tbase - 1 < a.nnz_l)
+        prev = (int64_t)divu(a.div_k, (uint64_t)a.l_liv[tbase - 1]);
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        const int64_t e = base + i;
+        const int j = warp * (32 * kScanItems) + 32 * i + lane;
+        const int64_t e = tbase + j;
         int64_t wi = 0, ri = -1;
         if (e < a.nnz_l) {
             const uint64_t liv = (uint64_t)a.l_liv[e];
@@ -440,12 +464,24 @@ __global__ void __launch_bounds__(kCT, 6) k_work_scan(const __grid_constant__ Sc
             mdt_lookup_entry(a.mdt, e, c, b0, len);
             wi = 1 + len;
             ri = (int64_t)row;
-            if ((int64_t)row != prev) heads |= 1u << i;
-            prev = (int64_t)row;
         }
-        s_w[i * kCT + threadIdx.x] = wi;
-        s_rows[i * kCT + threadIdx.x] = ri;
-        wsum += wi;
+        const int slot = (j % kScanItems) * kScanPitch + j / kScanItems;
+        s_w[slot] = wi;
+        s_rows[slot] = ri;
+    }
+    __syncthreads();
+    const int64_t base = tbase + (int64_t)threadIdx.x * kScanItems;
+    if (threadIdx.x > 0) prev = s_rows[(kScanItems - 1) * kScanPitch + threadIdx.x - 1];
+    int64_t wsum = 0, hsum = 0;
+    uint32_t heads = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t ri = s_rows[i * kScanPitch + threadIdx.x];
+        if (base + i < a.nnz_l) {
+            if (ri != prev) heads |= 1u << i;
+            prev = ri;
+        }
+        wsum += s_w[i * kScanPitch + threadIdx.x];
     }
     hsum = __popc(heads);
     int64_t wtot, htot;
@@ -490,12 +526,12 @@ __global__ void __launch_bounds__(kCT, 6) k_work_scan(const __grid_constant__ Sc
             if (a.P) a.P[e] = run;
             if (heads & (1u << i)) {
                 a.row_start[h] = e;
-                a.row_id[h] = s_rows[i * kCT + threadIdx.x];
+                a.row_id[h] = s_rows[i * kScanPitch + threadIdx.x];
                 a.row_work[h] = run;
                 ++h;
             }
         }
-        run += s_w[i * kCT + threadIdx.x];
+        run += s_w[i * kScanPitch + threadIdx.x];
     }
 }
 
@@ -1129,6 +1165,7 @@ static_assert(kHeavySmemBytes <= 227 * 1024, "heavy-row shared memory exceeds a 
 // ------------------------------------------------------------------------
 constexpr int kLaneProd = 64;          // products a lane merges by itself
 constexpr int kRowsThreads = 128;      // 4 warps per CTA
+constexpr int kRowsCtas = 4;           // resident CTAs per SM (registers and shared memory)
 constexpr int kWarpSortCap = kHeavyWork;   // products of a warp-sorted row
 
 struct RowsArgs {
@@ -1423,7 +1460,7 @@ __device__ __forceinline__ void net_gather_direct(const RowsArgs &a, int64_t es,
 // Otherwise a CTA takes kWarps consecutive 32-row tiles at a time (one per
 // warp) and finds their place in C with one decoupled look-back.
 template <typename KeyT, bool kScratch>
-__global__ void __launch_bounds__(kRowsThreads, 4) k_rows(const __grid_constant__ RowsArgs a) {
+__global__ void __launch_bounds__(kRowsThreads, kRowsCtas) k_rows(const __grid_constant__ RowsArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     RowsSmem &S = reinterpret_cast<RowsSmem *>(smem_raw)[warp];
@@ -2638,8 +2675,10 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
             ra.sup_tot = reinterpret_cast<unsigned long long *>(p2 + L.sup_tot);
         }
         const int warps = kRowsThreads / 32;
+        // persistent: one wave of resident CTAs takes every tile (CTAs of a
+        // later wave would only find the tile counter exhausted)
         int64_t grid = (nchunks_max + warps - 1) / warps;
-        if (grid > (int64_t)sms * 16) grid = (int64_t)sms * 16;
+        if (grid > (int64_t)sms * kRowsCtas) grid = (int64_t)sms * kRowsCtas;
         const size_t rows_smem = sizeof(RowsSmem) * warps;
         const bool narrow = p->nR <= (int64_t)0xfffffffell;
         if (scratch) {
