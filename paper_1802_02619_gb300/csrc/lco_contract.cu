@@ -442,6 +442,7 @@ __global__ void __launch_bounds__(kCT, 6) k_work_scan(const __grid_constant__ Sc
     __shared__ int64_t s_tmp[kCW + 1];
     __shared__ int64_t s_tile, s_ew, s_eh;
     __shared__ int64_t s_w[kScanItems * kScanPitch], s_rows[kScanItems * kScanPitch];
+    grid_dep_wait();
     if (threadIdx.x == 0) s_tile = atomicAdd(&a.hdr->counters[kCtrScan], 1u);
     __syncthreads();
     const int64_t tile = s_tile;
@@ -1133,6 +1134,7 @@ __global__ void __launch_bounds__(kCT, 1) k_heavy(const __grid_constant__ HeavyA
     HeavySmem &S = *reinterpret_cast<HeavySmem *>(smem_raw);
     AccSmem &SA = *reinterpret_cast<AccSmem *>(smem_raw);
     __shared__ int64_t s_h;
+    grid_dep_wait();
     const int tid = threadIdx.x;
     if (a.hdr->f > a.cap) return;
     const int64_t nheavy = (int64_t)*a.nheavy;
@@ -1464,6 +1466,7 @@ __global__ void __launch_bounds__(kRowsThreads, kRowsCtas) k_rows(const __grid_c
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     RowsSmem &S = reinterpret_cast<RowsSmem *>(smem_raw)[warp];
+    grid_dep_wait();
     if (a.hdr->f > a.cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             set_error(&a.hdr->status, LCO_ERR_CAPACITY);
@@ -1813,6 +1816,7 @@ __global__ void __launch_bounds__(kRowsThreads, kRowsCtas) k_rows(const __grid_c
 // k_rows has placed them (row_hout[r] = output offset); one CTA copies each.
 // ------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_copy_rows(const __grid_constant__ RowsArgs a) {
+    grid_dep_wait();
     if (a.hdr->f > a.cap) return;
     const int64_t ncopy = (int64_t)*a.ncopy;
     for (int64_t q = blockIdx.x; q < ncopy; q += gridDim.x) {
@@ -1884,6 +1888,7 @@ __global__ void __launch_bounds__(kCompactThreads, kCompactCtas) k_compact(const
     __shared__ int64_t s_goff;
     __shared__ int64_t s_pre[kCompactTiles + 1];
     __shared__ int64_t s_src[kCompactTiles];
+    grid_dep_wait();
     if (a.hdr->f > a.cap) return;
     const int64_t nact = a.act_rows ? (int64_t)*a.nact : a.hdr->nrows_l;
     const int64_t ntiles = (nact + 31) / 32;
@@ -2530,7 +2535,8 @@ int32_t symbolic_enqueue(const lco_plan *p, const int64_t *a_liv, const double *
     sa.state_h = scan_state + ((p->nnz_l + kScanTile - 1) / kScanTile) + 1;
     sa.hdr = hdr;
     const int64_t tiles = (p->nnz_l + kScanTile - 1) / kScanTile;
-    LCO_LAUNCH("k_work_scan", s, k_work_scan<<<(unsigned)tiles, kCT, 0, s>>>(sa));
+    // after a kernel (the row-pointer, DCSR or lookup launch): dependent launch
+    LCO_LAUNCH("k_work_scan", s, launch_dependent(k_work_scan, (unsigned)tiles, kCT, 0, s, sa));
     return cudaGetLastError() == cudaSuccess ? LCO_OK : LCO_ERR_CUDA;
 }
 
@@ -2635,7 +2641,8 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
             cudaFuncSetAttribute(k_rows<uint64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem);
             attr_done.fetch_or(bit);
         }
-        LCO_LAUNCH("k_heavy", s, k_heavy<<<(unsigned)sms, kCT, kHeavySmemBytes, s>>>(ha));
+        // this and the launches below follow a kernel: dependent launches
+        LCO_LAUNCH("k_heavy", s, launch_dependent(k_heavy, (unsigned)sms, kCT, kHeavySmemBytes, s, ha));
         RowsArgs ra{};
         ra.l_liv = o.l_liv;
         ra.l_val = o.l_val;
@@ -2683,18 +2690,18 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
         const bool narrow = p->nR <= (int64_t)0xfffffffell;
         if (scratch) {
             if (narrow) {
-                LCO_LAUNCH("k_rows", s, k_rows<uint32_t, true><<<(unsigned)grid, kRowsThreads, rows_smem, s>>>(ra));
+                LCO_LAUNCH("k_rows", s, launch_dependent(k_rows<uint32_t, true>, (unsigned)grid, kRowsThreads, rows_smem, s, ra));
             } else {
-                LCO_LAUNCH("k_rows", s, k_rows<uint64_t, true><<<(unsigned)grid, kRowsThreads, rows_smem, s>>>(ra));
+                LCO_LAUNCH("k_rows", s, launch_dependent(k_rows<uint64_t, true>, (unsigned)grid, kRowsThreads, rows_smem, s, ra));
             }
         } else {
             if (narrow) {
-                LCO_LAUNCH("k_rows", s, k_rows<uint32_t, false><<<(unsigned)grid, kRowsThreads, rows_smem, s>>>(ra));
+                LCO_LAUNCH("k_rows", s, launch_dependent(k_rows<uint32_t, false>, (unsigned)grid, kRowsThreads, rows_smem, s, ra));
             } else {
-                LCO_LAUNCH("k_rows", s, k_rows<uint64_t, false><<<(unsigned)grid, kRowsThreads, rows_smem, s>>>(ra));
+                LCO_LAUNCH("k_rows", s, launch_dependent(k_rows<uint64_t, false>, (unsigned)grid, kRowsThreads, rows_smem, s, ra));
             }
         }
-        LCO_LAUNCH("k_copy_rows", s, k_copy_rows<<<(unsigned)(sms * 2), 256, 0, s>>>(ra));
+        LCO_LAUNCH("k_copy_rows", s, launch_dependent(k_copy_rows, (unsigned)(sms * 2), 256, 0, s, ra));
         if (scratch) {
             CompactArgs ca{};
             ca.s_liv = ra.c_liv;
@@ -2711,7 +2718,8 @@ int32_t numeric_enqueue(const lco_plan *p, const int64_t *a_liv, const double *a
             ca.hdr = hdr;
             const int64_t nblk = (nchunks_max + 7) / 8;
             int64_t cgrid = nblk < (int64_t)sms * kCompactCtas ? nblk : (int64_t)sms * kCompactCtas;
-            LCO_LAUNCH("k_compact", s, k_compact<<<(unsigned)(cgrid > 0 ? cgrid : 1), kCompactThreads, 0, s>>>(ca));
+            LCO_LAUNCH("k_compact", s,
+                       launch_dependent(k_compact, (unsigned)(cgrid > 0 ? cgrid : 1), kCompactThreads, 0, s, ca));
         }
     } else {
         SopArgs sa{};

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cstdlib>
 #include <cuda_runtime.h>
 
 #include "lco.h"
@@ -366,6 +367,44 @@ struct NvtxRange {
 // Kernel timing / launch counting (implemented in lco_api.cu).
 void timing_begin(const char *name, cudaStream_t s);
 void timing_end(cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch.  A kernel launched by launch_dependent() is
+// scheduled while the kernel before it in the stream drains, instead of
+// after that kernel has completed; its CTAs then wait in grid_dep_wait()
+// until the predecessor has completed and its writes are visible.  Every
+// kernel launched this way calls grid_dep_wait() before any other memory
+// access, so that (by induction along the stream) it also sees the writes of
+// every earlier operation.  launch_dependent() is used only where the
+// operation before the launch in the stream is a kernel launch.  In a kernel
+// launched normally the wait returns at once.  LCO_PDL=0 in the environment
+// turns the programmatic launches into ordinary ones.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+inline bool pdl_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("LCO_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                             cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 }  // namespace lco
 

@@ -339,6 +339,7 @@ __global__ void __launch_bounds__(kRadixThreads, kScatterCtas)
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_wtot[kRadixWarps];
     using LB = LbWord<W>;
+    grid_dep_wait();
     const PassIO io = pass_io(j, pass);
     if (!io.run) return;
     const int D = j.D;
@@ -591,6 +592,7 @@ template <bool kShift>
 __global__ void __launch_bounds__(kLocalThreads, 2) k_radix_local(const __grid_constant__ RadixJob j) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t s_wtot[kLocalWarps];
+    grid_dep_wait();
     if (!j.active[kFlagMsd]) return;
     const int D = j.D, NB = 1 << D;
     const int b = blockIdx.x;
@@ -769,8 +771,10 @@ namespace {
 
 template <bool kShift, typename W>
 void launch_scatter(const RadixJob &job, int p, unsigned grid, cudaStream_t stream) {
+    // after the counting launch or the previous pass: a dependent launch
     LCO_LAUNCH("k_radix_scatter", stream,
-               (k_radix_scatter<kShift, W><<<grid, kRadixThreads, scatter_smem_bytes(job.D), stream>>>(job, p)));
+               launch_dependent(k_radix_scatter<kShift, W>, grid, kRadixThreads, scatter_smem_bytes(job.D), stream,
+                                job, p));
 }
 
 }  // namespace
@@ -818,10 +822,13 @@ cudaError_t radix_enqueue(const RadixJob &job, cudaStream_t stream) {
     // high digit first (decided on the device; a no-op otherwise): possible
     // only for digit widths the local sort takes and two or more passes
     if (LCO_RADIX_LOCAL && !job.lsd_only && job.P >= 2 && job.D <= kLocalMaxBits) {
+        // after the last pass: a dependent launch
         if (shift) LCO_LAUNCH("k_radix_local", stream,
-                              (k_radix_local<true><<<(unsigned)NB, kLocalThreads, local_smem_bytes(), stream>>>(job)));
+                              launch_dependent(k_radix_local<true>, (unsigned)NB, kLocalThreads, local_smem_bytes(),
+                                               stream, job));
         else LCO_LAUNCH("k_radix_local", stream,
-                        (k_radix_local<false><<<(unsigned)NB, kLocalThreads, local_smem_bytes(), stream>>>(job)));
+                        launch_dependent(k_radix_local<false>, (unsigned)NB, kLocalThreads, local_smem_bytes(),
+                                         stream, job));
         err = cudaGetLastError();
     }
     return err;
