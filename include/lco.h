@@ -29,6 +29,12 @@
  *     serves one call at a time.
  *   - Outputs must not alias inputs.
  *   - No entry point allocates device memory except lco_serve_create.
+ *   - Within a call, a kernel that follows another kernel is enqueued as a
+ *     programmatic dependent launch (scheduled while its predecessor
+ *     drains; it waits for the predecessor's writes before touching
+ *     memory).  LCO_PDL=0 in the environment, read once per process, makes
+ *     these ordinary launches.  Results are identical either way, and both
+ *     forms can be captured in a CUDA graph.
  */
 #ifndef LCO_H
 #define LCO_H
