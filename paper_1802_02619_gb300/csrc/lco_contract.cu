@@ -1216,6 +1216,7 @@ constexpr int kSupTiles = 2048;
 
 constexpr int kStage = 32 * 16;           // staged outputs of a tile's register-sorted rows
 constexpr int kLaneEnt = 16;              // rows with more entries look their R rows up warp-wide
+constexpr int kLaneCopy = 8;              // merged lane rows: entries copied per round of loads
 
 // Per warp: the warp-sort buffer, later reused to stage the outputs of the
 // register-sorted rows so that they reach C as coalesced stores.
@@ -1594,7 +1595,16 @@ __global__ void __launch_bounds__(kRowsThreads, kRowsCtas) k_rows(const __grid_c
                 const int nr = collect_runs(a, es, ee, rid, st, ln, av);
                 if (nr <= kMergeRuns && frow <= kLaneProd) {
                     kind = kRowLane;
-                    cnt = lane_merge_g<false, KeyT>(a, st, ln, av, 0, nullptr, nullptr);
+                    if constexpr (kScratch) {
+                        cnt = lane_merge_g<false, KeyT>(a, st, ln, av, 0, nullptr, nullptr);
+                    } else {
+                        // look-back placement (small L, the latency regime):
+                        // merge once, into the product-offset scratch that
+                        // warp-sorted rows use, and copy out once placed,
+                        // instead of merging a second time after the look-back
+                        cnt = lane_merge_g<true, KeyT>(a, st, ln, av, 0, reinterpret_cast<int64_t *>(a.sk0 + pb),
+                                                       a.sv0 + pb);
+                    }
                 } else if (nr == 1) {
                     kind = kRowCopy;
                     cnt = ln[0];
@@ -1760,11 +1770,34 @@ __global__ void __launch_bounds__(kRowsThreads, kRowsCtas) k_rows(const __grid_c
             }
         }
         if (kind == kRowLane) {
-            int64_t st[kMergeRuns];
-            int32_t ln[kMergeRuns];
-            double av[kMergeRuns];
-            collect_runs(a, es, ee, rid, st, ln, av);
-            lane_merge_g<true, KeyT>(a, st, ln, av, cbase, a.c_liv + obase, a.c_val + obase);
+            if constexpr (kScratch) {
+                int64_t st[kMergeRuns];
+                int32_t ln[kMergeRuns];
+                double av[kMergeRuns];
+                collect_runs(a, es, ee, rid, st, ln, av);
+                lane_merge_g<true, KeyT>(a, st, ln, av, cbase, a.c_liv + obase, a.c_val + obase);
+            } else {
+                // the merged row, from the product-offset scratch: eight
+                // entries' loads in flight at a time
+                const uint64_t *hk = a.sk0 + pb;
+                const double *hv = a.sv0 + pb;
+                for (int64_t i0 = 0; i0 < cnt; i0 += kLaneCopy) {
+                    uint64_t kk[kLaneCopy];
+                    double vv[kLaneCopy];
+#pragma unroll
+                    for (int u = 0; u < kLaneCopy; ++u) {
+                        kk[u] = i0 + u < cnt ? hk[i0 + u] : 0;
+                        vv[u] = i0 + u < cnt ? hv[i0 + u] : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kLaneCopy; ++u) {
+                        if (i0 + u < cnt) {
+                            a.c_liv[obase + i0 + u] = cbase + (int64_t)kk[u];
+                            a.c_val[obase + i0 + u] = vv[u];
+                        }
+                    }
+                }
+            }
         }
         // copies done by the whole warp
         unsigned wm = __ballot_sync(kFull, kind == kRowCopy || kind == kRowSort || kind == kRowHeavy);
