@@ -496,7 +496,8 @@ int32_t lco_batch_results(const lco_batch *batch, const int64_t *caps, const voi
 /* ------------------------------------------------------------------ */
 
 /* Every device-side wait in the library (decoupled look-back over tiles,
- * bulk-copy mbarrier phases) gives up after a budget of SM clock cycles
+ * and the mbarrier phase wait of its bulk-copy helper) gives up after a
+ * budget of SM clock cycles
  * (about one second), records LCO_ERR_TIMEOUT in the status word and lets
  * its kernel finish, so a lost producer never hangs the GPU.  This call
  * makes both kinds of wait run out on purpose: with the budget lowered to

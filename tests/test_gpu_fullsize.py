@@ -1,10 +1,11 @@
 """GPU parity at the sizes the benchmarks run, element by element against the
 oracle.
 
-The radix scatter changes form with the input size (ranges of many tiles
-take the double-buffered bulk-copy input), and the DCSR entry cache packs
-row starts into 40 bits: both only engage on large inputs.  These tests run
-them at full size -- stand-alone permutations of 8M and 12M keys, the
+At full size the radix passes run thousands of tiles whose look-backs
+overlap, two-pass keys have high-digit buckets too large for one CTA (so
+the LSD passes run), and the DCSR entry cache packs row starts into 40
+bits: none of this engages on small inputs.  These tests run them at full
+size -- stand-alone permutations of 8M and 12M keys, the
 hyper-sparse R-MAT product C3 (10M non-zeros per operand, DCSR, B permuted
 with a 32-bit key in four passes) and the Sec. 6 product b_ii'jl d_i'k at
 N = 2047 (b has 8.4M entries) -- and compare every LIV bit-exactly and every
@@ -49,7 +50,7 @@ def _check_perm(T, new_sig, passes=None):
     ([256, 512, 128, 1024], 12_000_000, [2, 0, 3, 1], 3),  # power-of-two dims (bit fields), 19-bit key
     ([4096, 4096, 4096], 8_000_000, [0, 2, 1], 3),         # order 3, 24-bit key
 ])
-def test_bulk_form_permutations(dims, nnz, new_sig, passes):
+def test_full_size_permutations(dims, nnz, new_sig, passes):
     _check_perm(_rand(dims, nnz, seed=nnz % 1000 + len(dims)), new_sig, passes)
 
 
