@@ -497,9 +497,9 @@ int32_t lco_batch_results(const lco_batch *batch, const int64_t *caps, const voi
 
 /* Every device-side wait in the library (decoupled look-back over tiles,
  * and the mbarrier phase wait of its bulk-copy helper) gives up after a
- * budget of SM clock cycles
- * (about one second), records LCO_ERR_TIMEOUT in the status word and lets
- * its kernel finish, so a lost producer never hangs the GPU.  This call
+ * budget of SM clock cycles (about one second), records LCO_ERR_TIMEOUT in
+ * the status word and lets its kernel finish, so a lost producer never
+ * hangs the GPU.  This call
  * makes both kinds of wait run out on purpose: with the budget lowered to
  * budget_cycles (an argument of this test kernel only: kernels running at
  * the same time on other streams keep the full budget), one warp looks back over tiles
